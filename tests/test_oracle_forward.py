@@ -1,0 +1,198 @@
+"""Pins of the FP64 oracle's forward operator and adjoint against what the mathematics fixes.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign or
+shift, a transposed operand, a wrong unit conversion) fails at least one of them:
+
+* exact discrete solution p^n = F^-1 cos(n c |k| dt) F p0 (homogeneous, lossless, periodic),
+* the leapfrog energy invariant on a heterogeneous medium,
+* the transpose identities (D-)^T = -D+ and <Hx, h> = <x, H^T h>,
+* the staggered derivative of a sine,
+* the physical decay rate and dispersion sign of a plane mode under power-law absorption,
+* linear interpolation reproduces linear fields; an on-node sensor reads the node value,
+* finite differences of the quadratic data misfit.
+"""
+import numpy as np
+import pytest
+from numpy.fft import irfftn, rfftn
+
+from oracle.pat_oracle import Operator, sensor_matrix
+from paper_1603_02329_gb300 import synth
+
+
+def _all_points(shape):
+    return np.arange(int(np.prod(shape)))
+
+
+@pytest.mark.parametrize("shape", [(24, 30), (12, 14, 10)])
+def test_exact_periodic_solution(shape):
+    # Homogeneous lossless medium without PML: the kappa-corrected leapfrog is exact in time,
+    # P^{n+1} - 2 cos(w) P^n + P^{n-1} = 0 with w = c |k| dt and P^1 = cos(w) P^0.
+    rng = np.random.default_rng(1)
+    h = 1e-4
+    c = 1500.0
+    dt = 0.3 * h / c
+    Nt = 25
+    op = Operator(shape, (h,) * len(shape), (0,) * len(shape), 2.0, c, 1000.0, 0.0, 1.5, dt, Nt,
+                  sensor_index=_all_points(shape))
+    p0 = rng.standard_normal(shape)
+    data = op.forward(p0)
+    kx = [2 * np.pi * np.fft.fftfreq(n, h) for n in shape]
+    kk = np.meshgrid(*kx, indexing="ij")
+    w = c * np.sqrt(sum(k * k for k in kk)) * dt
+    for n in (1, 2, 7, Nt - 1):
+        ref = np.real(np.fft.ifftn(np.cos(n * w) * np.fft.fftn(p0)))
+        assert np.max(np.abs(data[n] - ref.ravel())) < 1e-12 * np.max(np.abs(p0)) * 10
+
+
+def test_energy_invariant_heterogeneous():
+    # E^n = 1/2 sum p^2/(rho0 c0^2) + 1/2 sum_xi u^(n-1/2) u^(n+1/2) / b_xi is conserved by the
+    # leapfrog when (D-)^T = -D+, with PML and absorption off and a heterogeneous medium.
+    rng = np.random.default_rng(2)
+    shape = (32, 36)
+    h = 1e-4
+    c, rho = synth.heterogeneous_medium(rng, shape, sigma_px=3.0)
+    dt = 0.3 * h / c.max()
+    Nt = 60
+    op = Operator(shape, (h, h), (0, 0), 2.0, c, rho, 0.0, 1.5, dt, Nt, sensor_index=[0])
+    p0 = synth.discs(rng, shape, (h, h), 3, 1e-3, (2e-4, 6e-4), (0.5, 1.0))
+    _, ps, us = op.forward(p0, keep_fields=True)
+    E = []
+    for n in range(Nt - 1):
+        ep = 0.5 * np.sum(ps[n] ** 2 / (rho * c * c))
+        eu = 0.5 * sum(np.sum(us[n][a] * us[n + 1][a] / op.b[a]) for a in range(2))
+        E.append(ep + eu)
+    E = np.array(E)
+    assert np.max(np.abs(E - E[0])) / E[0] < 1e-12
+    # the pressure part alone is not conserved: the check is not vacuous
+    ep_only = [0.5 * np.sum(ps[n] ** 2 / (rho * c * c)) for n in range(Nt - 1)]
+    assert np.ptp(ep_only) / ep_only[0] > 1e-3
+
+
+def test_derivative_transpose_and_sine():
+    rng = np.random.default_rng(3)
+    shape = (16, 20)
+    h = (1e-4, 2e-4)
+    op = Operator(shape, h, (0, 0), 2.0, 1500.0, 1000.0, 0.0, 1.5, 1e-8, 2, sensor_index=[0])
+    f = rng.standard_normal(shape)
+    g = rng.standard_normal(shape)
+    for a in range(2):
+        lhs = np.sum(op.Dminus(a, f) * g)
+        rhs = -np.sum(f * op.Dplus(a, g))
+        assert abs(lhs - rhs) < 1e-12 * np.linalg.norm(f) * np.linalg.norm(g) * 1e3
+    # D+_x sin(k0 x) = k0 kappa(k0) cos(k0 (x + h/2)), a single-mode identity
+    nx = shape[1]
+    x = (np.arange(nx) - nx // 2) * h[1]
+    k0 = 2 * np.pi * 3 / (nx * h[1])
+    s = np.broadcast_to(np.sin(k0 * x), shape)
+    zk = 1500.0 * k0 * 1e-8 / 2
+    kappa = np.sin(zk) / zk
+    ref = k0 * kappa * np.cos(k0 * (x + h[1] / 2))
+    assert np.max(np.abs(op.Dplus(1, s) - ref[None, :])) < 1e-9 * k0
+
+
+@pytest.mark.parametrize("case", ["lossy2d_offgrid", "lossy3d_ongrid", "lossless2d"])
+def test_adjoint_dot_product(case):
+    if case == "lossy2d_offgrid":
+        pb = synth.small_lossy_2d(shape=(32, 40), pml=6, Nt=40, n_sensors=12)
+    elif case == "lossy3d_ongrid":
+        pb = synth.small_lossy_3d(shape=(12, 16, 20), pml=3, Nt=20)
+    else:
+        pb = synth.disc_phantom_2d(interior=24, pml=6, Nt=40, n_sensors=10, sensor_radius=1e-3)
+    op = Operator.from_problem(pb)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(pb.shape)
+    hh = rng.standard_normal((pb.Nt, op.Ns))
+    Hx = op.forward(x)
+    HTh = op.adjoint(hh)
+    lhs, rhs = np.sum(Hx * hh), np.sum(x * HTh)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Hx) * np.linalg.norm(hh)
+    assert np.linalg.norm(Hx) > 0 and np.linalg.norm(HTh) > 0
+
+
+def test_finite_difference_gradient():
+    # f is quadratic, so the central difference equals <grad f, v> for any step
+    pb = synth.small_lossy_2d(shape=(24, 28), pml=5, Nt=30, n_sensors=10)
+    op = Operator.from_problem(pb)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(pb.shape)
+    phat = rng.standard_normal((pb.Nt, op.Ns))
+    g = op.gradient(x, phat)
+    for _ in range(3):
+        v = rng.standard_normal(pb.shape)
+        eps = np.linalg.norm(x) / np.linalg.norm(v)
+        fd = (op.data_misfit(x + eps * v, phat) - op.data_misfit(x - eps * v, phat)) / (2 * eps)
+        assert abs(fd - np.sum(g * v)) <= 1e-9 * abs(fd) + 1e-12
+
+
+def test_absorption_decay_and_dispersion():
+    # A single plane mode on a homogeneous periodic grid without PML: the pressure coefficient
+    # follows a two-term recurrence (state = (rho, u)), so a least-squares fit of
+    # P_{n+1} = a1 P_n + a2 P_{n-1} recovers the damping exactly. Physical law (Sec. II.A):
+    # spatial attenuation alpha0 f_MHz^y dB/cm, temporal decay ~ c * attenuation.
+    nx, ny = 64, 4
+    h = 0.1e-3
+    c = 1500.0
+    y = 1.5
+    a0 = 5.0
+    dt = 0.3 * h / c
+    m = 4
+    k0 = 2 * np.pi * m / (nx * h)
+    Nt = 400
+    op = Operator((ny, nx), (h, h), (0, 0), 2.0, c, 1000.0, a0, y, dt, Nt,
+                  sensor_index=np.arange(nx * ny))
+    x = (np.arange(nx) - nx // 2) * h
+    p0 = np.broadcast_to(np.cos(k0 * x), (ny, nx))
+    data = op.forward(p0).reshape(Nt, ny, nx)
+    P = np.array([np.fft.rfft(d[0])[m] for d in data]).real
+    # P^0 = p0 is imposed (not produced by the recurrence from rho^0, u^(-1/2)): fit from n = 1
+    A = np.stack([P[2:-1], P[1:-2]], axis=1)
+    coef, *_ = np.linalg.lstsq(A, P[3:], rcond=None)
+    assert np.max(np.abs(A @ coef - P[3:])) < 1e-10
+    r = np.sqrt(-coef[1])
+    gamma = -np.log(r) / dt
+    omega = np.arccos(coef[0] / (2 * r)) / dt
+    f_mhz = c * k0 / (2 * np.pi) / 1e6
+    atten_np_per_m = a0 * f_mhz**y * 100.0 / (20 * np.log10(np.e))
+    gamma_ref = c * atten_np_per_m
+    assert abs(gamma / gamma_ref - 1) < 0.02
+    # dispersion: y = 1.5 gives eta < 0, so the mode runs faster than c (sound speed rises with
+    # frequency) by the (1 - eta k^(y-1)) factor of Eq. (state)
+    assert omega > c * k0
+    assert np.max(np.abs(P[-50:])) < 0.7 * np.max(np.abs(P[:50]))
+
+
+def test_sensor_interpolation():
+    shape = (10, 12)
+    h = (1e-4, 1e-4)
+    # exactly on a node: weight 1 on that node
+    pos = np.array([[(7 - 6) * 1e-4, (3 - 5) * 1e-4]])
+    M = sensor_matrix(shape, h, pos=pos)
+    assert M.nnz == 1 and M[0, 3 * 12 + 7] == 1.0
+    # linear fields are reproduced exactly by the multilinear weights
+    rng = np.random.default_rng(6)
+    pos = rng.uniform(-3e-4, 3e-4, size=(20, 2))
+    M = sensor_matrix(shape, h, pos=pos)
+    yy, xx = np.meshgrid((np.arange(10) - 5) * 1e-4, (np.arange(12) - 6) * 1e-4, indexing="ij")
+    f = 2.0 + 3.0 * xx / 1e-4 - 1.5 * yy / 1e-4
+    ref = 2.0 + 3.0 * pos[:, 0] / 1e-4 - 1.5 * pos[:, 1] / 1e-4
+    assert np.max(np.abs(M @ f.ravel() - ref)) < 1e-10
+    assert np.allclose(np.asarray(M.sum(axis=1)).ravel(), 1.0)
+    with pytest.raises(ValueError):
+        sensor_matrix(shape, h, pos=np.array([[1.0, 0.0]]))
+
+
+def test_pml_damps_outgoing_energy():
+    # With the PML on, an outgoing pulse loses almost all of its energy after crossing the
+    # boundary, while without it the periodic grid keeps it.
+    shape = (48, 48)
+    h = 1e-4
+    c = 1500.0
+    dt = 0.3 * h / c
+    Nt = 300
+    p0 = synth.discs(np.random.default_rng(7), shape, (h, h), 1, 1e-4, (3e-4, 3e-4), (1.0, 1.0))
+    idx = np.arange(48 * 48)
+    with_pml = Operator(shape, (h, h), (8, 8), 2.0, c, 1000.0, 0.0, 1.5, dt, Nt, sensor_index=idx)
+    no_pml = Operator(shape, (h, h), (0, 0), 2.0, c, 1000.0, 0.0, 1.5, dt, Nt, sensor_index=idx)
+    e_pml = np.sum(with_pml.forward(p0)[-1] ** 2)
+    e_per = np.sum(no_pml.forward(p0)[-1] ** 2)
+    assert e_pml < 1e-2 * e_per

@@ -1,0 +1,233 @@
+"""Pins of the FP64 oracle's optimisation shell (TV, FGP prox, grid transfer, constraint
+restriction, ISTA / FISTA / MG-FISTA, power method) against what the mathematics fixes."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+from oracle import pat_optim as po
+from oracle.pat_oracle import Operator
+from paper_1603_02329_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_tv_difference_operator_transpose():
+    rng = np.random.default_rng(0)
+    for shape in [(5, 7), (3, 4, 6)]:
+        x = rng.standard_normal(shape)
+        q = [rng.standard_normal(shape) for _ in shape]
+        lhs = sum(np.sum(g * qa) for g, qa in zip(po.grad_fwd(x), q))
+        rhs = np.sum(x * po.grad_fwd_T(q))
+        assert abs(lhs - rhs) < 1e-12 * (1 + abs(lhs))
+    # D of a constant is zero; TV of a step edge of height s across a full column is s * rows
+    assert po.tv(np.full((4, 5), 3.0)) == 0.0
+    img = np.zeros((4, 6))
+    img[:, 3:] = 2.0
+    assert abs(po.tv(img) - 2.0 * 4) < 1e-14
+
+
+def test_tv_prox_special_cases():
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal((6, 7))
+    # lam' = 0 reduces to the projection on x >= 0
+    assert np.array_equal(po.tv_prox(z, 0.0, 20), np.maximum(z, 0.0))
+    # a constant non-negative image is a fixed point for every lam'
+    cst = np.full((5, 6), 0.7)
+    assert np.max(np.abs(po.tv_prox(cst, 0.3, 20) - cst)) < 1e-14
+    # without the constraint, the prox keeps the mean (D^T q sums to zero)
+    x = po.tv_prox(z, 0.2, 50, nonneg=False)
+    assert abs(x.mean() - z.mean()) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (3, 3, 3)])
+def test_tv_prox_matches_direct_minimisation(shape):
+    # FGP after many inner iterations: (i) the duality gap certificate -> 0, (ii) agreement with
+    # a generic bound-constrained minimiser on a finely smoothed copy of the same objective.
+    rng = np.random.default_rng(2)
+    z = rng.standard_normal(shape) + 0.5
+    lam = 0.15
+    x, q = po.tv_prox(z, lam, 3000, nonneg=True, return_dual=True)
+    gap = po.tv_prox_gap(z, lam, x, q)
+    assert -1e-12 < gap < 1e-7
+
+    eps = 1e-9
+
+    def obj(v):
+        v = v.reshape(shape)
+        g = po.grad_fwd(v)
+        nrm = np.sqrt(sum(ga * ga for ga in g) + eps * eps)
+        val = 0.5 * np.sum((v - z) ** 2) + lam * np.sum(nrm)
+        grad = (v - z) + lam * po.grad_fwd_T([ga / nrm for ga in g])
+        return val, grad.ravel()
+
+    res = minimize(obj, np.maximum(z, 0).ravel(), jac=True, method="L-BFGS-B",
+                   bounds=[(0, None)] * z.size, options={"maxiter": 20000, "ftol": 1e-15, "gtol": 1e-12})
+    assert np.max(np.abs(res.x.reshape(shape) - x)) < 5e-4
+    f_fgp = 0.5 * np.sum((x - z) ** 2) + lam * po.tv(x)
+    f_ref = 0.5 * np.sum((res.x.reshape(shape) - z) ** 2) + lam * po.tv(res.x.reshape(shape))
+    assert f_fgp <= f_ref + 1e-8
+
+
+def test_tv_prox_gap_detects_a_wrong_transpose():
+    # the certificate is not vacuous: with D^T replaced by -D^T the iteration does not converge
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal((4, 4))
+    lam = 0.2
+    x, q = po.tv_prox(z, lam, 500, return_dual=True)
+    assert po.tv_prox_gap(z, lam, x, q) < 1e-6
+    bad_x = np.maximum(z + lam * po.grad_fwd_T(q), 0)
+    assert po.tv_prox_gap(z, lam, bad_x, q) > 1e-3
+
+
+def test_smoothed_tv_gradient_and_limit():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((6, 5))
+    rho = 0.05
+    g = po.tv_smooth_grad(x, rho)
+    v = rng.standard_normal(x.shape)
+    e = 1e-6
+    fd = (po.tv_smooth(x + e * v, rho) - po.tv_smooth(x - e * v, rho)) / (2 * e)
+    assert abs(fd - np.sum(g * v)) < 1e-6 * (1 + abs(fd))
+    assert abs(po.tv_smooth(x, 1e-12) - po.tv(x)) < 1e-9
+    assert po.tv_smooth(np.ones((3, 3)), 0.1) == 0.0
+
+
+def test_transfer_operators():
+    rng = np.random.default_rng(5)
+    for shape_c in [(5, 6), (3, 4, 5)]:
+        d = len(shape_c)
+        shape_f = tuple(2 * n for n in shape_c)
+        xc = rng.standard_normal(shape_c)
+        xf = rng.standard_normal(shape_f)
+        # R = 2^-d P^T
+        lhs = np.sum(po.restrict(xf) * xc)
+        rhs = np.sum(xf * po.prolong(xc)) / 2**d
+        assert abs(lhs - rhs) < 1e-12 * (1 + abs(lhs))
+        # P reproduces constants and (away from the clamped last index) linear functions
+        assert np.allclose(po.prolong(np.ones(shape_c)), 1.0)
+        grids = np.meshgrid(*[np.arange(n, dtype=float) for n in shape_c], indexing="ij")
+        lin = sum((a + 1.0) * g for a, g in enumerate(grids))
+        pf = po.prolong(lin)
+        gf = np.meshgrid(*[np.arange(n, dtype=float) / 2 for n in shape_f], indexing="ij")
+        ref = sum((a + 1.0) * g for a, g in enumerate(gf))
+        inner = tuple(slice(0, n - 1) for n in shape_f)
+        assert np.max(np.abs(pf[inner] - ref[inner])) < 1e-12
+        # full weighting keeps constants away from the boundary
+        rc = po.restrict(np.ones(shape_f))
+        inner_c = tuple(slice(1, n - 1) for n in shape_c)
+        assert np.allclose(rc[inner_c], 1.0)
+
+
+def test_coarse_bound_keeps_feasibility():
+    # x = y + P(x_c - R y) >= 0 whenever x_c >= phi = R y - min_nbr(y)   (Sec. V.C)
+    rng = np.random.default_rng(6)
+    for shape in [(8, 10), (6, 4, 8)]:
+        for _ in range(20):
+            y = rng.standard_normal(shape)
+            phi = po.coarse_lower_bound(y)
+            xc = phi + np.abs(rng.standard_normal(phi.shape)) * rng.integers(0, 2, phi.shape)
+            x = y + po.prolong(xc - po.restrict(y))
+            assert x.min() >= -1e-12
+        # and the bound is tight somewhere: at x_c = phi some fine value touches zero
+        x = y + po.prolong(phi - po.restrict(y))
+        assert x.min() >= -1e-12 and x.min() < 1e-12
+
+
+def _tiny_problem():
+    pb = synth.small_lossy_2d(shape=(16, 16), pml=3, Nt=24, n_sensors=10, sensor_radius_frac=0.3)
+    return pb, Operator.from_problem(pb)
+
+
+def test_power_iteration_matches_dense_eigenvalue():
+    # Dense H (N forward solves) on a tiny grid: the power method's estimate lies below the
+    # largest eigenvalue of H^T H and within the textbook convergence bound of it.
+    pb, op = _tiny_problem()
+    N = pb.N
+    cols = [op.forward(np.eye(N)[i].reshape(pb.shape)).ravel() for i in range(N)]
+    H = np.stack(cols, axis=1)
+    w, V = np.linalg.eigh(H.T @ H)
+    lmax, l2 = w[-1], w[-2]
+    n_iter = 300
+    L = po.power_iteration(lambda v: op.adjoint(op.forward(v)), pb.shape, n_iter=n_iter, seed=1)
+    v0 = np.random.default_rng(1).standard_normal(pb.shape).ravel()
+    c1 = abs(V[:, -1] @ v0) / np.linalg.norm(v0)
+    # ||A^n v|| / ||A^(n-1) v|| >= lmax (1 - tan^2(angle) (l2/lmax)^(2n-2))
+    bound = (1 - c1**2) / c1**2 * (l2 / lmax) ** (2 * n_iter - 2)
+    assert L <= lmax * (1 + 1e-12)
+    assert (lmax - L) / lmax <= bound + 1e-12
+    assert abs(L / lmax - 1) < 1e-4
+
+
+def _mg_setup():
+    pb = synth.small_lossy_2d(shape=(32, 32), pml=4, Nt=40, n_sensors=24, sensor_radius_frac=0.3)
+    op = Operator.from_problem(pb)
+    phat = op.forward(pb.p0)
+    L = po.power_iteration(lambda v: op.adjoint(op.forward(v)), pb.shape, n_iter=15, seed=1)
+    op_c, Nt_c = po.coarse_operator(pb)
+    Lc = po.power_iteration(lambda v: op_c.adjoint(op_c.forward(v)), op_c.shape, n_iter=15, seed=2)
+    return pb, op, phat, L, (op_c, phat[::2][:Nt_c], Lc)
+
+
+def test_fista_theta_zero_is_ista_and_no_recursion_is_fista():
+    pb, op, phat, L, coarse = _mg_setup()
+    x0 = np.zeros(pb.shape)
+    o_ista = po.FistaOpts(variant=0, step_scale=2.0, max_iter=3, eps_d=-1.0)
+    xa, ra = po.mg_fista(op, phat, x0, L, o_ista, coarse=None, p_exact=pb.p0)
+    # Alg. 1 written out directly
+    x = x0.copy()
+    for _ in range(3):
+        g = op.adjoint(op.forward(x) - phat)
+        x = po.tv_prox(x - (2.0 / L) * g, (2.0 / L) * o_ista.lam, o_ista.n_tv)
+    assert np.max(np.abs(xa - x)) < 1e-12 * (1 + np.abs(x).max())
+    # recursion disabled == plain FISTA, whatever the coarse level
+    o_f = po.FistaOpts(variant=1, max_iter=4, eps_d=-1.0)
+    x1, r1 = po.mg_fista(op, phat, x0, L, o_f, coarse=None)
+    o_nr = po.FistaOpts(variant=1, max_iter=4, eps_d=-1.0, recursion=False)
+    x2, r2 = po.mg_fista(op, phat, x0, L, o_nr, coarse=coarse)
+    assert np.array_equal(x1, x2)
+    assert all(r.branch == "direct" for r in r2)
+
+
+def test_first_order_coherence():
+    # grad phi_{h-1}(x_{h-1,0}) = R grad F_h(y)   (Sec. V.A, Eqs. (fourteen)-(Fourteen))
+    pb, op, phat, L, (op_c, phat_c, Lc) = _mg_setup()
+    rng = np.random.default_rng(7)
+    y = np.abs(rng.standard_normal(pb.shape))
+    lam, rho = 1e-2, 1e-2
+    gF = op.adjoint(op.forward(y) - phat) + lam * po.tv_smooth_grad(y, rho)
+    xc0 = po.restrict(y)
+    gFc = op_c.adjoint(op_c.forward(xc0) - phat_c) + lam * po.tv_smooth_grad(xc0, rho)
+    v = po.restrict(gF) - gFc
+    gphi = op_c.adjoint(op_c.forward(xc0) - phat_c) + lam * po.tv_smooth_grad(xc0, rho) + v
+    assert np.max(np.abs(gphi - po.restrict(gF))) < 1e-12 * np.abs(gF).max()
+
+
+def test_mg_fista_runs_recursive_branch_and_stays_feasible():
+    pb, op, phat, L, coarse = _mg_setup()
+    opts = po.FistaOpts(variant=1, max_iter=6, eps_d=-1.0, kappa=0.25)
+    xs = []
+    x, recs = po.mg_fista(op, phat, np.zeros(pb.shape), L, opts, coarse=coarse, p_exact=pb.p0,
+                          callback=lambda r: xs.append(r))
+    assert recs[0].branch == "direct"
+    assert any(r.branch == "recursive" for r in recs)
+    assert x.min() >= -1e-12   # x = y + P(x_c - R y) >= 0 holds up to rounding
+    # the objective comes down from F(x0)
+    F0 = 0.5 * np.sum(phat**2)
+    assert recs[-1].F < 0.5 * F0
+
+
+def test_paper_parameters_golden():
+    # The algorithm parameters printed in Sec. VI.A / VI.B are the FistaOpts defaults (2-D).
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    o = po.FistaOpts()
+    assert o.lam == g["lambda"]["value"]
+    assert o.kappa == g["kappa_2d"]["value"]
+    assert o.vartheta == g["vartheta"]["value"]
+    assert o.q_d == g["q_d"]["value"] and o.q_c == g["q_c"]["value"]
+    assert o.eps_d == g["eps_d"]["value"] and o.eps_c == g["eps_c"]["value"]
+    assert o.tv_rho == g["rho_tv_2d"]["value"]

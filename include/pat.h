@@ -1,0 +1,142 @@
+/*
+ * pat.h -- C ABI of the GB300 (sm_103a) photoacoustic forward/adjoint library.
+ *
+ * Method: Javaherian & Holman, "A Multi-Grid Iterative Method for Photoacoustic Tomography",
+ * arXiv:1603.02329.  The library evaluates the discrete forward operator H = M w P of Sec. III
+ * (k-space pseudospectral time stepping of the first-order acoustic system of Sec. II.A,
+ * Eqs. (mom), (mass), (state), (Twelve), with a split-field PML, Sec. VI.A) and its exact
+ * transpose H^T (the discrete counterpart of the analytic adjoint of Sec. III, Eqs. (moma),
+ * (massa), (statea), (adjj)).  Every step of both solves runs in this library's own CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Fields are dense, row-major, x fastest: index (z * Ny + y) * Nx + x.  n[0] = Nx, n[1] = Ny,
+ *    n[2] = Nz (Nz = 1 and n[2] ignored for ndim = 2).  Physical coordinates are grid-centred:
+ *    x_i = (i - n/2) * dx.
+ *  - Data (sensor time series) are [Nt][Ns], one row per time sample t = 0, dt, ..., (Nt-1) dt.
+ *  - The element type of every field/data pointer is the plan's precision: float for PAT_F32,
+ *    double for PAT_F64.  Medium arrays passed to pat_plan_create are always double.
+ *  - Field/data pointers may be host (pageable or pinned) or device pointers; the library copies
+ *    them into its own device workspaces with cudaMemcpyAsync(cudaMemcpyDefault) on `stream`.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls enqueue work and
+ *    return without synchronising, except where a host pointer forces the copy to complete.
+ *  - Ownership: the caller owns every pointer it passes; the library never frees them.  A plan
+ *    owns its device workspaces, its CUDA graphs and its tables until pat_plan_destroy.
+ *  - Two calls on the same plan must not run concurrently (they share the plan's workspaces).
+ *  - Errors: every call returns a pat_status; nothing aborts, traps or exits.  pat_last_error()
+ *    returns a message for the calling thread's last failure.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PAT_OK = 0,
+    PAT_EINVAL = 1,        /* bad argument: null pointer, bad size, sensor outside the grid, ... */
+    PAT_ECUDA = 2,         /* a CUDA runtime call failed (message has the CUDA error string)      */
+    PAT_ENOMEM = 3,        /* device allocation failed                                           */
+    PAT_ENONFINITE = 4,    /* a result contains NaN or Inf                                        */
+    PAT_ETIMEOUT = 5,      /* reserved for bounded device-side waits                              */
+    PAT_EUNSUPPORTED = 6   /* valid but unsupported request (e.g. an FFT length with a prime > 7) */
+} pat_status;
+
+typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_precision;
+
+/* Computational grid.  Every n[i] must be even and factor into 2, 3, 5, 7 (the FFT radices).
+ * The PML occupies the outer pml[i] points of each axis (inside the grid); its absorption
+ * rises as (depth / pml)^4 to pml_alpha nepers per grid point at the edge (Sec. VI.A uses
+ * 20 points and 2 Np per point). */
+typedef struct {
+    int ndim;          /* 2 or 3 */
+    int n[3];          /* points per axis: x, y, z */
+    double dx[3];      /* spacing per axis [m] */
+    int pml[3];        /* PML thickness per axis [points]; 0 = no PML on that axis */
+    double pml_alpha;  /* maximum PML absorption [Np per grid point] */
+} pat_grid;
+
+/* Point sensors (Sec. III: M w restricts p to the sensors; Sec. VI.A: linear interpolation).
+ * Exactly one of pos / index is non-NULL.
+ *   pos   [count][ndim] physical positions (x, y[, z]) [m], grid-centred; multilinear weights.
+ *   index [count] flat field indices of on-grid sensors (weight 1). */
+typedef struct {
+    int count;
+    const double* pos;
+    const int64_t* index;
+} pat_sensors;
+
+typedef struct pat_plan pat_plan;
+
+/* Sizes of a plan, for callers that allocate inputs and outputs. */
+typedef struct {
+    int ndim;
+    int n[3];
+    int64_t N;          /* grid points */
+    int Ns;             /* sensors */
+    int Nt;             /* time samples */
+    int lossy;          /* 1 if any alpha0 != 0 (absorption/dispersion terms active) */
+    pat_precision precision;
+    double dt;
+    double c_ref;       /* max sound speed (kappa correction, PML scaling) */
+} pat_plan_info_t;
+
+/* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).
+ *   c, rho   [N] host doubles: sound speed [m/s] and ambient density [kg/m^3].
+ *   alpha0   [N] host doubles (or one value if alpha0_is_scalar): power-law absorption
+ *            coefficient in dB MHz^-y cm^-1 (Sec. II.A); all zeros = lossless.
+ *   y        power-law exponent (Sec. II.A), y != 1.
+ *   sensors  sensor geometry (see pat_sensors).
+ *   dt, Nt   time step [s] and number of recorded samples (t = 0 .. (Nt-1) dt), Nt >= 1.
+ *   prec     arithmetic precision of the fields (PAT_F32: FP32 stepping; PAT_F64: FP64).
+ * Derived per-point quantities (c0^2, 1/rho0 on the staggered grids, tau and eta of
+ * Eq. (Twelve), PML factors, k-space tables, interpolation weights) are computed here in FP64
+ * on the host and stored on the current device in the plan's precision.
+ * Errors: PAT_EINVAL (bad sizes, NULLs, y = 1, sensor outside grid), PAT_EUNSUPPORTED (FFT
+ * length not 2^a 3^b 5^c 7^d, or odd), PAT_ENOMEM, PAT_ECUDA. */
+pat_status pat_plan_create(const pat_grid* grid, const double* c, const double* rho,
+                           const double* alpha0, int alpha0_is_scalar, double y,
+                           const pat_sensors* sensors, double dt, int Nt, pat_precision prec,
+                           pat_plan** out);
+
+/* pat_plan_destroy -- free a plan and everything it owns (NULL is a no-op).  Synchronises the
+ * device work the plan enqueued. */
+pat_status pat_plan_destroy(pat_plan* plan);
+
+/* pat_plan_get_info -- sizes of a plan. */
+pat_status pat_plan_get_info(const pat_plan* plan, pat_plan_info_t* info);
+
+/* pat_forward_plan -- data = H p0 (Sec. III: H[p0] = M w p; forward model of Sec. II.A).
+ *   p0    [N]      initial pressure (host or device, plan precision).
+ *   data  [Nt][Ns] output, overwritten (host or device, plan precision).
+ * Runs the whole Nt-step solve as one CUDA-graph launch on `stream`. */
+pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* stream);
+
+/* pat_adjoint -- grad = H^T residual (Sec. III, Eq. (adjj); Sec. IV, Eq. (Six) uses it as
+ * grad f = H^T (H x - p_hat)).  The transpose is exact: <H x, h> = <x, H^T h> to rounding.
+ *   residual [Nt][Ns] input (host or device, plan precision).
+ *   grad     [N]      output, overwritten (host or device, plan precision). */
+pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* stream);
+
+/* pat_forward -- one-shot form of the forward operator following the paper's statement of the
+ * problem (Sec. II.B, Sec. III): builds a plan from (c, rho, alpha0, y, grid, sensor_mask, dt,
+ * Nt), runs pat_forward_plan, synchronises `stream` and frees the plan.  For repeated solves
+ * create a plan once instead. */
+pat_status pat_forward(const void* p0, const double* c, const double* rho, const double* alpha0,
+                       int alpha0_is_scalar, double y, const pat_grid* grid,
+                       const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
+                       void* data, void* stream);
+
+/* pat_last_error -- message describing the calling thread's last failed call ("" if none).
+ * The pointer stays valid until the next pat_* call on the same thread. */
+const char* pat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAT_H */

@@ -1,0 +1,78 @@
+"""ctypes declarations of the C ABI in ``include/pat.h`` (argument marshalling only).
+
+The shared library ``libpat_gb300.so`` must have been built (``build.build()``); importing
+this module raises if it is missing, so nothing silently falls back to another code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PAT_OK, PAT_EINVAL, PAT_ECUDA, PAT_ENOMEM, PAT_ENONFINITE, PAT_ETIMEOUT, PAT_EUNSUPPORTED = range(7)
+PAT_F32, PAT_F64 = 0, 1
+STATUS_NAMES = {0: "PAT_OK", 1: "PAT_EINVAL", 2: "PAT_ECUDA", 3: "PAT_ENOMEM", 4: "PAT_ENONFINITE",
+                5: "PAT_ETIMEOUT", 6: "PAT_EUNSUPPORTED"}
+
+
+class pat_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("pml", ctypes.c_int * 3), ("pml_alpha", ctypes.c_double)]
+
+
+class pat_sensors(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("pos", ctypes.POINTER(ctypes.c_double)),
+                ("index", ctypes.POINTER(ctypes.c_int64))]
+
+
+class pat_plan_info_t(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("N", ctypes.c_int64), ("Ns", ctypes.c_int),
+                ("Nt", ctypes.c_int), ("lossy", ctypes.c_int), ("precision", ctypes.c_int),
+                ("dt", ctypes.c_double), ("c_ref", ctypes.c_double)]
+
+
+class PatError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_1603_02329_gb300.build.build() (needs nvcc)")
+    L = ctypes.CDLL(path)
+    vp, i32, f64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    plan_pp = ctypes.POINTER(ctypes.c_void_p)
+    L.pat_plan_create.argtypes = [ctypes.POINTER(pat_grid), dp, dp, dp, i32, f64, ctypes.POINTER(pat_sensors), f64, i32,
+                                  i32, plan_pp]
+    L.pat_plan_create.restype = i32
+    L.pat_plan_destroy.argtypes = [vp]
+    L.pat_plan_destroy.restype = i32
+    L.pat_plan_get_info.argtypes = [vp, ctypes.POINTER(pat_plan_info_t)]
+    L.pat_plan_get_info.restype = i32
+    L.pat_forward_plan.argtypes = [vp, vp, vp, vp]
+    L.pat_forward_plan.restype = i32
+    L.pat_adjoint.argtypes = [vp, vp, vp, vp]
+    L.pat_adjoint.restype = i32
+    L.pat_forward.argtypes = [vp, dp, dp, dp, i32, f64, ctypes.POINTER(pat_grid), ctypes.POINTER(pat_sensors), f64, i32,
+                              i32, vp, vp]
+    L.pat_forward.restype = i32
+    L.pat_last_error.argtypes = []
+    L.pat_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != PAT_OK:
+        msg = lib().pat_last_error().decode(errors="replace")
+        raise PatError(status, msg)

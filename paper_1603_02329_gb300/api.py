@@ -1,0 +1,172 @@
+"""Python binding of the C ABI: argument marshalling around ``libpat_gb300.so``.
+
+PyTorch provides device memory and streams; every step of the forward operator H and its
+transpose H^T (Sec. III of Javaherian & Holman, arXiv:1603.02329) runs in the library's own
+CUDA kernels.  Names follow the C calls of ``include/pat.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PAT_F32, PAT_F64, check, lib
+
+_DTYPES = {PAT_F32: torch.float32, PAT_F64: torch.float64}
+
+
+def _as_f64(a, N, name):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    if arr.size not in (1, N):
+        raise ValueError(f"{name} must have 1 or {N} values, got {arr.size}")
+    return arr
+
+
+def make_grid(shape, spacing, pml, pml_alpha=2.0) -> _lib.pat_grid:
+    """numpy-order shape/spacing/pml ((Ny, Nx) or (Nz, Ny, Nx)) -> pat_grid (x first)."""
+    d = len(shape)
+    g = _lib.pat_grid()
+    g.ndim = d
+    for a in range(3):
+        g.n[a] = int(shape[d - 1 - a]) if a < d else 1
+        g.dx[a] = float(spacing[d - 1 - a]) if a < d else 1.0
+        g.pml[a] = int(pml[d - 1 - a]) if a < d else 0
+    g.pml_alpha = float(pml_alpha)
+    return g
+
+
+def _stream_ptr(stream, device):
+    if stream is None:
+        if device is None or device.type != "cuda":
+            return None
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class PATOperator:
+    """Plan of the forward operator H and its exact transpose (``pat_plan_*`` calls).
+
+    Fields are numpy-ordered (``shape`` = (Ny, Nx) or (Nz, Ny, Nx)); data are [Nt][Ns].
+    ``forward`` / ``adjoint`` accept CUDA or CPU tensors of the plan's dtype and return a tensor
+    on the same device (CPU tensors go through the library's host-pointer path)."""
+
+    def __init__(self, shape, spacing, pml, pml_alpha, c, rho, alpha0, y, dt, Nt,
+                 sensor_pos=None, sensor_index=None, precision="f32", device=None):
+        self.shape = tuple(int(n) for n in shape)
+        self.N = int(np.prod(self.shape))
+        self.Nt = int(Nt)
+        self.prec = PAT_F64 if precision in ("f64", "float64", torch.float64, PAT_F64) else PAT_F32
+        self.dtype = _DTYPES[self.prec]
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._grid = make_grid(self.shape, spacing, pml, pml_alpha)
+        self._c = _as_f64(c, self.N, "c")
+        self._rho = _as_f64(rho, self.N, "rho")
+        if self._c.size == 1:
+            self._c = np.full(self.N, self._c[0])
+        if self._rho.size == 1:
+            self._rho = np.full(self.N, self._rho[0])
+        self._a0 = _as_f64(alpha0, self.N, "alpha0")
+        sens = _lib.pat_sensors()
+        if sensor_index is not None:
+            self._sidx = np.ascontiguousarray(np.asarray(sensor_index, dtype=np.int64).reshape(-1))
+            sens.count = int(self._sidx.size)
+            sens.index = self._sidx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            sens.pos = None
+        else:
+            self._spos = np.ascontiguousarray(np.asarray(sensor_pos, dtype=np.float64))
+            sens.count = int(self._spos.shape[0])
+            sens.pos = self._spos.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            sens.index = None
+        self.Ns = sens.count
+        self._plan = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
+        with torch.cuda.device(self.device):
+            check(lib().pat_plan_create(ctypes.byref(self._grid), self._c.ctypes.data_as(dp),
+                                        self._rho.ctypes.data_as(dp), self._a0.ctypes.data_as(dp),
+                                        int(self._a0.size == 1), float(y), ctypes.byref(sens), float(dt),
+                                        self.Nt, self.prec, ctypes.byref(self._plan)))
+        info = _lib.pat_plan_info_t()
+        check(lib().pat_plan_get_info(self._plan, ctypes.byref(info)))
+        self.info = info
+        self.lossy = bool(info.lossy)
+
+    @classmethod
+    def from_problem(cls, pb, precision="f32", Nt=None, device=None):
+        return cls(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, pb.c, pb.rho, pb.alpha0, pb.y, pb.dt,
+                   pb.Nt if Nt is None else Nt, sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index,
+                   precision=precision, device=device)
+
+    # -- calls ---------------------------------------------------------------------------------
+    def _check_in(self, t, n, name):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
+        if t.numel() != n:
+            raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    def forward(self, p0: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """pat_forward_plan: data[Nt][Ns] = H p0."""
+        self._check_in(p0, self.N, "p0")
+        if out is None:
+            out = torch.empty((self.Nt, self.Ns), dtype=self.dtype, device=p0.device)
+        self._check_in(out, self.Nt * self.Ns, "out")
+        with torch.cuda.device(self.device):
+            check(lib().pat_forward_plan(self._plan, ctypes.c_void_p(p0.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         _stream_ptr(stream, self.device)))
+        return out
+
+    def adjoint(self, residual: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """pat_adjoint: grad = H^T residual, shaped like the grid."""
+        self._check_in(residual, self.Nt * self.Ns, "residual")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=residual.device)
+        self._check_in(out, self.N, "out")
+        with torch.cuda.device(self.device):
+            check(lib().pat_adjoint(self._plan, ctypes.c_void_p(residual.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream, self.device)))
+        return out
+
+    def close(self):
+        if getattr(self, "_plan", None) is not None and self._plan.value:
+            lib().pat_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pat_forward(p0: torch.Tensor, c, rho, alpha0, y, shape, spacing, pml, pml_alpha, sensor_pos=None,
+                sensor_index=None, dt=None, Nt=None, precision="f32", stream=None) -> torch.Tensor:
+    """One-shot ``pat_forward`` (builds and frees a plan inside the library)."""
+    prec = PAT_F64 if precision in ("f64", "float64", torch.float64) else PAT_F32
+    dtype = _DTYPES[prec]
+    if p0.dtype != dtype or not p0.is_contiguous():
+        raise TypeError("p0 must be a contiguous tensor of the requested precision")
+    N = int(np.prod(shape))
+    grid = make_grid(shape, spacing, pml, pml_alpha)
+    cc = np.ascontiguousarray(np.broadcast_to(np.asarray(c, np.float64), (N,)) if np.size(c) == 1 else np.asarray(c, np.float64).reshape(-1))
+    rr = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, np.float64), (N,)) if np.size(rho) == 1 else np.asarray(rho, np.float64).reshape(-1))
+    aa = np.ascontiguousarray(np.asarray(alpha0, np.float64).reshape(-1))
+    sens = _lib.pat_sensors()
+    if sensor_index is not None:
+        sidx = np.ascontiguousarray(np.asarray(sensor_index, np.int64).reshape(-1))
+        sens.count, sens.index, sens.pos = int(sidx.size), sidx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None
+    else:
+        spos = np.ascontiguousarray(np.asarray(sensor_pos, np.float64))
+        sens.count, sens.pos, sens.index = int(spos.shape[0]), spos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None
+    out = torch.empty((int(Nt), sens.count), dtype=dtype, device=p0.device)
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib().pat_forward(ctypes.c_void_p(p0.data_ptr()), cc.ctypes.data_as(dp), rr.ctypes.data_as(dp),
+                            aa.ctypes.data_as(dp), int(aa.size == 1), float(y), ctypes.byref(grid), ctypes.byref(sens),
+                            float(dt), int(Nt), prec, ctypes.c_void_p(out.data_ptr()),
+                            _stream_ptr(stream, p0.device)))
+    return out

@@ -1,0 +1,36 @@
+// pat_host.h -- FP64 host tables of a plan (computed once, then rounded to the plan precision).
+#pragma once
+
+#include <complex>
+#include <vector>
+
+#include "pat_internal.cuh"
+
+namespace pat {
+
+struct HostTables {
+    pat_plan_info_t info;
+    int d = 2, nx = 1, ny = 1, nz = 1, nxh = 1, ldh = 1;
+    long long N = 0;
+    int Ns = 0, Nt = 0, lossy = 0;
+    double dt = 0.0, c_ref = 0.0;
+    LaunchCfg cfg{};
+
+    std::vector<double> c2, rho0, b[3], c2tau, c2eta;
+    std::vector<double> a[3], au[3];
+    std::vector<std::complex<double>> dp[3], dm[3], tw[3];
+    std::vector<double> kapN, kpa, kpb;
+    FftAxis fx{}, fy{}, fz{};
+
+    // sensors (see DevSensors)
+    std::vector<int> g_lineptr, g_seg_line, g_seg_sensor, g_seg_e0, g_ent_x;
+    std::vector<double> g_ent_w;
+    std::vector<int> s_lineptr, s_seg_line, s_seg_x, s_seg_e0, s_ent_sensor;
+    std::vector<double> s_ent_w;
+};
+
+PlanBase* make_plan_f32(const HostTables& h, pat_status* st);
+PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
+pat_status plan_capture(PlanBase* base, bool adjoint);
+
+}  // namespace pat

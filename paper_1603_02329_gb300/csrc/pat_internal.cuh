@@ -1,0 +1,159 @@
+// pat_internal.cuh -- types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pat.h"
+
+namespace pat {
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (float2 / double2 storage)
+// ------------------------------------------------------------------------------------------
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 type; };
+template <> struct CT<double> { typedef double2 type; };
+
+template <typename T> using cplx = typename CT<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mkc(T a, T b) {
+    cplx<T> r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+
+// ------------------------------------------------------------------------------------------
+// FFT description of one axis (Stockham autosort, radices 2,3,4,5,7,8)
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxStages = 16;
+struct FftAxis {
+    int n;
+    int nst;
+    int rad[kMaxStages];
+};
+
+// Maximum line length handled by the shared-memory FFT.
+constexpr int kMaxFftLen = 1024;
+
+// ------------------------------------------------------------------------------------------
+// Sensor lists, grouped by grid line (x-line index = z * Ny + y)
+// ------------------------------------------------------------------------------------------
+template <typename T> struct DevSensors {
+    int Ns;
+    // forward gather: segments grouped by (line, sensor); one atomic add per segment
+    const int* g_lineptr;   // [nlines + 1] -> segment range
+    const int* g_seg_line;  // [nseg]
+    const int* g_seg_sensor;
+    const int* g_seg_e0;    // [nseg + 1] -> entry range
+    const int* g_ent_x;     // [nent]
+    const T* g_ent_w;
+    // adjoint scatter: segments grouped by (line, x); entries (sensor, weight)
+    const int* s_lineptr;
+    const int* s_seg_line;
+    const int* s_seg_x;
+    const int* s_seg_e0;
+    const int* s_ent_sensor;
+    const T* s_ent_w;
+};
+
+// ------------------------------------------------------------------------------------------
+// Device-side view of a plan: passed by value to every kernel
+// ------------------------------------------------------------------------------------------
+template <typename T> struct DevPlan {
+    int d;            // 2 or 3
+    int nx, ny, nz;   // nz = 1 in 2-D
+    int nxh;          // nx/2 + 1 (half spectrum along x)
+    int ldh;          // row pitch of half-spectrum arrays (complex elements, >= nxh)
+    int nlines;       // ny * nz x-lines
+    long long N;      // nx * ny * nz
+    int lossy;
+    T dt;
+
+    // medium (N each)
+    const T* c2;
+    const T* rho0;
+    const T* b[3];    // 1/rho0 at r + dx_xi / 2
+    const T* c2tau;   // c0^2 tau  (lossy only)
+    const T* c2eta;   // c0^2 eta  (lossy only)
+    // PML factors per axis: a at normal points, au at staggered points
+    const T* a[3];
+    const T* au[3];
+    // k-space: staggered derivative symbols per axis (i k e^{+-i k dx/2}), scaled kappa and
+    // fractional Laplacian symbols on the half spectrum [nz][ny][nxh] (all include 1/N)
+    const cplx<T>* dp[3];
+    const cplx<T>* dm[3];
+    const T* kapN;
+    const T* kpa;     // |k|^(y-2) / N
+    const T* kpb;     // |k|^(y-1) / N
+    // FFT plans and twiddles exp(-2 pi i m / n) per axis
+    FftAxis fx, fy, fz;
+    const cplx<T>* twx;
+    const cplx<T>* twy;
+    const cplx<T>* twz;
+
+    // state and workspaces (N each unless noted)
+    T* u[3];
+    T* rh[3];
+    T* rsum;          // r = sum rho_xi (forward, lossy)
+    T* pbar;          // adjoint pressure (lossy)
+    cplx<T>* spec[3]; // half-spectrum workspaces [nz][ny][ldh]
+    T* img;           // p0 in / gradient out
+    T* data;          // [Nt][Ns]
+
+    DevSensors<T> sens;
+};
+
+// ------------------------------------------------------------------------------------------
+// Host-side plan
+// ------------------------------------------------------------------------------------------
+struct LaunchCfg {
+    int row_lines;    // x-lines per CTA in row kernels (even)
+    int row_threads;
+    int col_w;        // columns per CTA in strided-axis kernels
+    int col_threads;
+};
+
+struct PlanBase {
+    virtual ~PlanBase() {}
+    pat_plan_info_t info;
+    int device = 0;
+    LaunchCfg cfg;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t fwd_exec = nullptr;
+    cudaGraphExec_t adj_exec = nullptr;
+    std::vector<void*> allocs;   // every device allocation owned by the plan
+    void* img_ptr = nullptr;
+    void* data_ptr = nullptr;
+    size_t elem = 4;
+};
+
+// error reporting (thread-local message)
+void set_error(const std::string& msg);
+pat_status cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace pat
+
+struct pat_plan {
+    pat::PlanBase* impl;
+};

@@ -1,0 +1,298 @@
+// pat_wave.cu -- device plan, launch sequence and CUDA-graph capture of the forward operator H
+// and its exact transpose H^T (Sec. III).  The whole Nt-step loop of one solve is captured once
+// per plan into a CUDA graph and replayed with a single cudaGraphLaunch per call.
+#include <algorithm>
+#include <cstring>
+
+#include "pat_host.h"
+#include "pat_kernels.cuh"
+
+namespace pat {
+
+template <typename T> struct Plan : public PlanBase {
+    DevPlan<T> P{};
+    HostTables H;   // kept for the FP64 tables' sizes and for rebuilding
+    size_t row_smem = 0, spec_smem = 0;
+
+    template <typename U> U* dalloc(size_t count, pat_status* st) {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(U));
+        if (e != cudaSuccess) {
+            *st = (e == cudaErrorMemoryAllocation) ? PAT_ENOMEM : PAT_ECUDA;
+            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            cudaGetLastError();
+            return nullptr;
+        }
+        allocs.push_back(p);
+        return static_cast<U*>(p);
+    }
+    template <typename U, typename V> const U* upload(const std::vector<V>& v, pat_status* st) {
+        U* d = dalloc<U>(v.size(), st);
+        if (!d) return nullptr;
+        std::vector<U> tmp(v.size());
+        for (size_t i = 0; i < v.size(); ++i) tmp[i] = static_cast<U>(v[i]);
+        if (!v.empty()) {
+            cudaError_t e = cudaMemcpy(d, tmp.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                *st = cuda_fail(e, "cudaMemcpy (plan tables)");
+                return nullptr;
+            }
+        }
+        return d;
+    }
+    const cplx<T>* upload_c(const std::vector<std::complex<double>>& v, pat_status* st) {
+        cplx<T>* d = dalloc<cplx<T>>(v.size(), st);
+        if (!d) return nullptr;
+        std::vector<cplx<T>> tmp(v.size());
+        for (size_t i = 0; i < v.size(); ++i) tmp[i] = mkc<T>((T)v[i].real(), (T)v[i].imag());
+        if (!v.empty()) {
+            cudaError_t e = cudaMemcpy(d, tmp.data(), v.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                *st = cuda_fail(e, "cudaMemcpy (plan tables)");
+                return nullptr;
+            }
+        }
+        return d;
+    }
+
+    ~Plan() override {
+        if (cap_stream) cudaStreamSynchronize(cap_stream);
+        cudaDeviceSynchronize();
+        if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
+        if (adj_exec) cudaGraphExecDestroy(adj_exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (void* p : allocs) cudaFree(p);
+    }
+
+    pat_status build(const HostTables& h) {
+        H = h;
+        pat_status st = PAT_OK;
+        elem = sizeof(T);
+        const int D = h.d;
+        P.d = D;
+        P.nx = h.nx;
+        P.ny = h.ny;
+        P.nz = h.nz;
+        P.nxh = h.nxh;
+        P.ldh = h.ldh;
+        P.nlines = h.ny * h.nz;
+        P.N = h.N;
+        P.lossy = h.lossy;
+        P.dt = (T)h.dt;
+        const size_t N = (size_t)h.N;
+        const size_t Nh = (size_t)h.nz * h.ny * h.ldh;
+#define CHK(x) \
+    do {       \
+        if (!(x)) return st; \
+    } while (0)
+        CHK(P.c2 = upload<T>(h.c2, &st));
+        CHK(P.rho0 = upload<T>(h.rho0, &st));
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) CHK(P.b[a] = upload<T>(h.b[a], &st));
+            else P.b[a] = nullptr;
+            CHK(P.a[a] = upload<T>(h.a[a], &st));
+            CHK(P.au[a] = upload<T>(h.au[a], &st));
+            CHK(P.dp[a] = upload_c(h.dp[a], &st));
+            CHK(P.dm[a] = upload_c(h.dm[a], &st));
+        }
+        if (h.lossy) {
+            CHK(P.c2tau = upload<T>(h.c2tau, &st));
+            CHK(P.c2eta = upload<T>(h.c2eta, &st));
+            CHK(P.kpa = upload<T>(h.kpa, &st));
+            CHK(P.kpb = upload<T>(h.kpb, &st));
+        }
+        CHK(P.kapN = upload<T>(h.kapN, &st));
+        P.fx = h.fx;
+        P.fy = h.fy;
+        P.fz = h.fz;
+        CHK(P.twx = upload_c(h.tw[0], &st));
+        CHK(P.twy = upload_c(h.tw[1], &st));
+        CHK(P.twz = upload_c(h.tw[2], &st));
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) {
+                CHK(P.u[a] = dalloc<T>(N, &st));
+                CHK(P.rh[a] = dalloc<T>(N, &st));
+            } else {
+                P.u[a] = nullptr;
+                P.rh[a] = nullptr;
+            }
+        }
+        if (h.lossy) {
+            CHK(P.rsum = dalloc<T>(N, &st));
+            CHK(P.pbar = dalloc<T>(N, &st));
+        }
+        const int nspec = std::max(D, 2);
+        for (int a = 0; a < 3; ++a) {
+            if (a < nspec) CHK(P.spec[a] = dalloc<cplx<T>>(Nh, &st));
+            else P.spec[a] = nullptr;
+        }
+        CHK(P.img = dalloc<T>(N, &st));
+        CHK(P.data = dalloc<T>((size_t)h.Nt * h.Ns, &st));
+        img_ptr = P.img;
+        data_ptr = P.data;
+        // sensors
+        DevSensors<T>& S = P.sens;
+        S.Ns = h.Ns;
+        CHK(S.g_lineptr = upload<int>(h.g_lineptr, &st));
+        CHK(S.g_seg_line = upload<int>(h.g_seg_line, &st));
+        CHK(S.g_seg_sensor = upload<int>(h.g_seg_sensor, &st));
+        CHK(S.g_seg_e0 = upload<int>(h.g_seg_e0, &st));
+        CHK(S.g_ent_x = upload<int>(h.g_ent_x, &st));
+        CHK(S.g_ent_w = upload<T>(h.g_ent_w, &st));
+        CHK(S.s_lineptr = upload<int>(h.s_lineptr, &st));
+        CHK(S.s_seg_line = upload<int>(h.s_seg_line, &st));
+        CHK(S.s_seg_x = upload<int>(h.s_seg_x, &st));
+        CHK(S.s_seg_e0 = upload<int>(h.s_seg_e0, &st));
+        CHK(S.s_ent_sensor = upload<int>(h.s_ent_sensor, &st));
+        CHK(S.s_ent_w = upload<T>(h.s_ent_w, &st));
+#undef CHK
+        // launch configuration
+        cfg = h.cfg;
+        const int qmax = std::max(D, 2) * cfg.row_lines / 2;
+        row_smem = (size_t)(h.nx + 2 * qmax * h.nx) * sizeof(cplx<T>);
+        const int L = std::max(h.ny, h.nz);
+        spec_smem = (size_t)(L + 3 * L * cfg.col_w) * sizeof(cplx<T>);
+        if (D == 2) st = set_attrs<2>();
+        else st = set_attrs<3>();
+        if (st != PAT_OK) return st;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        return PAT_OK;
+    }
+
+    template <int D> pat_status set_attrs() {
+        cudaError_t e = cudaSuccess;
+        auto seta = [&](const void* f, size_t bytes) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        };
+        seta((const void*)k_fwd_init<T, D>, row_smem);
+        seta((const void*)k_fwd_u<T, D>, row_smem);
+        seta((const void*)k_fwd_rho<T, D>, row_smem);
+        seta((const void*)k_fwd_p<T, D>, row_smem);
+        seta((const void*)k_adj_init<T, D>, row_smem);
+        seta((const void*)k_adj_rho<T, D>, row_smem);
+        seta((const void*)k_adj_u<T, D>, row_smem);
+        seta((const void*)k_adj_p<T, D>, row_smem);
+        seta((const void*)k_spec<T, D, SPEC_PLAIN_FWD>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_PLAIN_INV>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_GRAD>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_DIV>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_ABS>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_DIVT>, spec_smem);
+        seta((const void*)k_spec<T, D, SPEC_GRADT>, spec_smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (shared memory)");
+        return PAT_OK;
+    }
+
+    // ---------------------------------------------------------------------------------------
+    // launch helpers (used while capturing)
+    // ---------------------------------------------------------------------------------------
+    int row_grid() const { return P.nlines / cfg.row_lines; }
+
+    template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F) {
+        const int tiles = (P.nxh + cfg.col_w - 1) / cfg.col_w;
+        const int outer = (lax == 1) ? P.nz : P.ny;
+        k_spec<T, D, MODE><<<dim3(tiles, outer), cfg.col_threads, spec_smem, s>>>(P, cfg.col_w, lax, F);
+    }
+
+    template <int D, int MODE> void spectral(cudaStream_t s) {
+        if (D == 2) {
+            spec_launch<D, MODE>(s, 1, 0);
+            return;
+        }
+        const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+        const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+        spec_launch<D, SPEC_PLAIN_FWD>(s, 1, fin);
+        spec_launch<D, MODE>(s, 2, 0);
+        spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout);
+    }
+
+    template <int D> void record_forward(cudaStream_t s) {
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        const int Nt = H.Nt, Ns = H.Ns;
+        cudaMemsetAsync(P.data, 0, (size_t)Nt * Ns * sizeof(T), s);
+        k_fwd_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1);
+        for (int n = 0; n + 1 < Nt; ++n) {
+            const int last = (n + 2 == Nt);
+            T* row = P.data + (size_t)(n + 1) * Ns;
+            spectral<D, SPEC_GRAD>(s);
+            k_fwd_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
+            spectral<D, SPEC_DIV>(s);
+            k_fwd_rho<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
+            if (P.lossy) {
+                spectral<D, SPEC_ABS>(s);
+                k_fwd_p<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
+            }
+        }
+    }
+
+    template <int D> void record_adjoint(cudaStream_t s) {
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        const int Nt = H.Nt, Ns = H.Ns;
+        const size_t N = (size_t)P.N;
+        for (int a = 0; a < D; ++a) {
+            cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
+            cudaMemsetAsync(P.rh[a], 0, N * sizeof(T), s);
+        }
+        k_adj_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1, P.data + (size_t)(Nt - 1) * Ns);
+        for (int n = Nt - 2; n >= 0; --n) {
+            if (P.lossy) {
+                spectral<D, SPEC_ABS>(s);
+                k_adj_rho<T, D><<<G, B, row_smem, s>>>(P, R);
+            }
+            spectral<D, SPEC_DIVT>(s);
+            k_adj_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
+            spectral<D, SPEC_GRADT>(s);
+            k_adj_p<T, D><<<G, B, row_smem, s>>>(P, R, n == 0, P.data + (size_t)n * Ns);
+        }
+    }
+
+    pat_status capture(bool adjoint, cudaGraphExec_t* out) {
+        cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        if (P.d == 2) {
+            if (adjoint) record_adjoint<2>(cap_stream);
+            else record_forward<2>(cap_stream);
+        } else {
+            if (adjoint) record_adjoint<3>(cap_stream);
+            else record_forward<3>(cap_stream);
+        }
+        cudaError_t le = cudaGetLastError();
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap_stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(le, "kernel launch during capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        return PAT_OK;
+    }
+};
+
+template <typename T> PlanBase* make_plan(const HostTables& h, pat_status* st) {
+    Plan<T>* p = new Plan<T>();
+    p->info = h.info;
+    cudaGetDevice(&p->device);
+    *st = p->build(h);
+    if (*st != PAT_OK) {
+        delete p;
+        return nullptr;
+    }
+    return p;
+}
+
+PlanBase* make_plan_f32(const HostTables& h, pat_status* st) { return make_plan<float>(h, st); }
+PlanBase* make_plan_f64(const HostTables& h, pat_status* st) { return make_plan<double>(h, st); }
+
+pat_status plan_capture(PlanBase* base, bool adjoint) {
+    cudaGraphExec_t* slot = adjoint ? &base->adj_exec : &base->fwd_exec;
+    if (*slot) return PAT_OK;
+    if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->capture(adjoint, slot);
+    return static_cast<Plan<double>*>(base)->capture(adjoint, slot);
+}
+
+}  // namespace pat

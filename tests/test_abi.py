@@ -1,0 +1,107 @@
+"""The C-ABI library loads, exports every symbol include/*.h declares, and validates arguments on
+the host (no GPU needed: every check below fails before any device call)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(pat_[A-Za-z0-9_]+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1603_02329_gb300 import build, _lib
+
+    build.build()
+    return _lib.lib()
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared_symbols()
+    for n in ["pat_plan_create", "pat_plan_destroy", "pat_forward", "pat_forward_plan", "pat_adjoint", "pat_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in _declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _grid(n=(16, 16), pml=(2, 2)):
+    from paper_1603_02329_gb300.api import make_grid
+
+    return make_grid(n, (1e-4, 1e-4), pml, 2.0)
+
+
+def _call_create(L, grid, c, rho, a0, y=1.5, sens_pos=None, sens_idx=None, dt=1e-8, Nt=10, prec=0):
+    from paper_1603_02329_gb300 import _lib
+
+    dp = ctypes.POINTER(ctypes.c_double)
+    s = _lib.pat_sensors()
+    keep = []
+    if sens_idx is not None:
+        a = np.ascontiguousarray(np.asarray(sens_idx, np.int64))
+        keep.append(a)
+        s.count, s.index = a.size, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if sens_pos is not None:
+        a = np.ascontiguousarray(np.asarray(sens_pos, np.float64))
+        keep.append(a)
+        s.count, s.pos = a.shape[0], a.ctypes.data_as(dp)
+    plan = ctypes.c_void_p()
+    st = L.pat_plan_create(ctypes.byref(grid), c.ctypes.data_as(dp), rho.ctypes.data_as(dp), a0.ctypes.data_as(dp),
+                           int(a0.size == 1), float(y), ctypes.byref(s), float(dt), int(Nt), int(prec),
+                           ctypes.byref(plan))
+    return st, plan
+
+
+def test_host_side_argument_validation(L):
+    from paper_1603_02329_gb300._lib import PAT_EINVAL, PAT_EUNSUPPORTED
+
+    N = 256
+    c = np.full(N, 1500.0)
+    rho = np.full(N, 1000.0)
+    a0 = np.zeros(1)
+    # odd grid size
+    st, _ = _call_create(L, _grid((16, 15)), np.full(240, 1500.0), np.full(240, 1000.0), a0, sens_idx=[0])
+    assert st == PAT_EUNSUPPORTED
+    # a prime factor of 11 (22 = 2 * 11) is not a supported FFT length
+    st, _ = _call_create(L, _grid((16, 22)), np.full(352, 1500.0), np.full(352, 1000.0), a0, sens_idx=[0])
+    assert st == PAT_EUNSUPPORTED
+    # sensor index outside the grid
+    st, _ = _call_create(L, _grid(), c, rho, a0, sens_idx=[N])
+    assert st == PAT_EINVAL
+    # sensor position outside the grid
+    st, _ = _call_create(L, _grid(), c, rho, a0, sens_pos=[[1.0, 0.0]])
+    assert st == PAT_EINVAL
+    # negative sound speed
+    bad = c.copy()
+    bad[3] = -1.0
+    st, _ = _call_create(L, _grid(), bad, rho, a0, sens_idx=[0])
+    assert st == PAT_EINVAL
+    # y = 1 with absorption (tan(pi y / 2) diverges)
+    st, _ = _call_create(L, _grid(), c, rho, np.full(1, 0.5), y=1.0, sens_idx=[0])
+    assert st == PAT_EINVAL
+    # Nt = 0, dt <= 0, PML wider than half the grid
+    assert _call_create(L, _grid(), c, rho, a0, sens_idx=[0], Nt=0)[0] == PAT_EINVAL
+    assert _call_create(L, _grid(), c, rho, a0, sens_idx=[0], dt=0.0)[0] == PAT_EINVAL
+    assert _call_create(L, _grid(pml=(9, 2)), c, rho, a0, sens_idx=[0])[0] == PAT_EINVAL
+    msg = L.pat_last_error().decode()
+    assert "PML" in msg
+    # NULL arguments
+    assert L.pat_plan_create(None, None, None, None, 0, 1.5, None, 1e-8, 10, 0, None) == PAT_EINVAL
+    assert L.pat_forward_plan(None, None, None, None) == PAT_EINVAL
+    assert L.pat_adjoint(None, None, None, None) == PAT_EINVAL
+    assert L.pat_plan_destroy(None) == 0

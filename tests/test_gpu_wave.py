@@ -1,0 +1,206 @@
+"""GPU parity of the forward operator H and its transpose against the FP64 oracle, through the C ABI.
+
+Tolerances: relative L2 <= 1e-5 for FP32 fields (data and gradients), <= 1e-11 for FP64 plans.
+Full-size workloads are checked on what the oracle can compute in seconds: the first time
+samples (a causal prefix) and the adjoint of a residual supported on that prefix, plus the
+dot-product identity, which holds at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.pat_oracle import Operator
+from paper_1603_02329_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-11
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / np.linalg.norm(np.asarray(b, float)))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_1603_02329_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda", 0)
+
+
+def _gpu_op(pb, prec, dev, Nt=None):
+    from paper_1603_02329_gb300.api import PATOperator
+
+    return PATOperator.from_problem(pb, precision=prec, device=dev, Nt=Nt)
+
+
+def _t(a, prec, dev):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32 if prec == "f32" else torch.float64, device=dev)
+
+
+CASES_2D = [
+    # name, factory kwargs
+    ("lossy_48x40_offgrid", dict(shape=(48, 40), pml=6, Nt=120, n_sensors=20)),
+    ("lossy_30x42_ragged", dict(shape=(30, 42), pml=5, Nt=80, n_sensors=12, sensor_radius_frac=0.25)),
+    ("lossy_64x64", dict(shape=(64, 64), pml=8, Nt=200, n_sensors=48)),
+    ("lossy_96x112", dict(shape=(96, 112), pml=10, Nt=150, n_sensors=32)),
+]
+
+
+@pytest.mark.parametrize("name,kw", CASES_2D, ids=[c[0] for c in CASES_2D])
+def test_forward_adjoint_parity_2d_f32(dev, name, kw):
+    pb = synth.small_lossy_2d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(3).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f32", dev)
+    d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+    g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+    assert rel(d, ref.forward(pb.p0)) <= TOL32
+    assert rel(g, ref.adjoint(h)) <= TOL32
+
+
+def test_forward_adjoint_parity_2d_f64_lossless(dev):
+    pb = synth.disc_phantom_2d(interior=40, pml=8, Nt=150, n_sensors=24, sensor_radius=1.6e-3)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(4).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f64", dev)
+    d = op.forward(_t(pb.p0, "f64", dev)).cpu().numpy()
+    g = op.adjoint(_t(h, "f64", dev)).cpu().numpy()
+    assert rel(d, ref.forward(pb.p0)) <= TOL64
+    assert rel(g, ref.adjoint(h)) <= TOL64
+
+
+def test_forward_adjoint_parity_2d_f64_lossy(dev):
+    pb = synth.small_lossy_2d(shape=(40, 48), pml=6, Nt=90, n_sensors=16)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(5).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f64", dev)
+    assert rel(op.forward(_t(pb.p0, "f64", dev)).cpu().numpy(), ref.forward(pb.p0)) <= TOL64
+    assert rel(op.adjoint(_t(h, "f64", dev)).cpu().numpy(), ref.adjoint(h)) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [(24, 32, 40), (16, 20, 28)])
+def test_forward_adjoint_parity_3d_f32(dev, shape):
+    pb = synth.small_lossy_3d(shape=shape, pml=4, Nt=50)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(6).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f32", dev)
+    assert rel(op.forward(_t(pb.p0, "f32", dev)).cpu().numpy(), ref.forward(pb.p0)) <= TOL32
+    assert rel(op.adjoint(_t(h, "f32", dev)).cpu().numpy(), ref.adjoint(h)) <= TOL32
+
+
+def test_forward_adjoint_parity_3d_f64_offgrid(dev):
+    rng = np.random.default_rng(9)
+    pb = synth.small_lossy_3d(shape=(16, 20, 24), pml=3, Nt=30)
+    pos = rng.uniform(-0.3, 0.3, size=(15, 3)) * np.array([24, 20, 16]) * pb.spacing[0]
+    pb.sensor_index = None
+    pb.sensor_pos = pos
+    ref = Operator.from_problem(pb)
+    h = rng.standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f64", dev)
+    assert rel(op.forward(_t(pb.p0, "f64", dev)).cpu().numpy(), ref.forward(pb.p0)) <= TOL64
+    assert rel(op.adjoint(_t(h, "f64", dev)).cpu().numpy(), ref.adjoint(h)) <= TOL64
+
+
+@pytest.mark.parametrize("Nt", [1, 2, 3])
+def test_short_time_axes(dev, Nt):
+    pb = synth.small_lossy_2d(shape=(32, 32), pml=4, Nt=Nt, n_sensors=8)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(7).standard_normal((Nt, ref.Ns))
+    op = _gpu_op(pb, "f64", dev)
+    assert rel(op.forward(_t(pb.p0, "f64", dev)).cpu().numpy(), ref.forward(pb.p0)) <= TOL64
+    assert rel(op.adjoint(_t(h, "f64", dev)).cpu().numpy(), ref.adjoint(h)) <= TOL64
+
+
+def test_coincident_and_corner_sensors(dev):
+    # two sensors at the same point, one exactly on a node, one on a cell corner of the PML
+    pb = synth.small_lossy_2d(shape=(32, 36), pml=4, Nt=40, n_sensors=6)
+    h = pb.spacing[0]
+    extra = np.array([[0.37 * h, -1.25 * h], [0.37 * h, -1.25 * h], [3 * h, 2 * h], [-18 * h, -16 * h]])
+    pb.sensor_pos = np.concatenate([pb.sensor_pos, extra])
+    ref = Operator.from_problem(pb)
+    hh = np.random.default_rng(8).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f64", dev)
+    d = op.forward(_t(pb.p0, "f64", dev)).cpu().numpy()
+    assert rel(d, ref.forward(pb.p0)) <= TOL64
+    assert np.array_equal(d[:, -3], d[:, -4])
+    assert rel(op.adjoint(_t(hh, "f64", dev)).cpu().numpy(), ref.adjoint(hh)) <= TOL64
+
+
+def test_dot_product_f32(dev):
+    pb = synth.small_lossy_2d(shape=(64, 64), pml=8, Nt=150, n_sensors=32)
+    op = _gpu_op(pb, "f32", dev)
+    rng = np.random.default_rng(10)
+    x = _t(rng.standard_normal(pb.shape), "f32", dev)
+    h = _t(rng.standard_normal((pb.Nt, op.Ns)), "f32", dev)
+    Hx = op.forward(x).double()
+    HTh = op.adjoint(h).double()
+    lhs = torch.sum(Hx * h.double()).item()
+    rhs = torch.sum(x.double() * HTh).item()
+    assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * h.double().norm().item()
+
+
+def test_host_pointer_path_and_determinism(dev):
+    pb = synth.small_lossy_2d(shape=(48, 48), pml=6, Nt=60, n_sensors=16)
+    op = _gpu_op(pb, "f32", dev)
+    x = _t(pb.p0, "f32", dev)
+    d1 = op.forward(x).cpu()
+    d2 = op.forward(x).cpu()
+    d_host = op.forward(x.cpu())
+    assert torch.equal(d1, d2) and torch.equal(d1, d_host)
+    g1 = op.adjoint(d1.to(dev)).cpu()
+    g_host = op.adjoint(d1)
+    assert torch.equal(g1, g_host)
+
+
+def test_one_shot_pat_forward(dev):
+    from paper_1603_02329_gb300.api import pat_forward
+
+    pb = synth.small_lossy_2d(shape=(32, 40), pml=4, Nt=30, n_sensors=10)
+    ref = Operator.from_problem(pb)
+    d = pat_forward(_t(pb.p0, "f64", dev), pb.c, pb.rho, pb.alpha0, pb.y, pb.shape, pb.spacing, pb.pml, pb.pml_alpha,
+                    sensor_pos=pb.sensor_pos, dt=pb.dt, Nt=pb.Nt, precision="f64")
+    assert rel(d.cpu().numpy(), ref.forward(pb.p0)) <= TOL64
+
+
+def test_disc_phantom_168_f64_full_size(dev):
+    # 128^2 interior + 20-point outer PML, 256 sensors on a 5.5 mm circle, Nt = 600, FP64
+    pb = synth.disc_phantom_2d()
+    ref = Operator.from_problem(pb)
+    op = _gpu_op(pb, "f64", dev)
+    d = op.forward(_t(pb.p0, "f64", dev)).cpu().numpy()
+    d_ref = ref.forward(pb.p0)
+    assert rel(d, d_ref) <= TOL64
+    g = op.adjoint(_t(d_ref, "f64", dev)).cpu().numpy()
+    assert rel(g, ref.adjoint(d_ref)) <= TOL64
+
+
+def test_vessel_512_full_size_prefix_and_dot(dev):
+    # 512^2 heterogeneous absorbing medium, Nt = 2000, 512 line sensors: the launch configuration
+    # the benchmark times.  Prefix of K samples vs the oracle (causality), adjoint of a residual
+    # supported on that prefix vs the oracle, and the dot identity over all 2000 samples.  K is past
+    # the first arrival at the sensor row (sources start >= 44 px from it, ~3.5 steps per px), so
+    # the compared data are not dominated by the pre-arrival noise floor.
+    pb = synth.vessel_phantom_2d()
+    K = 300
+    ref = Operator.from_problem(pb, Nt=K)
+    op = _gpu_op(pb, "f32", dev)
+    d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+    assert d.shape == (2000, 512)
+    assert rel(d[:K], ref.forward(pb.p0)) <= TOL32
+    rng = np.random.default_rng(12)
+    h = np.zeros((pb.Nt, op.Ns))
+    h[:K] = rng.standard_normal((K, op.Ns))
+    g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+    assert rel(g, ref.adjoint(h[:K])) <= TOL32
+    x = _t(rng.standard_normal(pb.shape), "f32", dev)
+    hh = _t(rng.standard_normal((pb.Nt, op.Ns)), "f32", dev)
+    Hx = op.forward(x).double()
+    HTh = op.adjoint(hh).double()
+    lhs = torch.sum(Hx * hh.double()).item()
+    rhs = torch.sum(x.double() * HTh).item()
+    assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * hh.double().norm().item()
+    assert np.isfinite(d).all() and np.abs(d).max() > 0

@@ -1,0 +1,336 @@
+"""Benchmark of the forward + adjoint solve pair (one H^T H product) on GB300.
+
+Workload (default): 2-D 512^2 heterogeneous absorbing medium (c = 1500 +/- 100 m/s, rho = 1000
++/- 5 %, alpha0 = 0.75 dB MHz^-1.5 cm^-1, y = 1.5), 20-point PML, 512 on-grid line sensors,
+Nt = 2000, FP32 fields.  One step = pat_forward_plan + pat_adjoint through the C ABI: 2 N Nt
+grid-point-steps.  value = grid-point-steps per second over all ranks (Gpt-steps/s).
+
+Multi-GPU: one independent instance per rank (weak scaling, no collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle (the test oracle under ``oracle/``) on a bounded
+sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adj Gpt-steps/s (%HBM roofline); MG-FISTA vs FISTA time to target RE"
+UNIT = "Gpt-steps/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="vessel2d_512", choices=["vessel2d_512", "disc2d_168"])
+    ap.add_argument("--probe-stride", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    from paper_1603_02329_gb300 import synth
+
+    if name == "vessel2d_512":
+        pb = synth.vessel_phantom_2d(seed=2 + rank)
+        prec = "f32"
+        desc = {"workload": "2-D 512^2 heterogeneous absorbing medium (alpha0=0.75, y=1.5), 20-pt PML, "
+                            "512 on-grid line sensors, Nt=2000, vessel+disc phantom",
+                "grid": [512, 512], "Nt": 2000, "Ns": 512, "pml": 20, "dx_m": 5e-5, "cfl": 0.3}
+    else:
+        pb = synth.disc_phantom_2d(seed=1 + rank)
+        prec = "f64"
+        desc = {"workload": "2-D 168^2 homogeneous lossless (128^2 + 20-pt outer PML), 256 circle sensors, "
+                            "Nt=600, disc phantom, FP64",
+                "grid": [168, 168], "Nt": 600, "Ns": 256, "pml": 20, "dx_m": 1e-4, "cfl": 0.3}
+    return pb, prec, desc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# algorithmic bytes per launch of each kernel (operands read + written once; 2-D, lossy or not)
+def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
+    Hs = Nh * 2 * w      # one half spectrum
+    F = N * w            # one real field
+    table = {
+        "spec_grad": (1 + D) * Hs,
+        "spec_div": 2 * D * Hs,
+        "spec_divt": 2 * D * Hs,
+        "spec_abs": 4 * Hs,
+        "spec_gradt": (D + 1) * Hs,
+        "fwd_u": 2 * D * Hs + 3 * D * F,
+        "fwd_rho": ((D + 2) * Hs + (2 * D + 2) * F) if lossy else ((D + 1) * Hs + (2 * D + 2) * F),
+        "fwd_p": 3 * Hs + 4 * F,
+        "adj_rho": (2 + D) * Hs + (3 + 2 * D) * F,
+        "adj_u": 2 * D * Hs + 3 * D * F,
+        "adj_p": (3 * Hs + 3 * F) if lossy else ((1 + D) * Hs + (2 + 2 * D) * F),
+    }
+    return table.get(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """FP64 CPU oracle, timed as it stands on the host cores, on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.pat_oracle import Operator
+
+    pb, prec, desc = workload(args.workload, 0)
+    Nt_s = 50 if args.workload == "vessel2d_512" else 150
+    op = Operator.from_problem(pb, Nt=Nt_s)
+    h = np.random.default_rng(0).standard_normal((Nt_s, op.Ns))
+    for _ in range(args.warmup):
+        op.adjoint(op.forward(pb.p0))
+        break
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        op.adjoint(op.forward(pb.p0))
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    v = 2.0 * pb.N * Nt_s / t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"forward+adjoint over the first {Nt_s} of {pb.Nt} time steps of the same grid"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(args, pb):
+    """Oracle timed on a bounded sample (same grid, first Nt_s steps), single-threaded numpy."""
+    from oracle.pat_oracle import Operator
+
+    Nt_s = 200 if args.workload == "vessel2d_512" else 600
+    op = Operator.from_problem(pb, Nt=Nt_s)
+    t0 = time.perf_counter()
+    op.adjoint(op.forward(pb.p0))
+    t = time.perf_counter() - t0
+    return {"value": 2.0 * pb.N * Nt_s / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one forward+adjoint over the first {Nt_s} of {pb.Nt} time steps of the same grid "
+                      f"({t:.1f} s), FP64 numpy"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_02329_gb300 import build
+    from paper_1603_02329_gb300.api import PATOperator
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    pb, prec, desc = workload(args.workload, rank)
+    dtype = torch.float32 if prec == "f32" else torch.float64
+    w = 4 if prec == "f32" else 8
+    op = PATOperator.from_problem(pb, precision=prec, device=dev)
+    if args.probe_stride > 0:
+        op.set_probe(args.probe_stride)
+    x = torch.tensor(pb.p0, dtype=dtype, device=dev)
+    data = torch.empty((pb.Nt, op.Ns), dtype=dtype, device=dev)
+    grad = torch.empty(pb.shape, dtype=dtype, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        op.forward(x, out=data, stream=stream)
+        op.adjoint(data, out=grad, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    probe_acc = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        op.forward(x, out=data, stream=stream)
+        fwd_probe_ready = True
+        op.adjoint(data, out=grad, stream=stream)
+        ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if args.probe_stride > 0 and fwd_probe_ready:
+            # the forward graph's probe events are final once the step has completed; the adjoint's too
+            for g, tag in ((0, "fwd"), (1, "adj")):
+                for name, ms, cnt in op.probe(bool(g)):
+                    acc = probe_acc.setdefault((tag, name), [0.0, 0])
+                    acc[0] += ms * cnt
+                    acc[1] += cnt
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    units = 2.0 * pb.N * pb.Nt * args.steps * world
+    value = units / total_s / 1e9
+
+    # e2e: the same step through the C ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.tensor(pb.p0, dtype=dtype).pin_memory()
+        dh = torch.empty((pb.Nt, op.Ns), dtype=dtype).pin_memory()
+        gh = torch.empty(pb.shape, dtype=dtype).pin_memory()
+        op.forward(xh, out=dh, stream=stream)
+        op.adjoint(dh, out=gh, stream=stream)
+        torch.cuda.synchronize()
+        t_e2e = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op.forward(xh, out=dh, stream=stream)
+            op.adjoint(dh, out=gh, stream=stream)
+            torch.cuda.synchronize()
+            t_e2e += time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        nb_in = pb.N * w + pb.Nt * op.Ns * w       # p0 for H, residual for H^T
+        nb_out = pb.Nt * op.Ns * w + pb.N * w      # data from H, gradient from H^T
+        e2e = {"value": units / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb_in, "d2h_bytes_per_step": nb_out}
+
+    # roofline of the dominant kernel (largest share of the probed step time)
+    peak, peak_kind = measured_peaks()
+    nxh = pb.shape[-1] // 2 + 1
+    Nh = nxh * int(np.prod(pb.shape[:-1]))
+    roof = None
+    kernels = {}
+    if probe_acc:
+        for (tag, name), (sm, cnt) in probe_acc.items():
+            kernels[f"{tag}:{name}"] = sm / max(cnt, 1)
+        dom = max(kernels, key=lambda k: kernels[k])
+        tag, name = dom.split(":")
+        b = kernel_bytes(name, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
+        ms = kernels[dom]
+        ach = b / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "kernel": dom, "kernel_ms": ms, "algorithmic_bytes": b,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "note": "working set is L2-resident (about 15 MB < 129 MB L2); the fraction is effective bandwidth"}
+    # whole-step roofline by the per-point-step algorithmic bytes (state once + medium once)
+    B_pt = (2 * (2 * len(pb.shape) + 1) + (4 if op.lossy else 2)) * w
+    step_roof = {"bytes_per_pt_step": B_pt, "achieved_gbs": value * 1e9 * B_pt / 1e9 / world,
+                 "frac": value * B_pt / world / peak}
+
+    slots_f = 6 if op.lossy else 4
+    launches = args.steps * 2 * (1 + (pb.Nt - 1) * slots_f)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+           "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
+                          parallelism=f"replicas x{world}"),
+           "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels,
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args, pb)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    op.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -131,6 +131,17 @@ pat_status pat_forward(const void* p0, const double* c, const double* rho, const
                        const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
                        void* data, void* stream);
 
+/* Kernel-timing probe (tracing).  With stride S > 0, the next captured graphs bracket every kernel
+ * launch of every S-th time step (starting at step S/2) with CUDA events; after a solve has
+ * completed, pat_plan_probe_read returns, for launch slot `slot` of the step (0 <= slot <
+ * pat_plan_probe_slots), its kernel name and its mean duration over the sampled steps of the last
+ * solve.  stride = 0 turns the probe off.  Changing the stride drops the captured graphs (they are
+ * re-captured on the next call).  `adjoint` selects the H (0) or H^T (1) graph. */
+pat_status pat_plan_set_probe(pat_plan* plan, int stride);
+int pat_plan_probe_slots(const pat_plan* plan, int adjoint);
+pat_status pat_plan_probe_read(pat_plan* plan, int adjoint, int slot, const char** name, double* mean_ms,
+                               int* samples);
+
 /* pat_last_error -- message describing the calling thread's last failed call ("" if none).
  * The pointer stays valid until the next pat_* call on the same thread. */
 const char* pat_last_error(void);

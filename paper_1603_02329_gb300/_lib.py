@@ -66,6 +66,13 @@ def lib() -> ctypes.CDLL:
     L.pat_forward.argtypes = [vp, dp, dp, dp, i32, f64, ctypes.POINTER(pat_grid), ctypes.POINTER(pat_sensors), f64, i32,
                               i32, vp, vp]
     L.pat_forward.restype = i32
+    L.pat_plan_set_probe.argtypes = [vp, i32]
+    L.pat_plan_set_probe.restype = i32
+    L.pat_plan_probe_slots.argtypes = [vp, i32]
+    L.pat_plan_probe_slots.restype = i32
+    L.pat_plan_probe_read.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f64),
+                                      ctypes.POINTER(i32)]
+    L.pat_plan_probe_read.restype = i32
     L.pat_last_error.argtypes = []
     L.pat_last_error.restype = ctypes.c_char_p
     _lib = L

@@ -132,6 +132,24 @@ class PATOperator:
                                     _stream_ptr(stream, self.device)))
         return out
 
+    # -- kernel-timing probe ------------------------------------------------------------------------
+    def set_probe(self, stride: int):
+        """pat_plan_set_probe: bracket the launches of every `stride`-th step with CUDA events."""
+        check(lib().pat_plan_set_probe(self._plan, int(stride)))
+
+    def probe(self, adjoint: bool):
+        """pat_plan_probe_read for every slot: list of (kernel name, mean ms, samples) of the last solve."""
+        out = []
+        n = lib().pat_plan_probe_slots(self._plan, int(adjoint))
+        for k in range(n):
+            name = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            cnt = ctypes.c_int()
+            check(lib().pat_plan_probe_read(self._plan, int(adjoint), k, ctypes.byref(name), ctypes.byref(ms),
+                                            ctypes.byref(cnt)))
+            out.append((name.value.decode(), ms.value, cnt.value))
+        return out
+
     def close(self):
         if getattr(self, "_plan", None) is not None and self._plan.value:
             lib().pat_plan_destroy(self._plan)

@@ -32,5 +32,6 @@ struct HostTables {
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st);
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
 pat_status plan_capture(PlanBase* base, bool adjoint);
+pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, double* mean_ms, int* samples);
 
 }  // namespace pat

@@ -143,6 +143,11 @@ struct PlanBase {
     cudaGraphExec_t fwd_exec = nullptr;
     cudaGraphExec_t adj_exec = nullptr;
     std::vector<void*> allocs;   // every device allocation owned by the plan
+    // kernel-timing probe: events around the launches of sampled steps
+    int probe_stride = 0;
+    std::vector<cudaEvent_t> probe_ev[2];          // [graph][sample * (slots + 1) + k]
+    std::vector<std::string> probe_names[2];       // slot names of one step
+    int probe_samples[2] = {0, 0};
     void* img_ptr = nullptr;
     void* data_ptr = nullptr;
     size_t elem = 4;

@@ -446,6 +446,36 @@ pat_status pat_forward(const void* p0, const double* c, const double* rho, const
     return st;
 }
 
+pat_status pat_plan_set_probe(pat_plan* plan, int stride) {
+    set_error("");
+    if (!plan || stride < 0) return fail(PAT_EINVAL, "bad probe arguments");
+    PlanBase* b = plan->impl;
+    if (stride == b->probe_stride) return PAT_OK;
+    DeviceGuard g(b->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (b->fwd_exec) cudaGraphExecDestroy(b->fwd_exec);
+    if (b->adj_exec) cudaGraphExecDestroy(b->adj_exec);
+    b->fwd_exec = b->adj_exec = nullptr;
+    b->probe_stride = stride;
+    return PAT_OK;
+}
+
+int pat_plan_probe_slots(const pat_plan* plan, int adjoint) {
+    if (!plan) return 0;
+    return (int)plan->impl->probe_names[adjoint ? 1 : 0].size();
+}
+
+pat_status pat_plan_probe_read(pat_plan* plan, int adjoint, int slot, const char** name, double* mean_ms,
+                               int* samples) {
+    set_error("");
+    if (!plan || !name || !mean_ms || !samples) return fail(PAT_EINVAL, "NULL argument");
+    DeviceGuard g(plan->impl->device);
+    pat_status st = plan_probe_read(plan->impl, adjoint ? 1 : 0, slot, name, mean_ms, samples);
+    if (st == PAT_EINVAL) set_error("probe slot out of range (probe off or graph not captured yet)");
+    return st;
+}
+
 const char* pat_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

@@ -62,6 +62,8 @@ template <typename T> struct Plan : public PlanBase {
         if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (int g = 0; g < 2; ++g)
+            for (cudaEvent_t ev : probe_ev[g]) cudaEventDestroy(ev);
         for (void* p : allocs) cudaFree(p);
     }
 
@@ -208,22 +210,77 @@ template <typename T> struct Plan : public PlanBase {
         spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout);
     }
 
+    // --- kernel-timing probe -----------------------------------------------------------------
+    // While recording a sampled step, `mark` records one event before each launch (and one after
+    // the last); names are collected on the first sampled step.
+    int probe_g = -1;         // graph being recorded (0 fwd, 1 adj) when sampling, else -1
+    size_t probe_next = 0;    // next event of probe_ev[probe_g]
+    bool probe_first = false;
+    void mark(cudaStream_t s, const char* name) {
+        if (probe_g < 0) return;
+        if (probe_next >= probe_ev[probe_g].size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            probe_ev[probe_g].push_back(ev);
+        }
+        // inside stream capture only an "external" record becomes an event-record node
+        cudaEventRecordWithFlags(probe_ev[probe_g][probe_next++], s, cudaEventRecordExternal);
+        if (probe_first && name) probe_names[probe_g].push_back(name);
+    }
+    bool sampled(int n, int Nt) const {
+        if (probe_stride <= 0) return false;
+        return n >= probe_stride / 2 && (n - probe_stride / 2) % probe_stride == 0 && n + 1 < Nt;
+    }
+    void begin_sample(int g, bool first) {
+        probe_g = g;
+        probe_first = first;
+    }
+    void end_sample(cudaStream_t s) {
+        mark(s, nullptr);
+        probe_g = -1;
+        probe_first = false;
+    }
+
+    template <int D, int MODE> void spectral_named(cudaStream_t s, const char* name) {
+        if (D == 2) {
+            mark(s, name);
+            spec_launch<D, MODE>(s, 1, 0);
+            return;
+        }
+        const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+        const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+        mark(s, "spec_y_fwd");
+        spec_launch<D, SPEC_PLAIN_FWD>(s, 1, fin);
+        mark(s, name);
+        spec_launch<D, MODE>(s, 2, 0);
+        mark(s, "spec_y_inv");
+        spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout);
+    }
+
     template <int D> void record_forward(cudaStream_t s) {
         const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         const int Nt = H.Nt, Ns = H.Ns;
+        probe_next = 0;
+        probe_names[0].clear();
+        probe_samples[0] = 0;
         cudaMemsetAsync(P.data, 0, (size_t)Nt * Ns * sizeof(T), s);
         k_fwd_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1);
         for (int n = 0; n + 1 < Nt; ++n) {
             const int last = (n + 2 == Nt);
             T* row = P.data + (size_t)(n + 1) * Ns;
-            spectral<D, SPEC_GRAD>(s);
+            if (sampled(n, Nt)) begin_sample(0, probe_samples[0]++ == 0);
+            spectral_named<D, SPEC_GRAD>(s, "spec_grad");
+            mark(s, "fwd_u");
             k_fwd_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
-            spectral<D, SPEC_DIV>(s);
+            spectral_named<D, SPEC_DIV>(s, "spec_div");
+            mark(s, "fwd_rho");
             k_fwd_rho<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
             if (P.lossy) {
-                spectral<D, SPEC_ABS>(s);
+                spectral_named<D, SPEC_ABS>(s, "spec_abs");
+                mark(s, "fwd_p");
                 k_fwd_p<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
             }
+            if (probe_g >= 0) end_sample(s);
         }
     }
 
@@ -235,16 +292,24 @@ template <typename T> struct Plan : public PlanBase {
             cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
             cudaMemsetAsync(P.rh[a], 0, N * sizeof(T), s);
         }
+        probe_next = 0;
+        probe_names[1].clear();
+        probe_samples[1] = 0;
         k_adj_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1, P.data + (size_t)(Nt - 1) * Ns);
         for (int n = Nt - 2; n >= 0; --n) {
+            if (sampled(n, Nt)) begin_sample(1, probe_samples[1]++ == 0);
             if (P.lossy) {
-                spectral<D, SPEC_ABS>(s);
+                spectral_named<D, SPEC_ABS>(s, "spec_abs");
+                mark(s, "adj_rho");
                 k_adj_rho<T, D><<<G, B, row_smem, s>>>(P, R);
             }
-            spectral<D, SPEC_DIVT>(s);
+            spectral_named<D, SPEC_DIVT>(s, "spec_divt");
+            mark(s, "adj_u");
             k_adj_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
-            spectral<D, SPEC_GRADT>(s);
+            spectral_named<D, SPEC_GRADT>(s, "spec_gradt");
+            mark(s, "adj_p");
             k_adj_p<T, D><<<G, B, row_smem, s>>>(P, R, n == 0, P.data + (size_t)n * Ns);
+            if (probe_g >= 0) end_sample(s);
         }
     }
 
@@ -287,6 +352,27 @@ template <typename T> PlanBase* make_plan(const HostTables& h, pat_status* st) {
 
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st) { return make_plan<float>(h, st); }
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st) { return make_plan<double>(h, st); }
+
+pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, double* mean_ms, int* samples) {
+    const int slots = (int)b->probe_names[g].size();
+    if (slot < 0 || slot >= slots) return PAT_EINVAL;
+    const int ns = b->probe_samples[g];
+    double sum = 0.0;
+    int cnt = 0;
+    for (int k = 0; k < ns; ++k) {
+        const size_t e0 = (size_t)k * (slots + 1) + slot;
+        if (e0 + 1 >= b->probe_ev[g].size()) break;
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, b->probe_ev[g][e0], b->probe_ev[g][e0 + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime (probe)");
+        sum += ms;
+        ++cnt;
+    }
+    *name = b->probe_names[g][slot].c_str();
+    *mean_ms = cnt ? sum / cnt : 0.0;
+    *samples = cnt;
+    return PAT_OK;
+}
 
 pat_status plan_capture(PlanBase* base, bool adjoint) {
     cudaGraphExec_t* slot = adjoint ? &base->adj_exec : &base->fwd_exec;

@@ -181,11 +181,12 @@ def test_disc_phantom_168_f64_full_size(dev):
 def test_vessel_512_full_size_prefix_and_dot(dev):
     # 512^2 heterogeneous absorbing medium, Nt = 2000, 512 line sensors: the launch configuration
     # the benchmark times.  Prefix of K samples vs the oracle (causality), adjoint of a residual
-    # supported on that prefix vs the oracle, and the dot identity over all 2000 samples.  K is past
-    # the first arrival at the sensor row (sources start >= 44 px from it, ~3.5 steps per px), so
-    # the compared data are not dominated by the pre-arrival noise floor.
+    # supported on that prefix vs the oracle, and the dot identity over all 2000 samples.  The first
+    # arrival at the sensor row is near step 300 (the phantom starts 76 px away, ~4 steps per px);
+    # K = 500 puts 200 steps of arrived signal in the prefix, so the comparison is not dominated by
+    # the pre-arrival floor (data ~1e-4 of the field, where FP32 rounding of the field dominates).
     pb = synth.vessel_phantom_2d()
-    K = 300
+    K = 500
     ref = Operator.from_problem(pb, Nt=K)
     op = _gpu_op(pb, "f32", dev)
     d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()

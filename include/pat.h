@@ -142,6 +142,35 @@ int pat_plan_probe_slots(const pat_plan* plan, int adjoint);
 pat_status pat_plan_probe_read(pat_plan* plan, int adjoint, int slot, const char** name, double* mean_ms,
                                int* samples);
 
+/* Size of the fixed device scratch array that pat_forward_static works in: 32 MiB in every GPU's
+ * memory, held from the first use of the library on that GPU until the process exits. */
+#define PAT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* pat_forward_static -- pat_forward for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a deployment variant of the same forward operator H.
+ *
+ * Some callers cannot call cudaMalloc: an application that hands the whole device to its own pool
+ * allocator and forbids any other device allocation, or a long-running service that must not
+ * allocate (and so risk fragmentation or an out-of-memory failure) once it is running.  This call
+ * computes exactly what pat_forward computes, with the same arguments, but allocates nothing:
+ * every device buffer it needs (medium tables, state fields, spectrum workspaces, sensor lists,
+ * the data record) is carved from one fixed array of PAT_STATIC_SCRATCH_BYTES that the library
+ * embeds as a device global.  It calls no cudaMalloc, cudaFree or allocating library routine and
+ * launches its kernels directly on `stream`; it returns after synchronising `stream`.
+ *   - The caller still passes p0 and data (host or device pointers, plan precision).
+ *   - A problem whose buffers do not fit in PAT_STATIC_SCRATCH_BYTES is rejected with PAT_EINVAL
+ *     before any device work (for scale: a 2-D 512^2 FP32 absorbing problem with Nt = 2000 and
+ *     512 sensors needs about 21 MB).
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture on the device.
+ *   - Every call on a device shares that device's array, and the array keeps the last call's
+ *     contents.  Calls that overlap on the same GPU (for example from several host threads) race
+ *     on it: serialise them. */
+pat_status pat_forward_static(const void* p0, const double* c, const double* rho, const double* alpha0,
+                              int alpha0_is_scalar, double y, const pat_grid* grid,
+                              const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
+                              void* data, void* stream);
+
 /* pat_last_error -- message describing the calling thread's last failed call ("" if none).
  * The pointer stays valid until the next pat_* call on the same thread. */
 const char* pat_last_error(void);

@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
     L.pat_forward.argtypes = [vp, dp, dp, dp, i32, f64, ctypes.POINTER(pat_grid), ctypes.POINTER(pat_sensors), f64, i32,
                               i32, vp, vp]
     L.pat_forward.restype = i32
+    L.pat_forward_static.argtypes = L.pat_forward.argtypes
+    L.pat_forward_static.restype = i32
     L.pat_plan_set_probe.argtypes = [vp, i32]
     L.pat_plan_set_probe.restype = i32
     L.pat_plan_probe_slots.argtypes = [vp, i32]

@@ -32,6 +32,11 @@ struct HostTables {
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st);
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
 pat_status plan_capture(PlanBase* base, bool adjoint);
+PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap, pat_status* st);
+pat_status plan_forward_direct(PlanBase* base, cudaStream_t s);
+pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,
+                        int alpha0_is_scalar, double y, const pat_sensors* sensors, double dt, int Nt,
+                        pat_precision prec, HostTables& h);
 pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, double* mean_ms, int* samples);
 
 }  // namespace pat

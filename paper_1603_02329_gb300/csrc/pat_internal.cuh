@@ -148,6 +148,10 @@ struct PlanBase {
     std::vector<cudaEvent_t> probe_ev[2];          // [graph][sample * (slots + 1) + k]
     std::vector<std::string> probe_names[2];       // slot names of one step
     int probe_samples[2] = {0, 0};
+    // When `arena` is set, every device buffer of the plan is carved from that caller-provided
+    // region instead of cudaMalloc, and the plan owns no stream or graph (direct launches only).
+    unsigned char* arena = nullptr;
+    size_t arena_cap = 0, arena_used = 0;
     void* img_ptr = nullptr;
     void* data_ptr = nullptr;
     size_t elem = 4;

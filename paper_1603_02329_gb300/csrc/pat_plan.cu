@@ -180,7 +180,7 @@ static void build_sensor_lists(std::vector<SensorEntry> e, int nlines, HostTable
     }
 }
 
-static pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,
+pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,
                                int alpha0_is_scalar, double y, const pat_sensors* sensors, double dt, int Nt,
                                pat_precision prec, HostTables& h) {
     if (!grid || !c || !rho || !alpha0 || !sensors) return fail(PAT_EINVAL, "NULL argument");

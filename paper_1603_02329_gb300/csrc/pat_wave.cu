@@ -13,10 +13,27 @@ template <typename T> struct Plan : public PlanBase {
     DevPlan<T> P{};
     HostTables H;   // kept for the FP64 tables' sizes and for rebuilding
     size_t row_smem = 0, spec_smem = 0;
+    bool count_only = false;   // arena sizing pass: bump offsets, touch no memory
 
     template <typename U> U* dalloc(size_t count, pat_status* st) {
         void* p = nullptr;
         if (count == 0) count = 1;
+        if (arena) {
+            const size_t off = (arena_used + 255) & ~(size_t)255;
+            const size_t bytes = count * sizeof(U);
+            if (count_only) {
+                arena_used = off + bytes;
+                return reinterpret_cast<U*>(arena + 0);
+            }
+            if (off + bytes > arena_cap) {
+                *st = PAT_EINVAL;
+                set_error("problem too large for the static scratch array (" + std::to_string(arena_cap) +
+                          " bytes): reduce the grid, Nt * Ns or the precision");
+                return nullptr;
+            }
+            arena_used = off + bytes;
+            return reinterpret_cast<U*>(arena + off);
+        }
         cudaError_t e = cudaMalloc(&p, count * sizeof(U));
         if (e != cudaSuccess) {
             *st = (e == cudaErrorMemoryAllocation) ? PAT_ENOMEM : PAT_ECUDA;
@@ -30,6 +47,7 @@ template <typename T> struct Plan : public PlanBase {
     template <typename U, typename V> const U* upload(const std::vector<V>& v, pat_status* st) {
         U* d = dalloc<U>(v.size(), st);
         if (!d) return nullptr;
+        if (count_only) return d;
         std::vector<U> tmp(v.size());
         for (size_t i = 0; i < v.size(); ++i) tmp[i] = static_cast<U>(v[i]);
         if (!v.empty()) {
@@ -44,6 +62,7 @@ template <typename T> struct Plan : public PlanBase {
     const cplx<T>* upload_c(const std::vector<std::complex<double>>& v, pat_status* st) {
         cplx<T>* d = dalloc<cplx<T>>(v.size(), st);
         if (!d) return nullptr;
+        if (count_only) return d;
         std::vector<cplx<T>> tmp(v.size());
         for (size_t i = 0; i < v.size(); ++i) tmp[i] = mkc<T>((T)v[i].real(), (T)v[i].imag());
         if (!v.empty()) {
@@ -57,6 +76,7 @@ template <typename T> struct Plan : public PlanBase {
     }
 
     ~Plan() override {
+        if (arena) return;   // nothing owned on the device: the caller synchronised its stream
         if (cap_stream) cudaStreamSynchronize(cap_stream);
         cudaDeviceSynchronize();
         if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
@@ -155,9 +175,11 @@ template <typename T> struct Plan : public PlanBase {
         row_smem = (size_t)(h.nx + 2 * qmax * h.nx) * sizeof(cplx<T>);
         const int L = std::max(h.ny, h.nz);
         spec_smem = (size_t)(L + 3 * L * cfg.col_w) * sizeof(cplx<T>);
+        if (count_only) return PAT_OK;
         if (D == 2) st = set_attrs<2>();
         else st = set_attrs<3>();
         if (st != PAT_OK) return st;
+        if (arena) return PAT_OK;
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
         return PAT_OK;
@@ -338,8 +360,26 @@ template <typename T> struct Plan : public PlanBase {
     }
 };
 
-template <typename T> PlanBase* make_plan(const HostTables& h, pat_status* st) {
+template <typename T> PlanBase* make_plan(const HostTables& h, pat_status* st, unsigned char* arena = nullptr,
+                                          size_t arena_cap = 0) {
+    if (arena) {
+        // sizing pass: reject a problem that does not fit before any device memory is touched
+        Plan<T> sizing;
+        sizing.arena = arena;
+        sizing.arena_cap = arena_cap;
+        sizing.count_only = true;
+        *st = sizing.build(h);
+        if (*st != PAT_OK) return nullptr;
+        if (sizing.arena_used > arena_cap) {
+            *st = PAT_EINVAL;
+            set_error("problem too large for the static scratch array: needs " + std::to_string(sizing.arena_used) +
+                      " bytes, the array holds " + std::to_string(arena_cap));
+            return nullptr;
+        }
+    }
     Plan<T>* p = new Plan<T>();
+    p->arena = arena;
+    p->arena_cap = arena_cap;
     p->info = h.info;
     cudaGetDevice(&p->device);
     *st = p->build(h);
@@ -352,6 +392,24 @@ template <typename T> PlanBase* make_plan(const HostTables& h, pat_status* st) {
 
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st) { return make_plan<float>(h, st); }
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st) { return make_plan<double>(h, st); }
+
+PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap, pat_status* st) {
+    if (h.info.precision == PAT_F32) return make_plan<float>(h, st, arena, cap);
+    return make_plan<double>(h, st, arena, cap);
+}
+
+template <typename T> static pat_status run_direct_t(Plan<T>* p, cudaStream_t s) {
+    if (p->P.d == 2) p->template record_forward<2>(s);
+    else p->template record_forward<3>(s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PAT_OK;
+}
+
+pat_status plan_forward_direct(PlanBase* base, cudaStream_t s) {
+    if (base->info.precision == PAT_F32) return run_direct_t(static_cast<Plan<float>*>(base), s);
+    return run_direct_t(static_cast<Plan<double>*>(base), s);
+}
 
 pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, double* mean_ms, int* samples) {
     const int slots = (int)b->probe_names[g].size();

@@ -90,6 +90,12 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
     return table.get(name)
 
 
+def solve_bytes(N, Nt, w, D=2, lossy=True):
+    # one whole solve (persistent kernel): state (u_xi, rho_xi, p) read + written once and the
+    # medium read once per grid-point-step
+    return (2 * (2 * D + 1) + (4 if lossy else 2)) * w * N * Nt
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -302,7 +308,10 @@ def main():
             kernels[f"{tag}:{name}"] = sm / max(cnt, 1)
         dom = max(kernels, key=lambda k: kernels[k])
         tag, name = dom.split(":")
-        b = kernel_bytes(name, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
+        if name.startswith("k_persist"):
+            b = solve_bytes(pb.N, pb.Nt, w, D=len(pb.shape), lossy=op.lossy)
+        else:
+            b = kernel_bytes(name, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
         ms = kernels[dom]
         ach = b / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
@@ -315,12 +324,14 @@ def main():
                  "frac": value * B_pt / world / peak}
 
     slots_f = 6 if op.lossy else 4
-    launches = args.steps * 2 * (1 + (pb.Nt - 1) * slots_f)
+    persistent = int(op.info.path) == 1
+    launches = args.steps * 2 * (1 if persistent else (1 + (pb.Nt - 1) * slots_f))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
-                          parallelism=f"replicas x{world}"),
+                          parallelism=f"replicas x{world}",
+                          path="persistent kernel per solve" if persistent else "CUDA graph of per-phase kernels"),
            "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels,
            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -83,6 +83,7 @@ typedef struct {
     pat_precision precision;
     double dt;
     double c_ref;       /* max sound speed (kappa correction, PML scaling) */
+    int path;           /* 0: CUDA graph of per-phase kernels; 1: one persistent kernel per solve */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).
@@ -130,6 +131,11 @@ pat_status pat_forward(const void* p0, const double* c, const double* rho, const
                        int alpha0_is_scalar, double y, const pat_grid* grid,
                        const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
                        void* data, void* stream);
+
+/* pat_plan_status -- synchronise the device and return the status word of the plan's last solve:
+ * PAT_OK, or PAT_ETIMEOUT if a bounded device-side wait (the grid barrier of the persistent
+ * kernel) ran out; the kernel then stopped early and its outputs are not valid. */
+pat_status pat_plan_status(pat_plan* plan);
 
 /* Kernel-timing probe (tracing).  With stride S > 0, the next captured graphs bracket every kernel
  * launch of every S-th time step (starting at step S/2) with CUDA events; after a solve has

@@ -29,7 +29,7 @@ class pat_sensors(ctypes.Structure):
 class pat_plan_info_t(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("N", ctypes.c_int64), ("Ns", ctypes.c_int),
                 ("Nt", ctypes.c_int), ("lossy", ctypes.c_int), ("precision", ctypes.c_int),
-                ("dt", ctypes.c_double), ("c_ref", ctypes.c_double)]
+                ("dt", ctypes.c_double), ("c_ref", ctypes.c_double), ("path", ctypes.c_int)]
 
 
 class PatError(RuntimeError):
@@ -68,6 +68,8 @@ def lib() -> ctypes.CDLL:
     L.pat_forward.restype = i32
     L.pat_forward_static.argtypes = L.pat_forward.argtypes
     L.pat_forward_static.restype = i32
+    L.pat_plan_status.argtypes = [vp]
+    L.pat_plan_status.restype = i32
     L.pat_plan_set_probe.argtypes = [vp, i32]
     L.pat_plan_set_probe.restype = i32
     L.pat_plan_probe_slots.argtypes = [vp, i32]

@@ -144,13 +144,12 @@ template <typename T, int R, bool INV> __device__ __forceinline__ void dft(cplx<
     else dft_odd<T, R, INV>(v);
 }
 
-// One Stockham butterfly: j in [0, n/R), Ns = product of the radices of earlier stages.
-// src/dst point at the line start; element e of the line lives at [e * es].
+// One Stockham butterfly: j in [0, n/R), k = j mod Ns with Ns = product of the radices of earlier
+// stages.  src/dst point at the line start; element e of the line lives at [e * es].
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void stockham_bfly(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
-                                              int j, int m, int Ns, int twstep,
+                                              int j, int k, int m, int Ns, int twstep,
                                               const cplx<T>* __restrict__ tw, int es) {
-    const int k = j % Ns;
     cplx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es];
@@ -167,13 +166,24 @@ __device__ __forceinline__ void stockham_bfly(const cplx<T>* __restrict__ src, c
     for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];
 }
 
-// Transform `nlines` lines held in shared memory.  Line l starts at a + l * ls; element stride es.
-// `lines_fast` maps consecutive threads to consecutive lines (for column tiles, es > 1) rather
-// than to consecutive butterflies of one line.  Returns the buffer holding the result (a or b).
-// The caller must __syncthreads() before (inputs written) and the routine ends synchronised.
 template <typename T, bool INV>
-__device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, const FftAxis& ax, const cplx<T>* tw,
-                              int nlines, int es, int ls, bool lines_fast) {
+__device__ __forceinline__ void bfly_dispatch(int R, const cplx<T>* src, cplx<T>* dst, int j, int k, int m, int Ns,
+                                              int twstep, const cplx<T>* tw, int es) {
+    switch (R) {
+        case 8: stockham_bfly<T, 8, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+        case 4: stockham_bfly<T, 4, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+        case 2: stockham_bfly<T, 2, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+        case 3: stockham_bfly<T, 3, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+        case 5: stockham_bfly<T, 5, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+        default: stockham_bfly<T, 7, INV>(src, dst, j, k, m, Ns, twstep, tw, es); break;
+    }
+}
+
+// Transform `nlines` contiguous lines (line l at a + l n).  Consecutive threads take consecutive
+// butterflies of a line.  Returns the buffer holding the result (a or b).  The caller must
+// __syncthreads() before; the routine ends synchronised.
+template <typename T, bool INV>
+__device__ cplx<T>* fft_rows(cplx<T>* a, cplx<T>* b, const FftAxis& ax, const cplx<T>* tw, int nlines) {
     const int n = ax.n;
     int Ns = 1;
     for (int s = 0; s < ax.nst; ++s) {
@@ -182,29 +192,55 @@ __device__ cplx<T>* fft_lines(cplx<T>* a, cplx<T>* b, const FftAxis& ax, const c
         const int twstep = n / (Ns * R);
         const int total = nlines * m;
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            int line, j;
-            if (lines_fast) {
-                line = t % nlines;
-                j = t / nlines;
+            int line, j, k;
+            if (ax.pow2) {
+                const int lgm = ax.lgn - ax.lgr[s];
+                line = t >> lgm;
+                j = t & (m - 1);
+                k = j & (Ns - 1);
             } else {
-                j = t % m;
                 line = t / m;
+                j = t - line * m;
+                k = j % Ns;
             }
-            const cplx<T>* src = a + line * ls;
-            cplx<T>* dst = b + line * ls;
-            switch (R) {
-                case 2: stockham_bfly<T, 2, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-                case 3: stockham_bfly<T, 3, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-                case 4: stockham_bfly<T, 4, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-                case 5: stockham_bfly<T, 5, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-                case 7: stockham_bfly<T, 7, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-                default: stockham_bfly<T, 8, INV>(src, dst, j, m, Ns, twstep, tw, es); break;
-            }
+            bfly_dispatch<T, INV>(R, a + line * n, b + line * n, j, k, m, Ns, twstep, tw, 1);
         }
         __syncthreads();
-        cplx<T>* t = a;
+        cplx<T>* tmp = a;
         a = b;
-        b = t;
+        b = tmp;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Transform `nl` interleaved lines (element e of line l at a[l + e nl]).  Consecutive threads
+// take consecutive lines.  lgnl = log2(nl) when nl is a power of two, else -1.
+template <typename T, bool INV>
+__device__ cplx<T>* fft_cols(cplx<T>* a, cplx<T>* b, const FftAxis& ax, const cplx<T>* tw, int nl, int lgnl) {
+    const int n = ax.n;
+    int Ns = 1;
+    for (int s = 0; s < ax.nst; ++s) {
+        const int R = ax.rad[s];
+        const int m = n / R;
+        const int twstep = n / (Ns * R);
+        const int total = nl * m;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int line, j;
+            if (lgnl >= 0) {
+                line = t & (nl - 1);
+                j = t >> lgnl;
+            } else {
+                j = t / nl;
+                line = t - j * nl;
+            }
+            const int k = ax.pow2 ? (j & (Ns - 1)) : (j % Ns);
+            bfly_dispatch<T, INV>(R, a + line, b + line, j, k, m, Ns, twstep, tw, nl);
+        }
+        __syncthreads();
+        cplx<T>* tmp = a;
+        a = b;
+        b = tmp;
         Ns *= R;
     }
     return a;

@@ -19,12 +19,13 @@ struct HostTables {
     std::vector<double> c2, rho0, b[3], c2tau, c2eta;
     std::vector<double> a[3], au[3];
     std::vector<std::complex<double>> dp[3], dm[3], tw[3];
-    std::vector<double> kapN, kpa, kpb;
+    std::vector<double> kv[3];
+    double kap_a = 0.0, pha = 0.0, phb = 0.0, invN = 0.0;
     FftAxis fx{}, fy{}, fz{};
 
     // sensors (see DevSensors)
-    std::vector<int> g_lineptr, g_seg_line, g_seg_sensor, g_seg_e0, g_ent_x;
-    std::vector<double> g_ent_w;
+    std::vector<int> g_lineptr, g_seg_line, g_seg_sensor, g_seg_x0;
+    std::vector<double> g_seg_w0, g_seg_w1;
     std::vector<int> s_lineptr, s_seg_line, s_seg_x, s_seg_e0, s_ent_sensor;
     std::vector<double> s_ent_w;
 };
@@ -32,6 +33,7 @@ struct HostTables {
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st);
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
 pat_status plan_capture(PlanBase* base, bool adjoint);
+pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s);
 PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap, pat_status* st);
 pat_status plan_forward_direct(PlanBase* base, cudaStream_t s);
 pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,

@@ -51,6 +51,9 @@ struct FftAxis {
     int n;
     int nst;
     int rad[kMaxStages];
+    int pow2;              // n is a power of two: every index operation is a shift or a mask
+    int lgn;               // log2(n) when pow2
+    int lgr[kMaxStages];   // log2(rad[s]) when pow2
 };
 
 // Maximum line length handled by the shared-memory FFT.
@@ -61,13 +64,14 @@ constexpr int kMaxFftLen = 1024;
 // ------------------------------------------------------------------------------------------
 template <typename T> struct DevSensors {
     int Ns;
-    // forward gather: segments grouped by (line, sensor); one atomic add per segment
+    // forward gather: segments grouped by (line, sensor); weights w0 at x0 and w1 at x0 + 1
+    // (w1 = 0 for a single entry); one atomic add per segment
     const int* g_lineptr;   // [nlines + 1] -> segment range
     const int* g_seg_line;  // [nseg]
     const int* g_seg_sensor;
-    const int* g_seg_e0;    // [nseg + 1] -> entry range
-    const int* g_ent_x;     // [nent]
-    const T* g_ent_w;
+    const int* g_seg_x0;
+    const T* g_seg_w0;
+    const T* g_seg_w1;
     // adjoint scatter: segments grouped by (line, x); entries (sensor, weight)
     const int* s_lineptr;
     const int* s_seg_line;
@@ -88,6 +92,7 @@ template <typename T> struct DevPlan {
     int nlines;       // ny * nz x-lines
     long long N;      // nx * ny * nz
     int lossy;
+    int Nt;
     T dt;
 
     // medium (N each)
@@ -99,13 +104,14 @@ template <typename T> struct DevPlan {
     // PML factors per axis: a at normal points, au at staggered points
     const T* a[3];
     const T* au[3];
-    // k-space: staggered derivative symbols per axis (i k e^{+-i k dx/2}), scaled kappa and
-    // fractional Laplacian symbols on the half spectrum [nz][ny][nxh] (all include 1/N)
+    // k-space: per-axis wavenumbers and staggered derivative symbols i k e^{+-i k dx/2}
+    // (x: half spectrum 0..nx/2; y, z: full); kappa and |k|^s are evaluated from these
+    const T* kv[3];
     const cplx<T>* dp[3];
     const cplx<T>* dm[3];
-    const T* kapN;
-    const T* kpa;     // |k|^(y-2) / N
-    const T* kpb;     // |k|^(y-1) / N
+    T kap_a;          // c_ref dt / 2  (kappa = sinc(kap_a |k|))
+    T pha, phb;       // (y - 2) / 2, (y - 1) / 2: exponents applied to |k|^2
+    T invN;           // 1 / N (inverse-transform scaling)
     // FFT plans and twiddles exp(-2 pi i m / n) per axis
     FftAxis fx, fy, fz;
     const cplx<T>* twx;
@@ -155,6 +161,11 @@ struct PlanBase {
     void* img_ptr = nullptr;
     void* data_ptr = nullptr;
     size_t elem = 4;
+    // persistent single-kernel path (2-D): grid size, barrier/status words [count, -, status, -]
+    int persistent = 0;
+    int persist_grid = 0;
+    size_t persist_smem = 0;
+    unsigned* gbar = nullptr;
 };
 
 // error reporting (thread-local message)

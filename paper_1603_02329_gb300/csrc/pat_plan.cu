@@ -8,6 +8,7 @@
 //   FFT twiddles and radix plans, and the sensor interpolation lists (Sec. III, Sec. VI.A).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -45,7 +46,16 @@ static bool factor_axis(int n, FftAxis* ax) {
             m /= r;
         }
     }
-    return m == 1;
+    if (m != 1) return false;
+    ax->pow2 = (n & (n - 1)) == 0;
+    ax->lgn = 0;
+    while ((1 << ax->lgn) < n) ++ax->lgn;
+    for (int s = 0; s < ax->nst; ++s) {
+        int l = 0;
+        while ((1 << l) < ax->rad[s]) ++l;
+        ax->lgr[s] = l;
+    }
+    return true;
 }
 
 static std::vector<std::complex<double>> twiddles(int n) {
@@ -124,25 +134,29 @@ static pat_status sensor_entries(const pat_grid& g, const pat_sensors& s, std::v
 }
 
 static void build_sensor_lists(std::vector<SensorEntry> e, int nlines, HostTables& h) {
-    // gather: segments by (line, sensor)
+    // gather: segments by (line, sensor), weights at x0 and x0 + 1
     std::sort(e.begin(), e.end(), [](const SensorEntry& a, const SensorEntry& b) {
         return std::tie(a.line, a.sensor, a.x) < std::tie(b.line, b.sensor, b.x);
     });
     h.g_seg_line.clear();
     h.g_seg_sensor.clear();
-    h.g_seg_e0.clear();
-    h.g_ent_x.clear();
-    h.g_ent_w.clear();
-    for (size_t k = 0; k < e.size(); ++k) {
-        if (k == 0 || e[k].line != e[k - 1].line || e[k].sensor != e[k - 1].sensor) {
-            h.g_seg_line.push_back(e[k].line);
-            h.g_seg_sensor.push_back(e[k].sensor);
-            h.g_seg_e0.push_back((int)k);
+    h.g_seg_x0.clear();
+    h.g_seg_w0.clear();
+    h.g_seg_w1.clear();
+    for (size_t k = 0; k < e.size();) {
+        h.g_seg_line.push_back(e[k].line);
+        h.g_seg_sensor.push_back(e[k].sensor);
+        h.g_seg_x0.push_back(e[k].x);
+        h.g_seg_w0.push_back(e[k].w);
+        if (k + 1 < e.size() && e[k + 1].line == e[k].line && e[k + 1].sensor == e[k].sensor &&
+            e[k + 1].x == e[k].x + 1) {
+            h.g_seg_w1.push_back(e[k + 1].w);
+            k += 2;
+        } else {
+            h.g_seg_w1.push_back(0.0);
+            k += 1;
         }
-        h.g_ent_x.push_back(e[k].x);
-        h.g_ent_w.push_back(e[k].w);
     }
-    h.g_seg_e0.push_back((int)e.size());
     h.g_lineptr.assign(nlines + 1, 0);
     {
         size_t s = 0;
@@ -205,7 +219,7 @@ pat_status build_tables(const pat_grid* grid, const double* c, const double* rho
     h.ny = g.n[1];
     h.nz = (d == 3) ? g.n[2] : 1;
     h.nxh = h.nx / 2 + 1;
-    h.ldh = (h.nxh + 3) / 4 * 4;
+    h.ldh = (h.nxh + 7) / 8 * 8;
     h.N = (long long)h.nx * h.ny * h.nz;
     h.Nt = Nt;
     h.Ns = sensors->count;
@@ -279,29 +293,14 @@ pat_status build_tables(const pat_grid* grid, const double* c, const double* rho
             h.dm[a][m] = std::complex<double>(k * sn, k * cs);   // i k e^{-i k h/2}
         }
     }
-    const size_t Nk = (size_t)h.nz * h.ny * h.nxh;
-    h.kapN.resize(Nk);
-    if (lossy) {
-        h.kpa.resize(Nk);
-        h.kpb.resize(Nk);
+    for (int a = 0; a < 3; ++a) {
+        h.kv[a].resize(klen[a]);
+        for (int m = 0; m < klen[a]; ++m) h.kv[a][m] = (a < d) ? kbin(m, n3[a], h3[a]) : 0.0;
     }
-    const double invN = 1.0 / (double)h.N;
-    for (int kz = 0; kz < h.nz; ++kz)
-        for (int ky = 0; ky < h.ny; ++ky)
-            for (int kx = 0; kx < h.nxh; ++kx) {
-                const double vx = kbin(kx, h.nx, h3[0]);
-                const double vy = kbin(ky, h.ny, h3[1]);
-                const double vz = (d == 3) ? kbin(kz, h.nz, h3[2]) : 0.0;
-                const double km = std::sqrt(vx * vx + vy * vy + vz * vz);
-                const double zarg = cmax * km * dt / 2.0;
-                const double kap = (zarg == 0.0) ? 1.0 : std::sin(zarg) / zarg;
-                const size_t idx = ((size_t)kz * h.ny + ky) * h.nxh + kx;
-                h.kapN[idx] = kap * invN;
-                if (lossy) {
-                    h.kpa[idx] = (km > 0.0) ? std::pow(km, y - 2.0) * invN : 0.0;
-                    h.kpb[idx] = (km > 0.0) ? std::pow(km, y - 1.0) * invN : 0.0;
-                }
-            }
+    h.kap_a = cmax * dt / 2.0;
+    h.pha = (y - 2.0) / 2.0;
+    h.phb = (y - 1.0) / 2.0;
+    h.invN = 1.0 / (double)h.N;
     // FFT plans
     if (!factor_axis(h.nx, &h.fx) || !factor_axis(h.ny, &h.fy) || !factor_axis(h.nz, &h.fz))
         return fail(PAT_EUNSUPPORTED, "FFT lengths must factor into 2, 3, 5, 7");
@@ -319,9 +318,21 @@ pat_status build_tables(const pat_grid* grid, const double* c, const double* rho
     h.cfg.col_threads = 256;
     const size_t cbytes = (prec == PAT_F32) ? 8 : 16;
     const int L = std::max(h.ny, h.nz);
-    int w = 4;
-    while (w > 1 && (size_t)(L + 3 * L * w) * cbytes > 160 * 1024) w /= 2;
+    // columns per spectral CTA: 16-byte rows (2 complex floats or 1 complex double) keep more
+    // CTAs in flight on small grids; overridable for tuning
+    int w = (prec == PAT_F32) ? 2 : 1;
+    if (const char* env = std::getenv("PAT_COL_W")) w = std::max(1, std::atoi(env));
+    int p2 = 1;
+    while (p2 * 2 <= w && p2 < 8) p2 *= 2;   // a power of two, at most 8
+    w = p2;
+    while (w > 1 && (size_t)(3 * L + 16 + 3 * d * L * w) * cbytes > 180 * 1024) w /= 2;
     h.cfg.col_w = w;
+    // threads: one radix-8 butterfly per thread for the widest interleaved batch (d W lines)
+    h.cfg.col_threads = std::min(256, std::max(64, (d * w * L / 8 + 31) / 32 * 32));
+    if (const char* env = std::getenv("PAT_ROW_LINES")) {
+        const int r = std::atoi(env);
+        if (r >= 2 && r % 2 == 0 && (h.ny * h.nz) % r == 0) h.cfg.row_lines = r;
+    }
     // info
     pat_plan_info_t& inf = h.info;
     std::memset(&inf, 0, sizeof(inf));
@@ -397,14 +408,19 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
     PlanBase* b = plan->impl;
     DeviceGuard g(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    pat_status st = plan_capture(b, false);
+    pat_status st = b->persistent ? PAT_OK : plan_capture(b, false);
     if (st != PAT_OK) return st;
     const size_t nimg = (size_t)b->info.N * b->elem;
     const size_t ndat = (size_t)b->info.Nt * b->info.Ns * b->elem;
     cudaError_t e = cudaMemcpyAsync(b->img_ptr, p0, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy p0");
-    e = cudaGraphLaunch(b->fwd_exec, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (forward)");
+    if (b->persistent) {
+        st = plan_run_persistent(b, false, s);
+        if (st != PAT_OK) return st;
+    } else {
+        e = cudaGraphLaunch(b->fwd_exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (forward)");
+    }
     e = cudaMemcpyAsync(data, b->data_ptr, ndat, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy data");
     return PAT_OK;
@@ -416,14 +432,19 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
     PlanBase* b = plan->impl;
     DeviceGuard g(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    pat_status st = plan_capture(b, true);
+    pat_status st = b->persistent ? PAT_OK : plan_capture(b, true);
     if (st != PAT_OK) return st;
     const size_t nimg = (size_t)b->info.N * b->elem;
     const size_t ndat = (size_t)b->info.Nt * b->info.Ns * b->elem;
     cudaError_t e = cudaMemcpyAsync(b->data_ptr, residual, ndat, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy residual");
-    e = cudaGraphLaunch(b->adj_exec, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (adjoint)");
+    if (b->persistent) {
+        st = plan_run_persistent(b, true, s);
+        if (st != PAT_OK) return st;
+    } else {
+        e = cudaGraphLaunch(b->adj_exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (adjoint)");
+    }
     e = cudaMemcpyAsync(grad, b->img_ptr, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy gradient");
     return PAT_OK;
@@ -458,6 +479,24 @@ pat_status pat_plan_set_probe(pat_plan* plan, int stride) {
     if (b->adj_exec) cudaGraphExecDestroy(b->adj_exec);
     b->fwd_exec = b->adj_exec = nullptr;
     b->probe_stride = stride;
+    return PAT_OK;
+}
+
+pat_status pat_plan_status(pat_plan* plan) {
+    set_error("");
+    if (!plan) return fail(PAT_EINVAL, "NULL argument");
+    PlanBase* b = plan->impl;
+    DeviceGuard g(b->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (!b->gbar) return PAT_OK;
+    unsigned w[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(w, b->gbar, sizeof(w), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status word");
+    if (w[2] != 0) {
+        set_error("a bounded device-side wait ran out (grid barrier of the persistent kernel)");
+        return (pat_status)w[2];
+    }
     return PAT_OK;
 }
 

@@ -2,10 +2,12 @@
 // and its exact transpose H^T (Sec. III).  The whole Nt-step loop of one solve is captured once
 // per plan into a CUDA graph and replayed with a single cudaGraphLaunch per call.
 #include <algorithm>
+#include <cstdlib>
+#include <cstdio>
 #include <cstring>
 
 #include "pat_host.h"
-#include "pat_kernels.cuh"
+#include "pat_persist.cuh"
 
 namespace pat {
 
@@ -102,11 +104,17 @@ template <typename T> struct Plan : public PlanBase {
         P.N = h.N;
         P.lossy = h.lossy;
         P.dt = (T)h.dt;
+        P.Nt = h.Nt;
         const size_t N = (size_t)h.N;
         const size_t Nh = (size_t)h.nz * h.ny * h.ldh;
 #define CHK(x) \
     do {       \
         if (!(x)) return st; \
+    } while (0)
+#define CHK2(x)                          \
+    do {                                 \
+        pat_status s2_ = (x);            \
+        if (s2_ != PAT_OK) return s2_;   \
     } while (0)
         CHK(P.c2 = upload<T>(h.c2, &st));
         CHK(P.rho0 = upload<T>(h.rho0, &st));
@@ -121,10 +129,12 @@ template <typename T> struct Plan : public PlanBase {
         if (h.lossy) {
             CHK(P.c2tau = upload<T>(h.c2tau, &st));
             CHK(P.c2eta = upload<T>(h.c2eta, &st));
-            CHK(P.kpa = upload<T>(h.kpa, &st));
-            CHK(P.kpb = upload<T>(h.kpb, &st));
         }
-        CHK(P.kapN = upload<T>(h.kapN, &st));
+        for (int a = 0; a < 3; ++a) CHK(P.kv[a] = upload<T>(h.kv[a], &st));
+        P.kap_a = (T)h.kap_a;
+        P.pha = (T)h.pha;
+        P.phb = (T)h.phb;
+        P.invN = (T)h.invN;
         P.fx = h.fx;
         P.fy = h.fy;
         P.fz = h.fz;
@@ -159,9 +169,9 @@ template <typename T> struct Plan : public PlanBase {
         CHK(S.g_lineptr = upload<int>(h.g_lineptr, &st));
         CHK(S.g_seg_line = upload<int>(h.g_seg_line, &st));
         CHK(S.g_seg_sensor = upload<int>(h.g_seg_sensor, &st));
-        CHK(S.g_seg_e0 = upload<int>(h.g_seg_e0, &st));
-        CHK(S.g_ent_x = upload<int>(h.g_ent_x, &st));
-        CHK(S.g_ent_w = upload<T>(h.g_ent_w, &st));
+        CHK(S.g_seg_x0 = upload<int>(h.g_seg_x0, &st));
+        CHK(S.g_seg_w0 = upload<T>(h.g_seg_w0, &st));
+        CHK(S.g_seg_w1 = upload<T>(h.g_seg_w1, &st));
         CHK(S.s_lineptr = upload<int>(h.s_lineptr, &st));
         CHK(S.s_seg_line = upload<int>(h.s_seg_line, &st));
         CHK(S.s_seg_x = upload<int>(h.s_seg_x, &st));
@@ -171,17 +181,119 @@ template <typename T> struct Plan : public PlanBase {
 #undef CHK
         // launch configuration
         cfg = h.cfg;
-        const int qmax = std::max(D, 2) * cfg.row_lines / 2;
-        row_smem = (size_t)(h.nx + 2 * qmax * h.nx) * sizeof(cplx<T>);
-        const int L = std::max(h.ny, h.nz);
-        spec_smem = (size_t)(L + 3 * L * cfg.col_w) * sizeof(cplx<T>);
+        row_smem = row_smem_bytes<T>(D, h.nx, h.ldh, cfg.row_lines);
+        spec_smem = spec_smem_bytes<T>(D, std::max(h.ny, h.nz), cfg.col_w);
         if (count_only) return PAT_OK;
+        // padding columns of the half spectra are read (never used) by full-width tiles: zero them
+        for (int a = 0; a < nspec; ++a) {
+            cudaError_t e = cudaMemset(P.spec[a], 0, Nh * sizeof(cplx<T>));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (spectra)");
+        }
         if (D == 2) st = set_attrs<2>();
         else st = set_attrs<3>();
         if (st != PAT_OK) return st;
         if (arena) return PAT_OK;
+        CHK2(configure_persistent(h));
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        return PAT_OK;
+    }
+
+    // ---------------------------------------------------------------------------------------
+    // persistent single-kernel path (2-D grids whose per-CTA state fits in shared memory)
+    // ---------------------------------------------------------------------------------------
+    PersistCfg pcfg{};
+
+    pat_status configure_persistent(const HostTables& h) {
+        persistent = 0;
+        const char* env = std::getenv("PAT_PERSIST");
+        if (env && std::atoi(env) == 0) return PAT_OK;
+        if (h.d != 2) return PAT_OK;
+        int W = (sizeof(T) == 4) ? 2 : 1;   // 16-byte rows: the tiles are read around L1
+        int lgW = (W == 2) ? 1 : 0;
+        const int ntiles = (h.nxh + W - 1) / W;
+        const int npairs = h.ny / 2;
+        const int ppc = (npairs + ntiles - 1) / ntiles;
+        const int G = std::max(ntiles, (npairs + ppc - 1) / ppc);
+        pcfg.W = W;
+        pcfg.lgW = lgW;
+        pcfg.ntiles = ntiles;
+        pcfg.ppc = ppc;
+        pcfg.rmax = 2 * ppc;
+        pcfg.nres = 11;
+        const size_t smem = persist_smem_bytes<T>(h.nx, h.ny, h.ldh, pcfg.rmax, W, pcfg.nres);
+        int dev = 0, optin = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        const bool dbg = std::getenv("PAT_DEBUG") != nullptr;
+        if (dbg)
+            fprintf(stderr, "[pat] persistent: G=%d W=%d ppc=%d smem=%zu optin=%d nsm=%d coop=%d\n", G, W, ppc, smem,
+                    optin, nsm, coop);
+        if (!coop || smem > (size_t)optin) return PAT_OK;
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_persist<T, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)k_persist<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) {
+            if (dbg) fprintf(stderr, "[pat] persistent: set attribute failed: %s\n", cudaGetErrorString(e));
+            cudaGetLastError();
+            return PAT_OK;
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T, false>, 256, smem);
+        if (dbg) fprintf(stderr, "[pat] persistent: per_sm=%d (%s)\n", per_sm, cudaGetErrorString(e));
+        if (e != cudaSuccess || per_sm * nsm < G) {
+            cudaGetLastError();
+            return PAT_OK;
+        }
+        pat_status st = PAT_OK;
+        gbar = dalloc<unsigned>(4, &st);
+        if (!gbar) return st;
+        persist_grid = G;
+        persist_smem = smem;
+        persistent = 1;
+        info.path = 1;
+        return PAT_OK;
+    }
+
+    pat_status run_persistent(bool adjoint, cudaStream_t s) {
+        cudaError_t e;
+        if (!adjoint) {
+            e = cudaMemsetAsync(P.data, 0, (size_t)H.Nt * H.Ns * sizeof(T), s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (data)");
+        }
+        e = cudaMemsetAsync(gbar, 0, 4 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (barrier)");
+        const int g = adjoint ? 1 : 0;
+        if (probe_stride > 0) {
+            if (probe_ev[g].size() < 2) {
+                for (cudaEvent_t ev : probe_ev[g]) cudaEventDestroy(ev);
+                probe_ev[g].assign(2, nullptr);
+                cudaEventCreate(&probe_ev[g][0]);
+                cudaEventCreate(&probe_ev[g][1]);
+            }
+            probe_names[g].assign(1, adjoint ? "k_persist_adj" : "k_persist_fwd");
+            probe_samples[g] = 1;
+            cudaEventRecord(probe_ev[g][0], s);
+        }
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(persist_grid);
+        lc.blockDim = dim3(256);
+        lc.dynamicSmemBytes = persist_smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (adjoint) e = cudaLaunchKernelEx(&lc, k_persist<T, true>, P, pcfg, gbar);
+        else e = cudaLaunchKernelEx(&lc, k_persist<T, false>, P, pcfg, gbar);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernelEx (persistent)");
+        if (probe_stride > 0) cudaEventRecord(probe_ev[g][1], s);
         return PAT_OK;
     }
 
@@ -210,14 +322,34 @@ template <typename T> struct Plan : public PlanBase {
     }
 
     // ---------------------------------------------------------------------------------------
-    // launch helpers (used while capturing)
+    // launch helpers (used while capturing, or directly on a stream)
     // ---------------------------------------------------------------------------------------
     int row_grid() const { return P.nlines / cfg.row_lines; }
+
+    // Every kernel is launched with programmatic stream serialization: it may start (and run
+    // its constant-data prologue) while its predecessor finishes; griddepcontrol.wait in the
+    // kernel orders everything that depends on earlier kernels.
+    template <typename... KArgs, typename... Args>
+    void launch(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = grid;
+        lc.blockDim = dim3(block);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        cudaLaunchKernelEx(&lc, kern, args...);
+    }
 
     template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F) {
         const int tiles = (P.nxh + cfg.col_w - 1) / cfg.col_w;
         const int outer = (lax == 1) ? P.nz : P.ny;
-        k_spec<T, D, MODE><<<dim3(tiles, outer), cfg.col_threads, spec_smem, s>>>(P, cfg.col_w, lax, F);
+        int lgw = 0;
+        while ((1 << lgw) < cfg.col_w) ++lgw;
+        launch(k_spec<T, D, MODE>, dim3(tiles, outer), cfg.col_threads, spec_smem, s, P, cfg.col_w, lgw, lax, F);
     }
 
     template <int D, int MODE> void spectral(cudaStream_t s) {
@@ -286,21 +418,21 @@ template <typename T> struct Plan : public PlanBase {
         probe_names[0].clear();
         probe_samples[0] = 0;
         cudaMemsetAsync(P.data, 0, (size_t)Nt * Ns * sizeof(T), s);
-        k_fwd_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1);
+        launch(k_fwd_init<T, D>, dim3(G), B, row_smem, s, P, R, (int)(Nt == 1));
         for (int n = 0; n + 1 < Nt; ++n) {
             const int last = (n + 2 == Nt);
             T* row = P.data + (size_t)(n + 1) * Ns;
             if (sampled(n, Nt)) begin_sample(0, probe_samples[0]++ == 0);
             spectral_named<D, SPEC_GRAD>(s, "spec_grad");
             mark(s, "fwd_u");
-            k_fwd_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
+            launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
             spectral_named<D, SPEC_DIV>(s, "spec_div");
             mark(s, "fwd_rho");
-            k_fwd_rho<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
+            launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, P, R, last, row);
             if (P.lossy) {
                 spectral_named<D, SPEC_ABS>(s, "spec_abs");
                 mark(s, "fwd_p");
-                k_fwd_p<T, D><<<G, B, row_smem, s>>>(P, R, last, row);
+                launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, P, R, last, row);
             }
             if (probe_g >= 0) end_sample(s);
         }
@@ -317,20 +449,21 @@ template <typename T> struct Plan : public PlanBase {
         probe_next = 0;
         probe_names[1].clear();
         probe_samples[1] = 0;
-        k_adj_init<T, D><<<G, B, row_smem, s>>>(P, R, Nt == 1, P.data + (size_t)(Nt - 1) * Ns);
+        launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, P, R, (int)(Nt == 1),
+               (const T*)(P.data + (size_t)(Nt - 1) * Ns));
         for (int n = Nt - 2; n >= 0; --n) {
             if (sampled(n, Nt)) begin_sample(1, probe_samples[1]++ == 0);
             if (P.lossy) {
                 spectral_named<D, SPEC_ABS>(s, "spec_abs");
                 mark(s, "adj_rho");
-                k_adj_rho<T, D><<<G, B, row_smem, s>>>(P, R);
+                launch(k_adj_rho<T, D>, dim3(G), B, row_smem, s, P, R);
             }
             spectral_named<D, SPEC_DIVT>(s, "spec_divt");
             mark(s, "adj_u");
-            k_adj_u<T, D><<<G, B, row_smem, s>>>(P, R, n == 0);
+            launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
             spectral_named<D, SPEC_GRADT>(s, "spec_gradt");
             mark(s, "adj_p");
-            k_adj_p<T, D><<<G, B, row_smem, s>>>(P, R, n == 0, P.data + (size_t)n * Ns);
+            launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * Ns));
             if (probe_g >= 0) end_sample(s);
         }
     }
@@ -430,6 +563,11 @@ pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, doub
     *mean_ms = cnt ? sum / cnt : 0.0;
     *samples = cnt;
     return PAT_OK;
+}
+
+pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {
+    if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->run_persistent(adjoint, s);
+    return static_cast<Plan<double>*>(base)->run_persistent(adjoint, s);
 }
 
 pat_status plan_capture(PlanBase* base, bool adjoint) {

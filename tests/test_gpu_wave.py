@@ -205,3 +205,29 @@ def test_vessel_512_full_size_prefix_and_dot(dev):
     rhs = torch.sum(x.double() * HTh).item()
     assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * hh.double().norm().item()
     assert np.isfinite(d).all() and np.abs(d).max() > 0
+
+
+def test_both_2d_paths_agree_with_oracle(dev, monkeypatch):
+    # 2-D plans use the persistent single-kernel path when the per-CTA state fits in shared
+    # memory; PAT_PERSIST=0 forces the per-phase CUDA-graph path.  Both must match the oracle.
+    pb = synth.small_lossy_2d(shape=(64, 80), pml=8, Nt=120, n_sensors=24)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(13).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    for flag, path in (("1", 1), ("0", 0)):
+        monkeypatch.setenv("PAT_PERSIST", flag)
+        for prec, tol in (("f32", TOL32), ("f64", TOL64)):
+            op = _gpu_op(pb, prec, dev)
+            assert op.info.path == path
+            assert rel(op.forward(_t(pb.p0, prec, dev)).cpu().numpy(), d_ref) <= tol
+            assert rel(op.adjoint(_t(h, prec, dev)).cpu().numpy(), g_ref) <= tol
+            op.close()
+
+
+def test_persistent_status_word_ok(dev):
+    from paper_1603_02329_gb300 import _lib
+
+    pb = synth.small_lossy_2d(shape=(48, 48), pml=6, Nt=30, n_sensors=8)
+    op = _gpu_op(pb, "f32", dev)
+    op.forward(_t(pb.p0, "f32", dev))
+    assert _lib.lib().pat_plan_status(op._plan) == 0

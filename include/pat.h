@@ -177,6 +177,15 @@ pat_status pat_forward_static(const void* p0, const double* c, const double* rho
                               const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
                               void* data, void* stream);
 
+/* Phase-timeline trace of the persistent kernel (tracing).  After pat_plan_set_trace(plan, k0, nk)
+ * (0 < nk <= 4096; nk = 0 turns it off), every solve records, for each CTA b and each grid barrier
+ * k in [k0, k0 + nk) (counted from 0 in launch order), the device globaltimer [ns] when the CTA
+ * entered the barrier and when it left it.  pat_plan_read_trace copies them, synchronising the
+ * device, as [grid][nk][2] unsigned 64-bit values into `out` (capacity `count` values) and sets
+ * *grid.  Plans on the per-phase graph path record nothing (*grid = 0). */
+pat_status pat_plan_set_trace(pat_plan* plan, int k0, int nk);
+pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t count, int* grid);
+
 /* pat_last_error -- message describing the calling thread's last failed call ("" if none).
  * The pointer stays valid until the next pat_* call on the same thread. */
 const char* pat_last_error(void);

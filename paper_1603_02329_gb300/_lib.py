@@ -68,6 +68,10 @@ def lib() -> ctypes.CDLL:
     L.pat_forward.restype = i32
     L.pat_forward_static.argtypes = L.pat_forward.argtypes
     L.pat_forward_static.restype = i32
+    L.pat_plan_set_trace.argtypes = [vp, i32, i32]
+    L.pat_plan_set_trace.restype = i32
+    L.pat_plan_read_trace.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.POINTER(i32)]
+    L.pat_plan_read_trace.restype = i32
     L.pat_plan_status.argtypes = [vp]
     L.pat_plan_status.restype = i32
     L.pat_plan_set_probe.argtypes = [vp, i32]

@@ -150,6 +150,26 @@ class PATOperator:
             out.append((name.value.decode(), ms.value, cnt.value))
         return out
 
+    # -- phase-timeline trace (persistent path) -------------------------------------------------
+    def set_trace(self, k0: int, nk: int):
+        """pat_plan_set_trace: record barrier entry/exit times for barriers k0 .. k0 + nk - 1."""
+        check(lib().pat_plan_set_trace(self._plan, int(k0), int(nk)))
+        self._trace_nk = int(nk)
+
+    def read_trace(self):
+        """pat_plan_read_trace: uint64 array [grid][nk][2] (entry, exit) in ns, or None."""
+        nk = getattr(self, "_trace_nk", 0)
+        if nk == 0:
+            return None
+        cap = 4096 * nk * 2
+        buf = np.zeros(cap, dtype=np.uint64)
+        grid = ctypes.c_int()
+        check(lib().pat_plan_read_trace(self._plan, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
+                                        ctypes.byref(grid)))
+        if grid.value == 0:
+            return None
+        return buf[: grid.value * nk * 2].reshape(grid.value, nk, 2)
+
     def close(self):
         if getattr(self, "_plan", None) is not None and self._plan.value:
             lib().pat_plan_destroy(self._plan)

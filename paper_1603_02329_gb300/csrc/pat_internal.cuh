@@ -128,6 +128,11 @@ template <typename T> struct DevPlan {
     T* data;          // [Nt][Ns]
 
     DevSensors<T> sens;
+
+    // phase-timeline trace of the persistent kernel (nullptr = off): globaltimer at entry and
+    // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA
+    unsigned long long* trace;
+    int trace_k0, trace_nk;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -166,6 +171,8 @@ struct PlanBase {
     int persist_grid = 0;
     size_t persist_smem = 0;
     unsigned* gbar = nullptr;
+    unsigned long long* trace = nullptr;
+    int trace_k0 = 0, trace_nk = 0;
 };
 
 // error reporting (thread-local message)

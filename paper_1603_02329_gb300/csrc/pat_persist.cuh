@@ -36,10 +36,25 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // Grid barrier #k (k counted from 1) over `nblocks` CTAs: a monotonically increasing arrival
 // counter (zeroed before the launch); barrier k completes when it reaches k * nblocks.
 // Returns false (every thread of the CTA) if the wait ran out or another CTA reported an error.
-__device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, unsigned& k, int* abort_s) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+struct TraceRef {
+    unsigned long long* buf;
+    int k0, nk;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, unsigned& k, int* abort_s,
+                                             TraceRef tr = TraceRef{nullptr, 0, 0}) {
     __syncthreads();
     ++k;
+    const int kt = (int)k - 1 - tr.k0;
+    const bool traced = tr.buf && kt >= 0 && kt < tr.nk;
     if (threadIdx.x == 0) {
+        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * 2] = globaltimer_ns();
         __threadfence();
         atomicAdd(&gbar[0], 1u);
         const unsigned target = k * nblocks;
@@ -58,6 +73,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
             __nanosleep(32);
         }
         __threadfence();
+        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * 2 + 1] = globaltimer_ns();
         *abort_s = ab;
     }
     __syncthreads();
@@ -282,6 +298,7 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
     const T dt = P.dt;
     const int Nt = P.Nt, Ns = P.sens.Ns;
     unsigned kbar = 0;
+    const TraceRef TR{P.trace, P.trace_k0, P.trace_nk};
 
     // ---- setup: tables and resident medium ----
     stage16(s.twx, P.twx, (size_t)nx * sizeof(cplx<T>));
@@ -358,13 +375,13 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
             pgather(s, P, seg, line0, A, P.data);
             if (Nt > 1) prow_r2c(s, P, A, A + (size_t)s.rmax * nx, 1, line0, R);
         }
-        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag)) return;
+        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
         for (int n = 0; n + 1 < Nt; ++n) {
             const bool last = (n + 2 == Nt);
             T* drow = P.data + (size_t)(n + 1) * Ns;
             // (1) g = D+ p
             if (tile) pcol<T, SPEC_GRAD>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             // u update, x-FFT of u
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
@@ -385,10 +402,10 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                     }
                 prow_r2c(s, P, out, res, 2, line0, R);
             }
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             // (2) e = D- u
             if (tile) pcol<T, SPEC_DIV>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             // rho update; lossless: p, sample; lossy: x-FFT of (dd, r)
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
@@ -424,10 +441,10 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                 }
             }
             if (P.lossy) {
-                if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
                 // (3) fractional Laplacians
                 if (tile) pcol<T, SPEC_ABS>(s, P, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
                 if (rows) {
                     cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                     cplx<T>* out = prow_other(s, P, res);
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                     if (!last) prow_r2c(s, P, out, res, 1, line0, R);
                 }
             }
-            if (!last && !grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!last && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
         }
     } else {
         // ================= adjoint: reverse time, exact transpose =================
@@ -497,12 +514,12 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
             tail(A, B, Nt == 1);
         }
         if (Nt == 1) return;
-        if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+        if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
         for (int n = Nt - 2; n >= 0; --n) {
             const bool final_ = (n == 0);
             if (P.lossy) {
                 if (tile) pcol<T, SPEC_ABS>(s, P, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
                 if (rows) {
                     cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                     cplx<T>* out = prow_other(s, P, res);
@@ -523,11 +540,11 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                         }
                     prow_r2c(s, P, out, res, 2, line0, R);
                 }
-                if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             }
             // transpose of e = D- u
             if (tile) pcol<T, SPEC_DIVT>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                 cplx<T>* out = prow_other(s, P, res);
@@ -548,10 +565,10 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                     }
                 prow_r2c(s, P, out, res, 2, line0, R);
             }
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             // transpose of g = D+ p
             if (tile) pcol<T, SPEC_GRADT>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 1, line0, R);
                 cplx<T>* other = prow_other(s, P, res);
@@ -559,7 +576,7 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
                 __syncthreads();
                 tail(res, other, final_);
             }
-            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag)) return;
+            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
         }
     }
 }

@@ -390,6 +390,10 @@ pat_status pat_plan_destroy(pat_plan* plan) {
     if (!plan) return PAT_OK;
     {
         DeviceGuard g(plan->impl->device);
+        if (plan->impl->trace) {
+            cudaDeviceSynchronize();
+            cudaFree(plan->impl->trace);
+        }
         delete plan->impl;
     }
     delete plan;
@@ -497,6 +501,45 @@ pat_status pat_plan_status(pat_plan* plan) {
         set_error("a bounded device-side wait ran out (grid barrier of the persistent kernel)");
         return (pat_status)w[2];
     }
+    return PAT_OK;
+}
+
+pat_status pat_plan_set_trace(pat_plan* plan, int k0, int nk) {
+    set_error("");
+    if (!plan || k0 < 0 || nk < 0 || nk > 4096) return fail(PAT_EINVAL, "bad trace arguments");
+    PlanBase* b = plan->impl;
+    if (!b->persistent) return PAT_OK;
+    DeviceGuard g(b->device);
+    if (b->trace) {
+        cudaDeviceSynchronize();
+        cudaFree(b->trace);
+        b->trace = nullptr;
+    }
+    b->trace_k0 = k0;
+    b->trace_nk = nk;
+    if (nk == 0) return PAT_OK;
+    const size_t bytes = (size_t)b->persist_grid * nk * 2 * sizeof(unsigned long long);
+    cudaError_t e = cudaMalloc(&b->trace, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (trace)");
+    e = cudaMemset(b->trace, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (trace)");
+    return PAT_OK;
+}
+
+pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t count, int* grid) {
+    set_error("");
+    if (!plan || !grid) return fail(PAT_EINVAL, "NULL argument");
+    PlanBase* b = plan->impl;
+    *grid = 0;
+    if (!b->trace) return PAT_OK;
+    const size_t n = (size_t)b->persist_grid * b->trace_nk * 2;
+    if (!out || count < n) return fail(PAT_EINVAL, "trace buffer too small");
+    DeviceGuard g(b->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    e = cudaMemcpy(out, b->trace, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read trace");
+    *grid = b->persist_grid;
     return PAT_OK;
 }
 

@@ -290,6 +290,9 @@ template <typename T> struct Plan : public PlanBase {
         attr[0].val.cooperative = 1;
         lc.attrs = attr;
         lc.numAttrs = 1;
+        P.trace = trace;
+        P.trace_k0 = trace_k0;
+        P.trace_nk = trace_nk;
         if (adjoint) e = cudaLaunchKernelEx(&lc, k_persist<T, true>, P, pcfg, gbar);
         else e = cudaLaunchKernelEx(&lc, k_persist<T, false>, P, pcfg, gbar);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernelEx (persistent)");

@@ -132,6 +132,99 @@ pat_status pat_forward(const void* p0, const double* c, const double* rho, const
                        const pat_sensors* sensor_mask, double dt, int Nt, pat_precision prec,
                        void* data, void* stream);
 
+/* ===========================================================================================
+ * Optimisation shell (Sec. IV, Sec. V): image-space operators on a grid (only ndim and n[] of
+ * pat_grid are used; images are [Nz][Ny][Nx], device pointers, plan-independent precision).
+ * D = forward differences per axis with a zero difference at the last index (Neumann),
+ * TV(x) = sum_i sqrt(sum_xi (D_xi x)_i^2) (isotropic).  Calls that return a host scalar
+ * synchronise `stream`; the others only enqueue.
+ * =========================================================================================== */
+
+/* pat_tv_prox -- x = argmin_u weight * TV(u) + indicator(u >= 0 if nonneg) + 1/2 ||u - z||^2, the
+ * proximal map of Sec. IV Eq. (proxmal) with weight = alpha * lambda, by n_inner iterations of the
+ * dual fast gradient projection cited there (zero warm start; step 1/(4 d weight)).
+ * weight <= 0 or n_inner = 0 returns the projection of z.  z and x must not alias. */
+pat_status pat_tv_prox(const pat_grid* grid, const void* z, void* x, double weight, int n_inner, int nonneg,
+                       pat_precision prec, void* stream);
+
+/* pat_tv -- *value = TV(x) (rho = 0) or the smoothed J_rho(x) = sum_i (sqrt(|D x|_i^2 + rho^2) - rho)
+ * of Sec. V.B Eq. (Thirty-two) (rho > 0), accumulated in FP64. */
+pat_status pat_tv(const pat_grid* grid, const void* x, double rho, double* value, pat_precision prec, void* stream);
+
+/* pat_tv_smooth_grad -- grad = D^T (D y / sqrt(|D y|^2 + rho^2)), the gradient of J_rho
+ * (Sec. V.B Eq. (Twentyone) without the data term), rho > 0. */
+pat_status pat_tv_smooth_grad(const pat_grid* grid, const void* y, double rho, void* grad, pat_precision prec,
+                              void* stream);
+
+/* pat_restrict / pat_prolong -- the grid transfer of Sec. V.A between the fine grid `fine` (even
+ * sizes) and the coarse grid of half the points per axis: prolongation P is tensor-product linear
+ * interpolation (fine 2i <- coarse i, fine 2i+1 <- mean of coarse i and min(i+1, n_c-1)),
+ * restriction R = 2^-d P^T (full weighting). */
+pat_status pat_restrict(const pat_grid* fine, const void* xf, void* xc, pat_precision prec, void* stream);
+pat_status pat_prolong(const pat_grid* fine, const void* xc, void* xf, pat_precision prec, void* stream);
+
+/* pat_coarse_bound -- the restricted lower bound of Sec. V.C Eq. (constraint), taken at y:
+ * phi_i = (R y)_i - min_{j in {2i-1, 2i, 2i+1}^d, clamped} y_j.  x = y + P(x_c - R y) is >= 0
+ * whenever x_c >= phi. */
+pat_status pat_coarse_bound(const pat_grid* fine, const void* y, void* phi, pat_precision prec, void* stream);
+
+/* pat_dot -- *out = sum_i a_i b_i over n elements, accumulated in FP64 (deterministic order). */
+pat_status pat_dot(const void* a, const void* b, int64_t n, pat_precision prec, double* out, void* stream);
+
+/* pat_power_iteration -- L_f = sigma_max(H^T H) by the power method (Sec. IV): v = v0 / ||v0||,
+ * then n_iter times w = H^T H v, L = ||w||, v = w / L.  v0 [N] device, plan precision. */
+pat_status pat_power_iteration(pat_plan* plan, const void* v0, int n_iter, double* L, void* stream);
+
+/* pat_plan_create_coarse -- the next coarser level of a plan (Sec. V): half the points per axis
+ * (fine sizes divisible by 4), twice the spacing, half the PML points (Sec. VI.A keeps its
+ * thickness), twice the time step and ceil(Nt / 2) samples, the medium sampled at the even fine
+ * points, the sensors at the same physical positions (on-grid sensors become point positions). */
+pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** coarse);
+
+/* Options of pat_mg_fista; the defaults of Sec. VI.A are noted. */
+typedef struct {
+    int variant;          /* 0: ISTA (theta = 0), 1: FISTA t-sequence (Alg. 2) */
+    double lambda;        /* TV weight (1e-2) */
+    double step_scale;    /* alpha = step_scale / L (2 for ISTA, 1 for FISTA) */
+    double kappa;         /* recursion test, Eq. (conditions) (1/4 in 2-D, 1/8 in 3-D) */
+    double vartheta;      /* recursion test (0.1) */
+    int q_d;              /* recursion test (3) */
+    int q_c;              /* maximum coarse iterations (8) */
+    double eps_d;         /* fine stopping tolerance on the relative decrease of F (1e-3) */
+    double eps_c;         /* coarse stopping tolerance on the relative decrease of phi (1e-2) */
+    double tv_rho;        /* smoothing of Eq. (Thirty-two) (1e-2 in 2-D, 3e-2 in 3-D) */
+    int n_tv;             /* inner iterations of the TV prox (20) */
+    int max_iter;         /* fine iterations at most */
+    int recursion;        /* 0: never take the coarse branch (plain ISTA / FISTA) */
+    double L;             /* sigma_max(H^T H) of the fine level (pat_power_iteration) */
+    double L_coarse;      /* the same for the coarse level; the coarse step is 1/(L_coarse + 4 d lambda / tv_rho) */
+    double target_re;     /* > 0: also stop when ||x - p_exact|| / ||p_exact|| <= target_re */
+    const void* p_exact;  /* optional [N] device image for RE reporting (plan precision) */
+} pat_fista_opts;
+
+typedef struct {
+    int iters, recursive_iters, fwd_solves, adj_solves;
+    double F;      /* 1/2 ||H x - p_hat||^2 + lambda TV(x) at the returned x */
+    double RES;    /* ||H x - p_hat|| */
+    double RE;     /* ||x - p_exact|| / ||p_exact|| (NaN without p_exact) */
+} pat_fista_report;
+
+/* called after every fine iteration k >= 1 (recursive = 1 if the coarse branch was taken) */
+typedef void (*pat_iter_callback)(void* ctx, int k, int recursive, double F, double RES, double RE, int fwd_solves,
+                                  int adj_solves);
+
+/* pat_mg_fista -- line-search multi-grid FISTA / ISTA with TV (Alg. 3, Sec. V.E) on two levels,
+ * or plain FISTA (Alg. 2) / ISTA (Alg. 1) when coarse is NULL or opts->recursion = 0.
+ *   fine, coarse   plans of the two levels (coarse from pat_plan_create_coarse, or NULL)
+ *   data [Nt][Ns]  measured data p_hat (device); x0 [N] start (device); x_out [N] result (device)
+ * Each fine iteration costs one forward and one adjoint solve (the cost-saving identity
+ * H y_{k+1} = (1 + theta) H x_k - theta H x_{k-1}); objective values, norms and the recursion test
+ * are FP64 scalars on the host (one synchronisation per reduction).  Stops when the relative
+ * decrease of F falls below eps_d, after max_iter iterations, or at target_re. */
+pat_status pat_mg_fista(pat_plan* fine, pat_plan* coarse, const void* data, const void* x0,
+                        const pat_fista_opts* opts, void* x_out, pat_fista_report* report, pat_iter_callback cb,
+                        void* cb_ctx, void* stream);
+
 /* pat_plan_status -- synchronise the device and return the status word of the plan's last solve:
  * PAT_OK, or PAT_ETIMEOUT if a bounded device-side wait (the grid barrier of the persistent
  * kernel) ran out; the kernel then stopped early and its outputs are not valid. */

@@ -32,6 +32,24 @@ class pat_plan_info_t(ctypes.Structure):
                 ("dt", ctypes.c_double), ("c_ref", ctypes.c_double), ("path", ctypes.c_int)]
 
 
+class pat_fista_opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("lambda_", ctypes.c_double), ("step_scale", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("vartheta", ctypes.c_double), ("q_d", ctypes.c_int), ("q_c", ctypes.c_int),
+                ("eps_d", ctypes.c_double), ("eps_c", ctypes.c_double), ("tv_rho", ctypes.c_double),
+                ("n_tv", ctypes.c_int), ("max_iter", ctypes.c_int), ("recursion", ctypes.c_int),
+                ("L", ctypes.c_double), ("L_coarse", ctypes.c_double), ("target_re", ctypes.c_double),
+                ("p_exact", ctypes.c_void_p)]
+
+
+class pat_fista_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("recursive_iters", ctypes.c_int), ("fwd_solves", ctypes.c_int),
+                ("adj_solves", ctypes.c_int), ("F", ctypes.c_double), ("RES", ctypes.c_double), ("RE", ctypes.c_double)]
+
+
+ITER_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, ctypes.c_int, ctypes.c_int)
+
+
 class PatError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -81,6 +99,28 @@ def lib() -> ctypes.CDLL:
     L.pat_plan_probe_read.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(f64),
                                       ctypes.POINTER(i32)]
     L.pat_plan_probe_read.restype = i32
+    G = ctypes.POINTER(pat_grid)
+    L.pat_tv_prox.argtypes = [G, vp, vp, f64, i32, i32, i32, vp]
+    L.pat_tv_prox.restype = i32
+    L.pat_tv.argtypes = [G, vp, f64, dp, i32, vp]
+    L.pat_tv.restype = i32
+    L.pat_tv_smooth_grad.argtypes = [G, vp, f64, vp, i32, vp]
+    L.pat_tv_smooth_grad.restype = i32
+    L.pat_restrict.argtypes = [G, vp, vp, i32, vp]
+    L.pat_restrict.restype = i32
+    L.pat_prolong.argtypes = [G, vp, vp, i32, vp]
+    L.pat_prolong.restype = i32
+    L.pat_coarse_bound.argtypes = [G, vp, vp, i32, vp]
+    L.pat_coarse_bound.restype = i32
+    L.pat_dot.argtypes = [vp, vp, ctypes.c_int64, i32, dp, vp]
+    L.pat_dot.restype = i32
+    L.pat_power_iteration.argtypes = [vp, vp, i32, dp, vp]
+    L.pat_power_iteration.restype = i32
+    L.pat_plan_create_coarse.argtypes = [vp, plan_pp]
+    L.pat_plan_create_coarse.restype = i32
+    L.pat_mg_fista.argtypes = [vp, vp, vp, vp, ctypes.POINTER(pat_fista_opts), vp, ctypes.POINTER(pat_fista_report),
+                               ITER_CB, vp, vp]
+    L.pat_mg_fista.restype = i32
     L.pat_last_error.argtypes = []
     L.pat_last_error.restype = ctypes.c_char_p
     _lib = L

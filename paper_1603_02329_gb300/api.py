@@ -132,6 +132,36 @@ class PATOperator:
                                     _stream_ptr(stream, self.device)))
         return out
 
+    # -- optimisation shell ---------------------------------------------------------------------
+    def power_iteration(self, v0: torch.Tensor, n_iter: int = 30, stream=None) -> float:
+        """pat_power_iteration: sigma_max(H^T H) from the start vector v0 (device, plan dtype)."""
+        self._check_in(v0, self.N, "v0")
+        L = ctypes.c_double()
+        with torch.cuda.device(self.device):
+            check(lib().pat_power_iteration(self._plan, ctypes.c_void_p(v0.data_ptr()), int(n_iter), ctypes.byref(L),
+                                            _stream_ptr(stream, self.device)))
+        return L.value
+
+    def coarse(self) -> "PATOperator":
+        """pat_plan_create_coarse: the next coarser level (half the points, twice dx and dt)."""
+        op = PATOperator.__new__(PATOperator)
+        op._plan = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().pat_plan_create_coarse(self._plan, ctypes.byref(op._plan)))
+        info = _lib.pat_plan_info_t()
+        check(lib().pat_plan_get_info(op._plan, ctypes.byref(info)))
+        d = info.ndim
+        op.info = info
+        op.shape = tuple(int(info.n[d - 1 - a]) for a in range(d))
+        op.N = int(info.N)
+        op.Nt = int(info.Nt)
+        op.Ns = int(info.Ns)
+        op.prec = self.prec
+        op.dtype = self.dtype
+        op.device = self.device
+        op.lossy = bool(info.lossy)
+        return op
+
     # -- kernel-timing probe ------------------------------------------------------------------------
     def set_probe(self, stride: int):
         """pat_plan_set_probe: bracket the launches of every `stride`-th step with CUDA events."""
@@ -208,3 +238,132 @@ def pat_forward(p0: torch.Tensor, c, rho, alpha0, y, shape, spacing, pml, pml_al
                             float(dt), int(Nt), prec, ctypes.c_void_p(out.data_ptr()),
                             _stream_ptr(stream, p0.device)))
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# image-space operators of the optimisation shell (Sec. IV, Sec. V)
+# ---------------------------------------------------------------------------------------------
+def _prec_of(t: torch.Tensor):
+    if t.dtype == torch.float32:
+        return PAT_F32
+    if t.dtype == torch.float64:
+        return PAT_F64
+    raise TypeError("float32 or float64 tensor expected")
+
+
+def _img_grid(shape):
+    return make_grid(tuple(shape), (1.0,) * len(shape), (0,) * len(shape), 0.0)
+
+
+def _dev_stream(t, stream):
+    return _stream_ptr(stream, t.device)
+
+
+def tv_prox(z: torch.Tensor, weight: float, n_inner: int = 20, nonneg: bool = True, stream=None) -> torch.Tensor:
+    """pat_tv_prox: argmin weight TV(x) + [x >= 0] + 1/2 ||x - z||^2 (dual FGP, n_inner steps)."""
+    x = torch.empty_like(z)
+    g = _img_grid(z.shape)
+    check(lib().pat_tv_prox(ctypes.byref(g), ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                            float(weight), int(n_inner), int(bool(nonneg)), _prec_of(z), _dev_stream(z, stream)))
+    return x
+
+
+def tv(x: torch.Tensor, rho: float = 0.0, stream=None) -> float:
+    """pat_tv: TV(x) (rho = 0) or J_rho(x) (rho > 0), FP64 accumulation."""
+    v = ctypes.c_double()
+    g = _img_grid(x.shape)
+    check(lib().pat_tv(ctypes.byref(g), ctypes.c_void_p(x.data_ptr()), float(rho), ctypes.byref(v), _prec_of(x),
+                       _dev_stream(x, stream)))
+    return v.value
+
+
+def tv_smooth_grad(y: torch.Tensor, rho: float, stream=None) -> torch.Tensor:
+    """pat_tv_smooth_grad: gradient of J_rho."""
+    out = torch.empty_like(y)
+    g = _img_grid(y.shape)
+    check(lib().pat_tv_smooth_grad(ctypes.byref(g), ctypes.c_void_p(y.data_ptr()), float(rho),
+                                   ctypes.c_void_p(out.data_ptr()), _prec_of(y), _dev_stream(y, stream)))
+    return out
+
+
+def restrict(xf: torch.Tensor, stream=None) -> torch.Tensor:
+    """pat_restrict: R = 2^-d P^T onto half the points per axis."""
+    xc = torch.empty(tuple(n // 2 for n in xf.shape), dtype=xf.dtype, device=xf.device)
+    g = _img_grid(xf.shape)
+    check(lib().pat_restrict(ctypes.byref(g), ctypes.c_void_p(xf.data_ptr()), ctypes.c_void_p(xc.data_ptr()),
+                             _prec_of(xf), _dev_stream(xf, stream)))
+    return xc
+
+
+def prolong(xc: torch.Tensor, stream=None) -> torch.Tensor:
+    """pat_prolong: linear interpolation onto twice the points per axis."""
+    fine = tuple(2 * n for n in xc.shape)
+    xf = torch.empty(fine, dtype=xc.dtype, device=xc.device)
+    g = _img_grid(fine)
+    check(lib().pat_prolong(ctypes.byref(g), ctypes.c_void_p(xc.data_ptr()), ctypes.c_void_p(xf.data_ptr()),
+                            _prec_of(xc), _dev_stream(xc, stream)))
+    return xf
+
+
+def coarse_bound(y: torch.Tensor, stream=None) -> torch.Tensor:
+    """pat_coarse_bound: phi = R y - min over the fine neighbourhood."""
+    phi = torch.empty(tuple(n // 2 for n in y.shape), dtype=y.dtype, device=y.device)
+    g = _img_grid(y.shape)
+    check(lib().pat_coarse_bound(ctypes.byref(g), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                 _prec_of(y), _dev_stream(y, stream)))
+    return phi
+
+
+def dot(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
+    """pat_dot: FP64-accumulated inner product."""
+    v = ctypes.c_double()
+    check(lib().pat_dot(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), a.numel(), _prec_of(a),
+                        ctypes.byref(v), _dev_stream(a, stream)))
+    return v.value
+
+
+FISTA_DEFAULTS = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25, vartheta=0.1, q_d=3, q_c=8, eps_d=1e-3,
+                      eps_c=1e-2, tv_rho=1e-2, n_tv=20, max_iter=50, recursion=True, target_re=0.0)
+
+
+def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.Tensor, x0: torch.Tensor, L: float,
+             L_coarse: float = 0.0, p_exact: Optional[torch.Tensor] = None, callback=None, stream=None, **opts):
+    """pat_mg_fista: Alg. 3 (two levels) or Alg. 2 / Alg. 1.  Returns (x, report dict, records)."""
+    o = dict(FISTA_DEFAULTS)
+    o.update(opts)
+    po = _lib.pat_fista_opts()
+    po.variant = int(o["variant"])
+    po.lambda_ = float(o["lam"])
+    po.step_scale = float(o["step_scale"])
+    po.kappa = float(o["kappa"])
+    po.vartheta = float(o["vartheta"])
+    po.q_d = int(o["q_d"])
+    po.q_c = int(o["q_c"])
+    po.eps_d = float(o["eps_d"])
+    po.eps_c = float(o["eps_c"])
+    po.tv_rho = float(o["tv_rho"])
+    po.n_tv = int(o["n_tv"])
+    po.max_iter = int(o["max_iter"])
+    po.recursion = int(bool(o["recursion"]))
+    po.L = float(L)
+    po.L_coarse = float(L_coarse)
+    po.target_re = float(o["target_re"])
+    po.p_exact = ctypes.c_void_p(p_exact.data_ptr()) if p_exact is not None else None
+    records = []
+
+    def _cb(ctx, k, rec, F, RES, RE, nf, na):
+        records.append(dict(k=k, branch="recursive" if rec else "direct", F=F, RES=RES, RE=RE, fwd=nf, adj=na))
+        if callback is not None:
+            callback(records[-1])
+
+    cb = _lib.ITER_CB(_cb)
+    rep = _lib.pat_fista_report()
+    x = torch.empty_like(x0)
+    cplan = coarse._plan if coarse is not None else None
+    with torch.cuda.device(fine.device):
+        check(lib().pat_mg_fista(fine._plan, cplan, ctypes.c_void_p(data.data_ptr()), ctypes.c_void_p(x0.data_ptr()),
+                                 ctypes.byref(po), ctypes.c_void_p(x.data_ptr()), ctypes.byref(rep), cb, None,
+                                 _stream_ptr(stream, fine.device)))
+    report = dict(iters=rep.iters, recursive_iters=rep.recursive_iters, fwd_solves=rep.fwd_solves,
+                  adj_solves=rep.adj_solves, F=rep.F, RES=rep.RES, RE=rep.RE)
+    return x, report, records

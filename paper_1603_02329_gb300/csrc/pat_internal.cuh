@@ -145,8 +145,22 @@ struct LaunchCfg {
     int col_threads;
 };
 
+// the arguments a plan was created from (kept on the host to build coarser levels)
+struct PlanInputs {
+    pat_grid grid{};
+    std::vector<double> c, rho, alpha0;
+    int alpha0_is_scalar = 0;
+    double y = 1.5, dt = 0.0;
+    int Nt = 0;
+    std::vector<double> pos;       // [Ns][ndim] or empty
+    std::vector<int64_t> index;    // [Ns] or empty
+    int Ns = 0;
+    pat_precision prec = PAT_F32;
+};
+
 struct PlanBase {
     virtual ~PlanBase() {}
+    PlanInputs in;
     pat_plan_info_t info;
     int device = 0;
     LaunchCfg cfg;

@@ -380,6 +380,22 @@ pat_status pat_plan_create(const pat_grid* grid, const double* c, const double* 
     if (st != PAT_OK) return st;
     PlanBase* impl = (prec == PAT_F32) ? make_plan_f32(h, &st) : make_plan_f64(h, &st);
     if (!impl) return st;
+    {
+        PlanInputs& in = impl->in;
+        in.grid = *grid;
+        const size_t N = (size_t)h.N;
+        in.c.assign(c, c + N);
+        in.rho.assign(rho, rho + N);
+        in.alpha0.assign(alpha0, alpha0 + (alpha0_is_scalar ? 1 : N));
+        in.alpha0_is_scalar = alpha0_is_scalar;
+        in.y = y;
+        in.dt = dt;
+        in.Nt = Nt;
+        in.Ns = sensors->count;
+        if (sensors->pos) in.pos.assign(sensors->pos, sensors->pos + (size_t)sensors->count * grid->ndim);
+        else in.index.assign(sensors->index, sensors->index + sensors->count);
+        in.prec = prec;
+    }
     pat_plan* p = new pat_plan;
     p->impl = impl;
     *out = p;

@@ -234,10 +234,10 @@ template <typename T> struct Plan : public PlanBase {
                     optin, nsm, coop);
         if (!coop || smem > (size_t)optin) return PAT_OK;
         cudaError_t e = cudaFuncSetAttribute((const void*)k_persist<T, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute((const void*)k_persist<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
+                                     optin);
         if (e != cudaSuccess) {
             if (dbg) fprintf(stderr, "[pat] persistent: set attribute failed: %s\n", cudaGetErrorString(e));
             cudaGetLastError();
@@ -300,10 +300,20 @@ template <typename T> struct Plan : public PlanBase {
         return PAT_OK;
     }
 
+    // The dynamic shared-memory limit is a property of the kernel function, shared by every plan:
+    // raise it to the device's opt-in maximum (plans of different sizes coexist), after checking
+    // that this plan's launches fit.
     template <int D> pat_status set_attrs() {
         cudaError_t e = cudaSuccess;
-        auto seta = [&](const void* f, size_t bytes) {
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (row_smem > (size_t)optin || spec_smem > (size_t)optin) {
+            set_error("grid too large for the shared-memory kernels of this device");
+            return PAT_EUNSUPPORTED;
+        }
+        auto seta = [&](const void* f, size_t) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         };
         seta((const void*)k_fwd_init<T, D>, row_smem);
         seta((const void*)k_fwd_u<T, D>, row_smem);

@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--probe-stride", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
+    ap.add_argument("--mg-iters", type=int, default=30)
     return ap.parse_args()
 
 
@@ -193,6 +195,57 @@ def cpu_baseline(args, pb):
                       f"({t:.1f} s), FP64 numpy"}
 
 
+def mg_vs_fista(args, dev):
+    """Wall time of two-level MG-FISTA and of single-grid FISTA to the same relative error (Sec. VI.A
+    compares the methods by RE and F against time).  Target: 1.05 x the best RE that FISTA reaches
+    in --mg-iters iterations.  L estimation (power method, 30 iterations per level) is setup and is
+    reported separately."""
+    import torch
+
+    from paper_1603_02329_gb300 import synth
+    from paper_1603_02329_gb300.api import PATOperator, mg_fista
+
+    pb = synth.vessel_phantom_2d(seed=2)
+    op = PATOperator.from_problem(pb, precision="f32", device=dev)
+    opc = op.coarse()
+    x_true = torch.tensor(pb.p0, dtype=torch.float32, device=dev)
+    clean = op.forward(x_true).cpu().numpy()
+    noisy = synth.awgn(np.random.default_rng(2), clean, 40.0)
+    data = torch.tensor(noisy, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    L = op.power_iteration(torch.tensor(synth.random_image(11, pb.shape), dtype=torch.float32, device=dev), 30)
+    Lc = opc.power_iteration(torch.tensor(synth.random_image(12, opc.shape), dtype=torch.float32, device=dev), 30)
+    setup_s = time.perf_counter() - t0
+    x0 = torch.zeros_like(x_true)
+    common = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25, vartheta=0.1, q_d=3, q_c=8, eps_d=-1.0,
+                  eps_c=1e-2, tv_rho=1e-2, n_tv=20)
+
+    def timed(coarse, recursion, max_iter, target):
+        stamps = []
+        t_start = time.perf_counter()
+        _, rep, recs = mg_fista(op, coarse, data, x0, L, L_coarse=Lc, p_exact=x_true, recursion=recursion,
+                                max_iter=max_iter, target_re=target,
+                                callback=lambda r: stamps.append(time.perf_counter() - t_start), **common)
+        for r, ts in zip(recs, stamps):
+            r["t"] = ts
+        return rep, recs
+
+    rep_f, recs_f = timed(None, False, args.mg_iters, 0.0)
+    best = min(r["RE"] for r in recs_f)
+    target = 1.05 * best
+    t_f = next(r["t"] for r in recs_f if r["RE"] <= target)
+    it_f = next(r["k"] for r in recs_f if r["RE"] <= target)
+    rep_m, recs_m = timed(opc, True, args.mg_iters, target)
+    hit = [r for r in recs_m if r["RE"] <= target]
+    t_m = hit[0]["t"] if hit else None
+    return {"target_re": target, "fista_best_re": best, "fista_s": t_f, "fista_iters": it_f,
+            "mgfista_s": t_m, "mgfista_iters": hit[0]["k"] if hit else None,
+            "mgfista_recursive_iters": sum(1 for r in recs_m if r["branch"] == "recursive"),
+            "speedup": (t_f / t_m) if t_m else None, "setup_s_power_method": setup_s,
+            "data": "forward of the phantom on the same grid + 40 dB AWGN (inverse crime, stated)",
+            "params": dict(common, lam=1e-2, L=L, L_coarse=Lc)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -336,6 +389,8 @@ def main():
            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, pb)
+    if args.mg and rank == 0:
+        out["mg_vs_fista"] = mg_vs_fista(args, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

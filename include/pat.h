@@ -178,7 +178,8 @@ pat_status pat_power_iteration(pat_plan* plan, const void* v0, int n_iter, doubl
 /* pat_plan_create_coarse -- the next coarser level of a plan (Sec. V): half the points per axis
  * (fine sizes divisible by 4), twice the spacing, half the PML points (Sec. VI.A keeps its
  * thickness), twice the time step and ceil(Nt / 2) samples, the medium sampled at the even fine
- * points, the sensors at the same physical positions (on-grid sensors become point positions). */
+ * points, the sensors at the same physical positions (on-grid sensors become point positions;
+ * a position beyond the first or last coarse node is clamped onto that node). */
 pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** coarse);
 
 /* Options of pat_mg_fista; the defaults of Sec. VI.A are noted. */

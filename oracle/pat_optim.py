@@ -23,7 +23,9 @@ O5  Bound restriction, Sec. V.C Eq. (constraint): phi_i = (R y)_i - min_{j in {2
     (indices clamped), evaluated at y_{h,k} (where the transfer happens, Sec. V.C last sentence).
 O6  Coarse level: n/2 points, spacing 2h, PML/2 points, dt_c = 2 dt, Nt_c = ceil(Nt/2)
     (Sec. V: the time step follows the spacing), medium decimated (c_c = c[::2, ::2]), sensors at
-    the same physical positions, data decimated in time (p_hat_c = p_hat[::2]).
+    the same physical positions, data decimated in time (p_hat_c = p_hat[::2]).  A position
+    beyond the first or last coarse node (a fine sensor on the last fine index) is clamped onto
+    that node, as P clamps at the last index.
 O7  Coarse iteration: FISTA (or ISTA) on phi_{h-1} with projection on {x >= phi} (Sec. V.E),
     step 1 / L_c, L_c = L(H_c^T H_c) + lambda 4 d / rho; its own t-sequence from 1; stop when
     (phi_k - phi_{k+1}) / max(|phi_k|, |phi_{k+1}|) < eps_c or after q_c iterations (the paper's
@@ -237,7 +239,12 @@ def coarse_operator(pb):
         idx = np.unravel_index(np.asarray(pb.sensor_index), pb.shape)
         pos = np.stack([(idx[a] - pb.shape[a] // 2) * pb.spacing[a] for a in range(d)][::-1], axis=1)
     else:
-        pos = np.asarray(pb.sensor_pos)
+        pos = np.asarray(pb.sensor_pos, dtype=float)
+    pos = np.array(pos, dtype=float)
+    for a in range(d):  # numpy axis a <-> position component d-1-a
+        lo = (0 - shape_c[a] // 2) * spacing_c[a]
+        hi = (shape_c[a] - 1 - shape_c[a] // 2) * spacing_c[a]
+        pos[:, d - 1 - a] = np.clip(pos[:, d - 1 - a], lo, hi)
     op = Operator(shape_c, spacing_c, pml_c, pb.pml_alpha, c_c, rho_c, a_c, pb.y, 2.0 * pb.dt, Nt_c,
                   sensor_pos=pos)
     return op, Nt_c

@@ -378,6 +378,14 @@ pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** out) {
             for (int a = 0; a < d; ++a) pos[(size_t)j * d + a] = (double)(ci[a] - g.n[a] / 2) * g.dx[a];
         }
     }
+    // positions beyond the first / last coarse node are clamped onto it (as P clamps)
+    for (int j = 0; j < in.Ns; ++j)
+        for (int a = 0; a < d; ++a) {
+            const double lo = (double)(0 - gc.n[a] / 2) * gc.dx[a];
+            const double hi = (double)(gc.n[a] - 1 - gc.n[a] / 2) * gc.dx[a];
+            double& v = pos[(size_t)j * d + a];
+            v = std::fmin(std::fmax(v, lo), hi);
+        }
     pat_sensors sc{in.Ns, pos.data(), nullptr};
     const int Ntc = (in.Nt + 1) / 2;
     return pat_plan_create(&gc, c.data(), rho.data(), a0.data(), in.alpha0_is_scalar, in.y, &sc, 2.0 * in.dt, Ntc,

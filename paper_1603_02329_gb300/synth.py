@@ -210,7 +210,8 @@ def vessel_phantom_2d(seed=2, n=512, pml=20, h=0.05e-3, Nt=2000, alpha0=0.75, y=
     a0 = np.full(shape, float(alpha0))
     ves = vessels_2d(rng, shape, n_vessels, margin_px=max(pml + 8, n // 8))
     r_ctr = 0.3 * n * h
-    dsk = discs(rng, shape, spacing, n_discs, r_ctr, (0.3e-3, 1.5e-3 * min(1.0, n / 512)), (0.5, 1.0))
+    sc = min(1.0, n / 512)
+    dsk = discs(rng, shape, spacing, n_discs, r_ctr, (0.3e-3 * sc, 1.5e-3 * sc), (0.5, 1.0))
     p0 = np.maximum(ves, dsk)
     dt = cfl * h / c.max()
     row = pml if sensor_row is None else sensor_row

@@ -135,3 +135,13 @@ def test_mg_fista_f32_close_to_oracle(dev):
     assert [r["branch"] for r in grecs] == [r.branch for r in recs]
     assert rel(x.cpu().numpy(), x_ref) <= 1e-4
     assert rep["iters"] == 5 and rep["fwd_solves"] >= 6
+
+
+def test_coarse_plan_with_edge_line_sensors(dev):
+    from paper_1603_02329_gb300.api import PATOperator
+
+    pb = synth.vessel_phantom_2d(n=64, pml=8, Nt=40, n_vessels=2, n_discs=2)
+    ref_c, Ntc = po.coarse_operator(pb)
+    opc = PATOperator.from_problem(pb, precision="f64", device=dev).coarse()
+    xc = np.random.default_rng(4).standard_normal(ref_c.shape)
+    assert rel(opc.forward(T(xc, dev)).cpu().numpy(), ref_c.forward(xc)) <= 1e-11

@@ -231,3 +231,17 @@ def test_paper_parameters_golden():
     assert o.q_d == g["q_d"]["value"] and o.q_c == g["q_c"]["value"]
     assert o.eps_d == g["eps_d"]["value"] and o.eps_c == g["eps_c"]["value"]
     assert o.tv_rho == g["rho_tv_2d"]["value"]
+
+
+def test_coarse_level_clamps_edge_sensors():
+    # a line of on-grid sensors spanning the whole row: the one on the last fine column lies beyond
+    # the last coarse node and is clamped onto it (weight 1), the even ones land on coarse nodes
+    pb = synth.vessel_phantom_2d(n=32, pml=4, Nt=10, n_vessels=1, n_discs=1)
+    op_c, Nt_c = po.coarse_operator(pb)
+    M = op_c.M.toarray()
+    assert np.allclose(M.sum(axis=1), 1.0)
+    row = pb.pml[0] // 2
+    last = row * 16 + 15
+    assert M[31, last] == 1.0          # fine x = 31 -> clamped onto coarse x = 15
+    assert M[30, last] == 1.0          # fine x = 30 -> coarse node 15
+    assert M[29, last - 1] == 0.5 and M[29, last] == 0.5

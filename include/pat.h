@@ -273,10 +273,13 @@ pat_status pat_forward_static(const void* p0, const double* c, const double* rho
 
 /* Phase-timeline trace of the persistent kernel (tracing).  After pat_plan_set_trace(plan, k0, nk)
  * (0 < nk <= 4096; nk = 0 turns it off), every solve records, for each CTA b and each grid barrier
- * k in [k0, k0 + nk) (counted from 0 in launch order), the device globaltimer [ns] when the CTA
- * entered the barrier and when it left it.  pat_plan_read_trace copies them, synchronising the
- * device, as [grid][nk][2] unsigned 64-bit values into `out` (capacity `count` values) and sets
- * *grid.  Plans on the per-phase graph path record nothing (*grid = 0). */
+ * k in [k0, k0 + nk) (counted from 0 in launch order), 8 device globaltimer stamps [ns]: [0] when
+ * the CTA entered the barrier, [1] when it left it, [2..7] sub-phase marks of the phase that ends
+ * at that barrier (row phase: spectra staged, packed, inverse x-FFT done, physics done, forward
+ * x-FFT done, spectra written; column phase: tile loaded, forward FFT done, multiplied, inverse
+ * FFT done; 0 = not reached).  pat_plan_read_trace copies them, synchronising the device, as
+ * [grid][nk][8] unsigned 64-bit values into `out` (capacity `count` values) and sets *grid.
+ * Plans on the per-phase graph path record nothing (*grid = 0). */
 pat_status pat_plan_set_trace(pat_plan* plan, int k0, int nk);
 pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t count, int* grid);
 

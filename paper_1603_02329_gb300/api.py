@@ -187,18 +187,18 @@ class PATOperator:
         self._trace_nk = int(nk)
 
     def read_trace(self):
-        """pat_plan_read_trace: uint64 array [grid][nk][2] (entry, exit) in ns, or None."""
+        """pat_plan_read_trace: uint64 array [grid][nk][8] (barrier entry, exit, sub-phase marks) in ns."""
         nk = getattr(self, "_trace_nk", 0)
         if nk == 0:
             return None
-        cap = 4096 * nk * 2
+        cap = 4096 * nk * 8
         buf = np.zeros(cap, dtype=np.uint64)
         grid = ctypes.c_int()
         check(lib().pat_plan_read_trace(self._plan, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), cap,
                                         ctypes.byref(grid)))
         if grid.value == 0:
             return None
-        return buf[: grid.value * nk * 2].reshape(grid.value, nk, 2)
+        return buf[: grid.value * nk * 8].reshape(grid.value, nk, 8)
 
     def close(self):
         if getattr(self, "_plan", None) is not None and self._plan.value:

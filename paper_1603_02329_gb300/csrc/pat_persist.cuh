@@ -42,6 +42,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// trace layout: [grid][nk][kTraceStride]: barrier entry, barrier exit, then sub-phase marks
+constexpr int kTraceStride = 8;
 struct TraceRef {
     unsigned long long* buf;
     int k0, nk;
@@ -54,7 +56,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
     const int kt = (int)k - 1 - tr.k0;
     const bool traced = tr.buf && kt >= 0 && kt < tr.nk;
     if (threadIdx.x == 0) {
-        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * 2] = globaltimer_ns();
+        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * kTraceStride] = globaltimer_ns();
         __threadfence();
         atomicAdd(&gbar[0], 1u);
         const unsigned target = k * nblocks;
@@ -73,7 +75,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
             __nanosleep(32);
         }
         __threadfence();
-        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * 2 + 1] = globaltimer_ns();
+        if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * kTraceStride + 1] = globaltimer_ns();
         *abort_s = ab;
     }
     __syncthreads();
@@ -99,7 +101,15 @@ template <typename T> struct PersistSm {
     T* seg_w;
     int* flag;
     int nx, rmax;
+    TraceRef tr;
+    const unsigned* kb;   // barriers passed so far
     __device__ T* row(int j) const { return res + (size_t)j * rmax * nx; }
+    // sub-phase mark j (call after a __syncthreads): time of the CTA reaching this point
+    __device__ void mark(int j) const {
+        if (!tr.buf || threadIdx.x != 0) return;
+        const int kt = (int)*kb - tr.k0;
+        if (kt >= 0 && kt < tr.nk) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * kTraceStride + 2 + j] = globaltimer_ns();
+    }
 };
 
 template <typename T> __host__ __device__ size_t persist_work_elems(int nx, int ny, int ldh, int rmax, int W) {
@@ -151,9 +161,13 @@ __device__ cplx<T>* prow_c2r(const PersistSm<T>& s, const DevPlan<T>& P, int F, 
     cp_commit();
     cp_wait_all();
     __syncthreads();
+    s.mark(0);
     c2r_pack(A, S, F, R, P.nx, P.ldh);
     __syncthreads();
-    return fft_rows<T, true>(A, B, P.fx, s.twx, F * R / 2);
+    s.mark(1);
+    cplx<T>* r = fft_rows<T, true>(A, B, P.fx, s.twx, F * R / 2);
+    s.mark(2);
+    return r;
 }
 template <typename T> __device__ cplx<T>* prow_other(const PersistSm<T>& s, const DevPlan<T>& P, cplx<T>* res) {
     cplx<T>* A = s.work;
@@ -163,8 +177,11 @@ template <typename T>
 __device__ void prow_r2c(const PersistSm<T>& s, const DevPlan<T>& P, cplx<T>* out, cplx<T>* scratch, int F,
                          int line0, int R) {
     __syncthreads();
+    s.mark(3);
     cplx<T>* r = fft_rows<T, false>(out, scratch, P.fx, s.twx, F * R / 2);
+    s.mark(4);
     r2c_unpack(r, P.spec, F, R, line0, P.nx, P.ldh);
+    s.mark(5);
 }
 
 // sensor gather for the CTA's lines (pressure of line r = item r of buf)
@@ -226,20 +243,43 @@ __device__ void pcol(const PersistSm<T>& s, const DevPlan<T>& P, int kx0, int W,
     const int fin = (MODE == SPEC_GRAD) ? 1 : 2;
     const int fout = (MODE == SPEC_GRADT) ? 1 : 2;
     const int LWin = fin * W, LWout = fout * W;
-    const int cpr = (int)((size_t)W * sizeof(cplx<T>) / 16);
-    constexpr int EPC = 16 / (int)sizeof(cplx<T>);
-    for (int f = 0; f < fin; ++f) {
-        const cplx<T>* src = P.spec[f] + base;
-        for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
-            const int i = t / cpr, ch = t - i * cpr;
-            cp_async<16>(X + (size_t)i * LWin + f * W + ch * EPC, src + (size_t)i * es + ch * EPC);
+    if ((size_t)W * sizeof(cplx<T>) >= 16) {
+        const int cpr = (int)((size_t)W * sizeof(cplx<T>) / 16);
+        constexpr int EPC = 16 / (int)sizeof(cplx<T>);
+        for (int f = 0; f < fin; ++f) {
+            const cplx<T>* src = P.spec[f] + base;
+            for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
+                const int i = t / cpr, ch = t - i * cpr;
+                cp_async<16>(X + (size_t)i * LWin + f * W + ch * EPC, src + (size_t)i * es + ch * EPC);
+            }
+        }
+        cp_commit();
+        cp_wait_all();
+    } else {
+        // one complex float per row: 8-byte loads cached in L2 only (the spectra were written by
+        // other CTAs in the previous phase), four in flight per thread
+        for (int f = 0; f < fin; ++f) {
+            const cplx<T>* src = P.spec[f] + base;
+            for (int i0 = threadIdx.x; i0 < L; i0 += 4 * blockDim.x) {
+                cplx<T> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < L) v[u] = __ldcg(src + (size_t)i * es);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < L) X[(size_t)i * LWin + f * W] = v[u];
+                }
+            }
         }
     }
-    cp_commit();
-    cp_wait_all();
     __syncthreads();
+    s.mark(0);
     auto lg = [](int v) { int l = 0; while ((1 << l) < v) ++l; return ((1 << l) == v) ? l : -1; };
     cplx<T>* res = fft_cols<T, false>(X, Y, P.fy, s.twy, LWin, lg(LWin));
+    s.mark(1);
     cplx<T>* spare = (res == X) ? Y : X;
     cplx<T>* O = (MODE == SPEC_GRAD || MODE == SPEC_GRADT) ? Z : res;
     for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
@@ -272,7 +312,9 @@ __device__ void pcol(const PersistSm<T>& s, const DevPlan<T>& P, int kx0, int W,
         }
     }
     __syncthreads();
+    s.mark(2);
     cplx<T>* r = fft_cols<T, true>(O, spare, P.fy, s.twy, LWout, lg(LWout));
+    s.mark(3);
     for (int f = 0; f < fout; ++f) {
         cplx<T>* dst = P.spec[f] + base;
         for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
@@ -286,7 +328,7 @@ __device__ void pcol(const PersistSm<T>& s, const DevPlan<T>& P, int kx0, int W,
 enum PersistSlot : int { PS_U0 = 0, PS_U1, PS_R0, PS_R1, PS_RS, PS_C2, PS_RHO0, PS_B0, PS_B1, PS_C2TAU, PS_C2ETA };
 
 template <typename T, bool ADJ>
-__global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, unsigned* gbar) {
+__global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, unsigned* gbar) {
     PersistSm<T> s = persist_carve<T>(P, C);
     const int nx = P.nx, ny = P.ny, b = blockIdx.x;
     const unsigned G = gridDim.x;
@@ -299,6 +341,8 @@ __global__ void __launch_bounds__(256, 1) k_persist(DevPlan<T> P, PersistCfg C, 
     const int Nt = P.Nt, Ns = P.sens.Ns;
     unsigned kbar = 0;
     const TraceRef TR{P.trace, P.trace_k0, P.trace_nk};
+    s.tr = TR;
+    s.kb = &kbar;
 
     // ---- setup: tables and resident medium ----
     stage16(s.twx, P.twx, (size_t)nx * sizeof(cplx<T>));

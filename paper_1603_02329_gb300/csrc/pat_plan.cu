@@ -534,7 +534,7 @@ pat_status pat_plan_set_trace(pat_plan* plan, int k0, int nk) {
     b->trace_k0 = k0;
     b->trace_nk = nk;
     if (nk == 0) return PAT_OK;
-    const size_t bytes = (size_t)b->persist_grid * nk * 2 * sizeof(unsigned long long);
+    const size_t bytes = (size_t)b->persist_grid * nk * 8 * sizeof(unsigned long long);
     cudaError_t e = cudaMalloc(&b->trace, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (trace)");
     e = cudaMemset(b->trace, 0, bytes);
@@ -548,7 +548,7 @@ pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t c
     PlanBase* b = plan->impl;
     *grid = 0;
     if (!b->trace) return PAT_OK;
-    const size_t n = (size_t)b->persist_grid * b->trace_nk * 2;
+    const size_t n = (size_t)b->persist_grid * b->trace_nk * 8;
     if (!out || count < n) return fail(PAT_EINVAL, "trace buffer too small");
     DeviceGuard g(b->device);
     cudaError_t e = cudaDeviceSynchronize();

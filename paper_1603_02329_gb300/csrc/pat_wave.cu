@@ -203,60 +203,78 @@ template <typename T> struct Plan : public PlanBase {
     // persistent single-kernel path (2-D grids whose per-CTA state fits in shared memory)
     // ---------------------------------------------------------------------------------------
     PersistCfg pcfg{};
+    int persist_threads = 256;
 
     pat_status configure_persistent(const HostTables& h) {
         persistent = 0;
         const char* env = std::getenv("PAT_PERSIST");
         if (env && std::atoi(env) == 0) return PAT_OK;
         if (h.d != 2) return PAT_OK;
-        int W = (sizeof(T) == 4) ? 2 : 1;   // 16-byte rows: the tiles are read around L1
-        int lgW = (W == 2) ? 1 : 0;
-        const int ntiles = (h.nxh + W - 1) / W;
-        const int npairs = h.ny / 2;
-        const int ppc = (npairs + ntiles - 1) / ntiles;
-        const int G = std::max(ntiles, (npairs + ppc - 1) / ppc);
-        pcfg.W = W;
-        pcfg.lgW = lgW;
-        pcfg.ntiles = ntiles;
-        pcfg.ppc = ppc;
-        pcfg.rmax = 2 * ppc;
-        pcfg.nres = 11;
-        const size_t smem = persist_smem_bytes<T>(h.nx, h.ny, h.ldh, pcfg.rmax, W, pcfg.nres);
-        int dev = 0, optin = 0, nsm = 0;
+        int dev = 0, optin = 0, nsm = 0, coop = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         const bool dbg = std::getenv("PAT_DEBUG") != nullptr;
-        if (dbg)
-            fprintf(stderr, "[pat] persistent: G=%d W=%d ppc=%d smem=%zu optin=%d nsm=%d coop=%d\n", G, W, ppc, smem,
-                    optin, nsm, coop);
-        if (!coop || smem > (size_t)optin) return PAT_OK;
+        if (!coop) return PAT_OK;
         cudaError_t e = cudaFuncSetAttribute((const void*)k_persist<T, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute((const void*)k_persist<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      optin);
         if (e != cudaSuccess) {
-            if (dbg) fprintf(stderr, "[pat] persistent: set attribute failed: %s\n", cudaGetErrorString(e));
             cudaGetLastError();
             return PAT_OK;
         }
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T, false>, 256, smem);
-        if (dbg) fprintf(stderr, "[pat] persistent: per_sm=%d (%s)\n", per_sm, cudaGetErrorString(e));
-        if (e != cudaSuccess || per_sm * nsm < G) {
-            cudaGetLastError();
+        // Candidate layouts, least work per CTA first (columns per CTA W, x-line pairs per CTA):
+        // the first whose grid is co-resident wins.
+        const int cands[][2] = {{2, 2}, {1, 1}, {2, 1}, {4, 2}, {4, 4}, {8, 4}, {8, 8}};
+        int forced_w = 0, forced_p = 0;
+        if (const char* ew = std::getenv("PAT_PERSIST_W")) forced_w = std::atoi(ew);
+        if (const char* ep = std::getenv("PAT_PERSIST_PPC")) forced_p = std::atoi(ep);
+        for (const auto& cnd : cands) {
+            const int W = cnd[0], ppc = cnd[1];
+            if (forced_w && W != forced_w) continue;
+            if (forced_p && ppc != forced_p) continue;
+            if (sizeof(T) == 8 && W > 4) continue;
+            const int ntiles = (h.nxh + W - 1) / W;
+            const int npairs = h.ny / 2;
+            const int G = std::max(ntiles, (npairs + ppc - 1) / ppc);
+            PersistCfg c{};
+            c.W = W;
+            c.lgW = (W == 1) ? 0 : (W == 2 ? 1 : (W == 4 ? 2 : 3));
+            c.ntiles = ntiles;
+            c.ppc = ppc;
+            c.rmax = 2 * ppc;
+            c.nres = 11;
+            const int need = std::max(c.rmax * h.nx / 8, 2 * W * h.ny / 8);
+            const int threads = std::min(256, std::max(64, (need + 31) / 32 * 32));
+            const size_t smem = persist_smem_bytes<T>(h.nx, h.ny, h.ldh, c.rmax, W, c.nres);
+            if (smem > (size_t)optin) continue;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T, false>, threads, smem);
+            int per_sm_a = 0;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_persist<T, true>, threads, smem);
+            if (dbg)
+                fprintf(stderr, "[pat] persistent cand W=%d ppc=%d G=%d threads=%d smem=%zu per_sm=%d/%d\n", W, ppc,
+                        G, threads, smem, per_sm, per_sm_a);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (std::min(per_sm, per_sm_a) * nsm < G) continue;
+            pat_status st = PAT_OK;
+            gbar = dalloc<unsigned>(4, &st);
+            if (!gbar) return st;
+            pcfg = c;
+            persist_grid = G;
+            persist_smem = smem;
+            persist_threads = threads;
+            persistent = 1;
+            info.path = 1;
             return PAT_OK;
         }
-        pat_status st = PAT_OK;
-        gbar = dalloc<unsigned>(4, &st);
-        if (!gbar) return st;
-        persist_grid = G;
-        persist_smem = smem;
-        persistent = 1;
-        info.path = 1;
         return PAT_OK;
     }
 
@@ -282,7 +300,7 @@ template <typename T> struct Plan : public PlanBase {
         }
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(persist_grid);
-        lc.blockDim = dim3(256);
+        lc.blockDim = dim3(persist_threads);
         lc.dynamicSmemBytes = persist_smem;
         lc.stream = s;
         cudaLaunchAttribute attr[1];

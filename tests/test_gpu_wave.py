@@ -214,8 +214,9 @@ def test_both_2d_paths_agree_with_oracle(dev, monkeypatch):
     ref = Operator.from_problem(pb)
     h = np.random.default_rng(13).standard_normal((pb.Nt, ref.Ns))
     d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
-    for flag, path in (("1", 1), ("0", 0)):
+    for flag, path, width in (("1", 1, "0"), ("1", 1, "2"), ("0", 0, "0")):
         monkeypatch.setenv("PAT_PERSIST", flag)
+        monkeypatch.setenv("PAT_PERSIST_W", width)   # 0: automatic layout; 2: two columns per CTA
         for prec, tol in (("f32", TOL32), ("f64", TOL64)):
             op = _gpu_op(pb, prec, dev)
             assert op.info.path == path

@@ -377,14 +377,15 @@ def main():
                  "frac": value * B_pt / world / peak}
 
     slots_f = 6 if op.lossy else 4
-    persistent = int(op.info.path) == 1
+    persistent = int(op.info.path) >= 1
     launches = args.steps * 2 * (1 if persistent else (1 + (pb.Nt - 1) * slots_f))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
                           parallelism=f"replicas x{world}",
-                          path="persistent kernel per solve" if persistent else "CUDA graph of per-phase kernels"),
+                          path={0: "CUDA graph of per-phase kernels", 1: "persistent kernel per solve",
+                                2: "persistent kernel per solve, register-fused power-of-two transforms"}[int(op.info.path)]),
            "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels,
            "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -83,7 +83,8 @@ typedef struct {
     pat_precision precision;
     double dt;
     double c_ref;       /* max sound speed (kappa correction, PML scaling) */
-    int path;           /* 0: CUDA graph of per-phase kernels; 1: one persistent kernel per solve */
+    int path;           /* 0: CUDA graph of per-phase kernels; 1: one persistent kernel per solve;
+                           2: the same, register-fused transforms (power-of-two 2-D grids) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

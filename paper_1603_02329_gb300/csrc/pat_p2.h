@@ -1,0 +1,37 @@
+// pat_p2.h -- host-side view of the power-of-two persistent kernel (pat_persist2.cuh): its
+// shared-memory layout and its launch entry, compiled in a translation unit per precision.
+#pragma once
+
+#include "pat_kernels.cuh"
+
+namespace pat {
+
+struct PersistCfg;
+
+__host__ __device__ __forceinline__ int p2_tab_len(int n) { return 2 * n; }
+
+// ---- shared-memory layout (pow2 kernel) ----
+// twx[2 nx] | twy[2 ny] | dpl[ny] | dml[ny] | cdp[8] | cdm[8] | work | gb[rmax / 2 nx] (complex)
+// | res[nres][rmax][nx] | ax, aux[nx] | ay, auy | kl2 | ckx2 | seg_w (real) | seg_i | flag (int)
+template <typename T> __host__ __device__ size_t p2_work_elems(int nx, int ny, int rmax, int W) {
+    const size_t rowp = (size_t)2 * rmax * nx;
+    const size_t colp = (size_t)4 * W * ny;
+    return rowp > colp ? rowp : colp;
+}
+template <typename T> size_t p2_smem_bytes(int nx, int ny, int rmax, int W, int nres) {
+    size_t b = (size_t)(p2_tab_len(nx) + p2_tab_len(ny) + 2 * ny + 16 + p2_work_elems<T>(nx, ny, rmax, W) +
+                        (size_t)(rmax / 2) * nx) *
+               sizeof(cplx<T>);
+    b += (size_t)((size_t)nres * rmax * nx + 2 * nx + 2 * ((rmax + 3) & ~3) + ((ny + 3) & ~3) + 8 + 2 * kSegCap) *
+         sizeof(T);
+    b += (size_t)(2 * kSegCap + 4) * sizeof(int);
+    return b;
+}
+
+// launch k_persist2<T, adjoint> with `lc` (cooperative attributes set by the caller)
+template <typename T>
+cudaError_t p2_launch(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<T>& P, const PersistCfg& C,
+                      unsigned* gbar);
+template <typename T> const void* p2_kernel(bool adjoint);
+
+}  // namespace pat

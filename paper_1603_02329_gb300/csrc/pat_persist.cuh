@@ -90,6 +90,7 @@ template <typename T> struct PersistSm {
     cplx<T>* cdp;
     cplx<T>* cdm;
     cplx<T>* work;   // row phase: A | B | S ; column phase: X | Y | Z
+    cplx<T>* gb;     // power-of-two kernel: sensor gather / injection buffer (rows packed in pairs)
     T* res;          // resident fields [nres][rmax][nx]
     T* ax;           // a, au along x
     T* aux;

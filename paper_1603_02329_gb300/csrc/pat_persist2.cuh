@@ -1,0 +1,710 @@
+// pat_persist2.cuh -- the persistent 2-D solve for power-of-two grids, with register-fused
+// transforms.
+//
+// Same resident-state scheme, phases, barriers and arithmetic as k_persist (pat_persist.cuh);
+// what changes is how a phase moves its data.  The generic phase stages the half spectra in
+// shared memory, packs them, runs an inverse transform (one shared-memory round trip per stage),
+// applies the physics, runs the forward transform and unpacks: ten shared-memory passes and nine
+// CTA barriers.  Here, for n = 2^lg, the Stockham schedule is fixed -- forward radices
+// (r0, 8, ..., 8), inverse radices the reverse (8, ..., 8, r0) -- so that
+//   * the first stage of a transform loads its operands straight from the L2-resident spectra
+//     (the C2R packing of two real lines is done on the loaded values);
+//   * the last stage of the first transform and the first stage of the second one act on the
+//     same elements {j + r n / R}: the thread that finishes butterfly j keeps its outputs in
+//     registers, applies the pointwise physics (row phase) or the k-space multiply (column phase)
+//     and runs the next transform's first butterfly on them;
+//   * the last forward x-stage holds both X[k] and X[n - k] in one thread (it takes butterflies j
+//     and m - j), so the R2C unpacking and the store to the spectra happen in registers.
+// A phase is then four shared-memory round trips for n = 512 and two for n = 64.  Shared-memory
+// lines are XOR-swizzled (element e at e ^ ((e >> 3) & 15)) so that the strided Stockham stores
+// are free of bank conflicts, and every stage reads its twiddles from its own table laid out
+// [r - 1][k], consecutive in k.
+#pragma once
+
+#include <type_traits>
+
+#include "pat_persist.cuh"
+#include "pat_p2.h"
+
+namespace pat {
+
+// ---- fixed power-of-two Stockham schedule ----
+// nst = ceil(lg / 3) stages (lg >= 4); forward stage s: radix r0 (s = 0) or 8, Ns = 1 (s = 0) or
+// r0 8^(s - 1); inverse stage s: radix 8 (s < nst - 1) or r0, Ns = 8^s.
+struct P2Axis {
+    int n, lg, nst, r0;
+};
+__host__ __device__ __forceinline__ P2Axis p2_axis(int lg) {
+    P2Axis a;
+    a.lg = lg;
+    a.n = 1 << lg;
+    a.nst = (lg + 2) / 3;
+    a.r0 = 1 << (lg - 3 * (a.nst - 1));
+    return a;
+}
+__device__ __forceinline__ int p2_fns(const P2Axis& a, int s) { return s == 0 ? 1 : a.r0 << (3 * (s - 1)); }
+__device__ __forceinline__ int p2_ins(int s) { return 1 << (3 * s); }
+__device__ __forceinline__ int p2_ir(const P2Axis& a, int s) { return s == a.nst - 1 ? a.r0 : 8; }
+// twiddle tables of one axis: forward stages 1..nst-1, then inverse stages 1..nst-1 (< 2 n entries)
+__device__ __forceinline__ int p2_off_f(const P2Axis& a, int s) { return p2_fns(a, s) - a.r0; }
+__device__ __forceinline__ int p2_off_i(const P2Axis& a, int s) { return a.n - a.r0 + p2_ins(s) - 8; }
+
+__device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
+template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
+
+// stage tables from the full table tw[m] = exp(-2 pi i m / n): entry (r, k) of a stage of radix R
+// and span Ns is tw[r k n / (Ns R)] (a copy, no new rounding)
+template <typename T> __device__ void p2_build_tables(cplx<T>* tab, const cplx<T>* tw, const P2Axis& a) {
+    for (int s = 1; s < a.nst; ++s) {
+        const int NsF = p2_fns(a, s), NsI = p2_ins(s), RI = p2_ir(a, s);
+        const int stepF = a.n / (NsF * 8), stepI = a.n / (NsI * RI);
+        cplx<T>* tf = tab + p2_off_f(a, s);
+        cplx<T>* ti = tab + p2_off_i(a, s);
+        for (int t = threadIdx.x; t < 7 * NsF; t += blockDim.x) {
+            const int r = t / NsF + 1, k = t - (r - 1) * NsF;
+            tf[t] = tw[r * k * stepF];
+        }
+        for (int t = threadIdx.x; t < (RI - 1) * NsI; t += blockDim.x) {
+            const int r = t / NsI + 1, k = t - (r - 1) * NsI;
+            ti[t] = tw[r * k * stepI];
+        }
+    }
+}
+
+// butterfly j of a stage (span Ns, stride m = n / R): load elements j + r m of `src`, twiddle
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void p2_load(cplx<T> (&v)[R], const cplx<T>* src, int j, int m, int Ns,
+                                        const cplx<T>* tws) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[swz(j + r * m)];
+    if (Ns > 1) {
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            const cplx<T> w = tws[(r - 1) * Ns + k];
+            v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+        }
+    }
+}
+template <typename T, int R>
+__device__ __forceinline__ void p2_store(cplx<T>* dst, int j, int Ns, const cplx<T> (&v)[R]) {
+    const int k = j & (Ns - 1);
+    const int b = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[swz(b + r * Ns)] = v[r];
+}
+
+// the middle stages 1 .. nst-2 (radix 8) over `nlines` lines, each followed by a CTA barrier
+template <typename T, bool INV>
+__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines) {
+    const int lgm = ax.lg - 3, m = 1 << lgm;
+    for (int s = 1; s + 1 < ax.nst; ++s) {
+        const int Ns = INV ? p2_ins(s) : p2_fns(ax, s);
+        const cplx<T>* tws = tab + (INV ? p2_off_i(ax, s) : p2_off_f(ax, s));
+        for (int t = threadIdx.x; t < (nlines << lgm); t += blockDim.x) {
+            const int line = t >> lgm, j = t & (m - 1);
+            cplx<T> v[8];
+            p2_load<T, 8, INV>(v, a + (size_t)line * ax.n, j, m, Ns, tws);
+            dft<T, 8, INV>(v);
+            p2_store<T, 8>(b + (size_t)line * ax.n, j, Ns, v);
+        }
+        __syncthreads();
+        cplx<T>* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+template <class Fn> __device__ __forceinline__ void with_radix(int r, Fn&& fn) {
+    if (r == 8) fn(std::integral_constant<int, 8>{});
+    else if (r == 4) fn(std::integral_constant<int, 4>{});
+    else fn(std::integral_constant<int, 2>{});
+}
+
+// ---------------------------------------------------------------------------------------------
+// row phase: complex line q = f np + p holds rows 2p (real part) and 2p + 1 (imaginary part) of
+// field f of the CTA's R = 2 np rows
+// ---------------------------------------------------------------------------------------------
+// inverse x-stage 0 (radix 8, no twiddles) on the C2R packing of the half spectra, read from L2
+template <typename T>
+__device__ void p2_row_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int np, int line0, const P2Axis& ax,
+                          int ldh) {
+    const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, half = n >> 1;
+    for (int t = threadIdx.x; t < ((FI * np) << lgm); t += blockDim.x) {
+        const int q = t >> lgm, j = t & (m - 1);
+        const int f = q / np, p = q - f * np;
+        const cplx<T>* a = spec[f] + (size_t)(line0 + 2 * p) * ldh;
+        const cplx<T>* b = a + ldh;
+        cplx<T> A[8], B[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int k = j + r * m;
+            const int kk = k <= half ? k : n - k;
+            A[r] = __ldcg(a + kk);
+            B[r] = __ldcg(b + kk);
+        }
+        cplx<T> v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int k = j + r * m;
+            if (k == 0 || k == half) {
+                A[r].y = 0;
+                B[r].y = 0;
+            }
+            v[r] = (k <= half) ? mkc<T>(A[r].x - B[r].y, A[r].y + B[r].x)    // A + i B
+                               : mkc<T>(A[r].x + B[r].y, B[r].x - A[r].y);   // conj(A) + i conj(B)
+        }
+        dft<T, 8, true>(v);
+        p2_store<T, 8>(dst + (size_t)q * n, j, 1, v);
+    }
+}
+
+// Last inverse x-stage (radix R, Ns = n / R) of FI fields, the pointwise physics
+// pw(row, x, in[FI], out[FO]) on every element, and -- when `fwd` -- forward x-stage 0 of the FO
+// outputs.  FI = 0: pw reads its inputs itself.
+template <typename T, int R, int FI, int FO, class PW>
+__device__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax, int np,
+                            bool fwd, PW&& pw) {
+    const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
+    const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
+    for (int t = threadIdx.x; t < (np << lgm); t += blockDim.x) {
+        const int p = t >> lgm, j = t & (m - 1);
+        cplx<T> z[FI > 0 ? FI : 1][R];
+#pragma unroll
+        for (int f = 0; f < FI; ++f) {
+            p2_load<T, R, true>(z[f], src + (size_t)(f * np + p) * n, j, m, m, twl);
+            dft<T, R, true>(z[f]);
+        }
+        cplx<T> o[FO > 0 ? FO : 1][R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int x = j + r * m;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                T in[FI > 0 ? FI : 1], out[FO > 0 ? FO : 1] = {};
+#pragma unroll
+                for (int f = 0; f < FI; ++f) in[f] = h ? z[f][r].y : z[f][r].x;
+                pw(2 * p + h, x, in, out);
+#pragma unroll
+                for (int g = 0; g < FO; ++g) {
+                    if (h) o[g][r].y = out[g];
+                    else o[g][r].x = out[g];
+                }
+            }
+        }
+        if (fwd) {
+#pragma unroll
+            for (int g = 0; g < FO; ++g) {
+                dft<T, R, false>(o[g]);
+                p2_store<T, R>(dst + (size_t)(g * np + p) * n, j, 1, o[g]);
+            }
+        }
+    }
+}
+
+// last forward x-stage (radix 8, Ns = n / 8) and R2C unpacking into the half spectra: unit u of a
+// line runs butterflies u and m - u (u = 0: 0 and m / 2), which hold every X[k] with its X[n - k]
+template <typename T>
+__device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, const P2Axis& ax,
+                           int FO, int np, int line0, int ldh) {
+    const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, lgh = lgm - 1, hm = m >> 1;
+    const cplx<T>* twl = tab + p2_off_f(ax, ax.nst - 1);
+    for (int t = threadIdx.x; t < ((FO * np) << lgh); t += blockDim.x) {
+        const int q = t >> lgh, u = t & (hm - 1);
+        const int f = q / np, p = q - f * np;
+        const int j1 = u, j2 = (u == 0) ? hm : m - u;
+        const cplx<T>* line = src + (size_t)q * n;
+        cplx<T> X1[8], X2[8];
+        p2_load<T, 8, false>(X1, line, j1, m, m, twl);
+        p2_load<T, 8, false>(X2, line, j2, m, m, twl);
+        dft<T, 8, false>(X1);
+        dft<T, 8, false>(X2);
+        cplx<T>* a = spec[f] + (size_t)(line0 + 2 * p) * ldh;
+        cplx<T>* b = a + ldh;
+        auto put = [&](int k, cplx<T> zk, cplx<T> zm) {
+            a[k] = mkc<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            b[k] = mkc<T>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+        };
+        if (u != 0) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                put(j1 + r * m, X1[r], X2[7 - r]);
+                put(j2 + r * m, X2[r], X1[7 - r]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r <= 4; ++r) put(r * m, X1[r], X1[(8 - r) & 7]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) put(hm + r * m, X2[r], X2[7 - r]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// column phase: line q = f W + c is column kx0 + c of field f (length ny)
+// ---------------------------------------------------------------------------------------------
+// forward y-stage 0 (radix R, no twiddles) on columns read from L2
+template <typename T, int R>
+__device__ void p2_col_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int W, int lgW, int kx0, int nxh,
+                          const P2Axis& ay, int ldh) {
+    const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
+    for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
+        const cplx<T>* src = spec[f] + min(kx0 + c, nxh - 1);
+        cplx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcg(src + (size_t)(j + r * m) * ldh);
+        dft<T, R, false>(v);
+        p2_store<T, R>(dst + (size_t)(f * W + c) * n, j, 1, v);
+    }
+}
+
+// last forward y-stage (radix 8, Ns = n / 8), the k-space multiply of MODE, inverse y-stage 0
+template <typename T, int MODE>
+__device__ void p2_col_fuse(const PersistSm<T>& s, const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst,
+                            const P2Axis& ay, int W, int lgW) {
+    constexpr int FI = (MODE == SPEC_GRAD) ? 1 : 2;
+    constexpr int FO = (MODE == SPEC_GRADT) ? 1 : 2;
+    const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
+    const cplx<T>* twl = s.twy + p2_off_f(ay, ay.nst - 1);
+    for (int t = threadIdx.x; t < (W << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = t >> lgW;
+        cplx<T> z[FI][8];
+#pragma unroll
+        for (int f = 0; f < FI; ++f) {
+            p2_load<T, 8, false>(z[f], src + (size_t)(f * W + c) * n, j, m, m, twl);
+            dft<T, 8, false>(z[f]);
+        }
+        cplx<T> o[FO][8];
+        const T kx2 = s.ckx2[c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = j + r * m;
+            const T k2 = kx2 + s.kl2[i];
+            if constexpr (MODE == SPEC_ABS) {
+                const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+                const T s1 = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
+                o[0][r] = cscale(z[0][r], s0);
+                o[1][r] = cscale(z[FI - 1][r], s1);
+            } else {
+                const T kap = sinc_sq(P.kap_a * P.kap_a * k2) * P.invN;
+                constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
+                const T sg = (MODE == SPEC_DIVT || MODE == SPEC_GRADT) ? -kap : kap;
+                const cplx<T> m0 = plus ? s.cdp[c] : s.cdm[c];
+                const cplx<T> m1 = plus ? s.dpl[i] : s.dml[i];
+                if constexpr (MODE == SPEC_GRAD) {
+                    const cplx<T> v = cscale(z[0][r], sg);
+                    o[0][r] = cmul(v, m0);
+                    o[FO - 1][r] = cmul(v, m1);
+                } else if constexpr (MODE == SPEC_GRADT) {
+                    o[0][r] = cscale(cadd(cmul(z[0][r], m0), cmul(z[FI - 1][r], m1)), sg);
+                } else {
+                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
+                    o[FO - 1][r] = cscale(cmul(z[FI - 1][r], m1), sg);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < FO; ++g) {
+            dft<T, 8, true>(o[g]);
+            p2_store<T, 8>(dst + (size_t)(g * W + c) * n, j, 1, o[g]);
+        }
+    }
+}
+
+// last inverse y-stage (radix R, Ns = n / R), stored to the spectra (valid columns only)
+template <typename T, int R>
+__device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, int FO, int W, int lgW,
+                           int kx0, int wv, const P2Axis& ay, int ldh) {
+    const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
+    const cplx<T>* twl = tab + p2_off_i(ay, ay.nst - 1);
+    for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
+        cplx<T> v[R];
+        p2_load<T, R, true>(v, src + (size_t)(f * W + c) * n, j, m, m, twl);
+        dft<T, R, true>(v);
+        if (c < wv) {
+            cplx<T>* dst = spec[f] + kx0 + c;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[(size_t)(j + r * m) * ldh] = v[r];
+        }
+    }
+}
+
+// whole column phase of MODE for columns [kx0, kx0 + W)
+template <typename T, int MODE>
+__device__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& P, const P2Axis& ay, int kx0, int W, int lgW) {
+    constexpr int FI = (MODE == SPEC_GRAD) ? 1 : 2;
+    constexpr int FO = (MODE == SPEC_GRADT) ? 1 : 2;
+    cplx<T>* A = s.work;
+    cplx<T>* B = A + (size_t)2 * W * ay.n;
+    with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, P.spec, FI, W, lgW, kx0, P.nxh, ay, P.ldh); });
+    __syncthreads();
+    s.mark(0);
+    cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, FI * W);
+    cplx<T>* b = (a == A) ? B : A;
+    s.mark(1);
+    p2_col_fuse<T, MODE>(s, P, a, b, ay, W, lgW);
+    __syncthreads();
+    s.mark(2);
+    a = p2_mid<T, true>(b, a, ay, s.twy, FO * W);
+    s.mark(3);
+    const int wv = min(W, P.nxh - kx0);
+    with_radix(ay.r0, [&](auto RC) {
+        p2_col_out<T, decltype(RC)::value>(a, P.spec, s.twy, FO, W, lgW, kx0, wv, ay, P.ldh);
+    });
+}
+
+template <typename T> __device__ PersistSm<T> p2_carve(const DevPlan<T>& P, const PersistCfg& C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PersistSm<T> s;
+    s.nx = P.nx;
+    s.rmax = C.rmax;
+    s.twx = reinterpret_cast<cplx<T>*>(smem_raw);
+    s.twy = s.twx + p2_tab_len(P.nx);
+    s.dpl = s.twy + p2_tab_len(P.ny);
+    s.dml = s.dpl + P.ny;
+    s.cdp = s.dml + P.ny;
+    s.cdm = s.cdp + 8;
+    s.work = s.cdm + 8;
+    s.gb = s.work + p2_work_elems<T>(P.nx, P.ny, C.rmax, C.W);
+    s.res = reinterpret_cast<T*>(s.gb + (size_t)(C.rmax / 2) * P.nx);
+    s.ax = s.res + (size_t)C.nres * C.rmax * P.nx;
+    s.aux = s.ax + P.nx;
+    s.ay = s.aux + P.nx;
+    s.auy = s.ay + ((C.rmax + 3) & ~3);
+    s.kl2 = s.auy + ((C.rmax + 3) & ~3);
+    s.ckx2 = s.kl2 + ((P.ny + 3) & ~3);
+    s.seg_w = s.ckx2 + 8;
+    s.seg_i = reinterpret_cast<int*>(s.seg_w + 2 * kSegCap);
+    s.flag = s.seg_i + 2 * kSegCap;
+    return s;
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, unsigned* gbar) {
+    PersistSm<T> s = p2_carve<T>(P, C);
+    const int nx = P.nx, ny = P.ny, b = blockIdx.x;
+    const unsigned G = gridDim.x;
+    const int pair0 = b * C.ppc;
+    const int npair = max(0, min(ny / 2 - pair0, C.ppc));
+    const int R = 2 * npair, line0 = 2 * pair0;
+    const bool rows = R > 0, tile = b < C.ntiles;
+    const int kx0 = b * C.W;
+    const T dt = P.dt;
+    const int Nt = P.Nt, Ns = P.sens.Ns;
+    const P2Axis axx = p2_axis(P.fx.lgn), axy = p2_axis(P.fy.lgn);
+    unsigned kbar = 0;
+    const TraceRef TR{P.trace, P.trace_k0, P.trace_nk};
+    s.tr = TR;
+    s.kb = &kbar;
+    cplx<T>* const A = s.work;
+    cplx<T>* const B = s.work + (size_t)s.rmax * nx;
+
+    // ---- setup: stage twiddle tables, tables and resident medium ----
+    p2_build_tables<T>(s.twx, P.twx, axx);
+    p2_build_tables<T>(s.twy, P.twy, axy);
+    stage16(s.dpl, P.dp[1], (size_t)ny * sizeof(cplx<T>));
+    stage16(s.dml, P.dm[1], (size_t)ny * sizeof(cplx<T>));
+    stage_elems(s.ax, P.a[0], nx);
+    stage_elems(s.aux, P.au[0], nx);
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) {
+        const T k = P.kv[1][i];
+        s.kl2[i] = k * k;
+    }
+    if (threadIdx.x < (unsigned)C.W && tile) {
+        const int kx = min(kx0 + (int)threadIdx.x, P.nxh - 1);
+        s.cdp[threadIdx.x] = P.dp[0][kx];
+        s.cdm[threadIdx.x] = P.dm[0][kx];
+        const T k = P.kv[0][kx];
+        s.ckx2[threadIdx.x] = k * k;
+    }
+    for (int t = threadIdx.x; t < npair * nx; t += blockDim.x) s.gb[t] = mkc<T>(0, 0);
+    int2 seg = make_int2(0, 0);
+    if (rows) {
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+            s.ay[r] = P.a[1][line0 + r];
+            s.auy[r] = P.au[1][line0 + r];
+        }
+        stage_rows(s.row(PS_C2), P.c2, line0, R, nx);
+        stage_rows(s.row(PS_RHO0), P.rho0, line0, R, nx);
+        stage_rows(s.row(PS_B0), P.b[0], line0, R, nx);
+        stage_rows(s.row(PS_B1), P.b[1], line0, R, nx);
+        if (P.lossy) {
+            stage_rows(s.row(PS_C2TAU), P.c2tau, line0, R, nx);
+            stage_rows(s.row(PS_C2ETA), P.c2eta, line0, R, nx);
+        }
+        if (!ADJ) stage_rows(s.row(PS_RS), P.img, line0, R, nx);   // p0 (consumed by the init)
+        const DevSensors<T>& S = P.sens;
+        if (!ADJ) {
+            seg = make_int2(S.g_lineptr[line0], S.g_lineptr[line0 + R]);
+            for (int t = threadIdx.x; t < min(seg.y - seg.x, kSegCap); t += blockDim.x) {
+                const int q = seg.x + t;
+                s.seg_i[2 * t] = S.g_seg_sensor[q];
+                s.seg_i[2 * t + 1] = (S.g_seg_line[q] - line0) * nx + S.g_seg_x0[q];
+                s.seg_w[2 * t] = S.g_seg_w0[q];
+                s.seg_w[2 * t + 1] = S.g_seg_w1[q];
+            }
+        } else {
+            seg = make_int2(S.s_lineptr[line0], S.s_lineptr[line0 + R]);
+            for (int t = threadIdx.x; t < min(seg.y - seg.x, kSegCap); t += blockDim.x) {
+                const int q = seg.x + t;
+                s.seg_i[t] = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
+            }
+        }
+    }
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+
+    auto pml_a = [&](int xi, int r, int i) { return xi == 0 ? s.ax[i] : s.ay[r]; };
+    auto pml_au = [&](int xi, int r, int i) { return xi == 0 ? s.aux[i] : s.auy[r]; };
+
+    // Row phase: inverse x-transform of FI spectra (FI > 0), pointwise pw, and -- when `fwd` --
+    // forward x-transform of the FO outputs into the spectra.  `post` runs after the first CTA
+    // barrier that follows the pointwise step (sensor gather from gb).
+    auto row_phase = [&](auto FIc, auto FOc, bool fwd, auto&& pw, auto&& post) {
+        constexpr int FI = decltype(FIc)::value, FO = decltype(FOc)::value;
+        cplx<T>* a = A;
+        cplx<T>* bb = B;
+        if constexpr (FI > 0) {
+            p2_row_in<T>(A, P.spec, FI, npair, line0, axx, P.ldh);
+            __syncthreads();
+            s.mark(0);
+            a = p2_mid<T, true>(A, B, axx, s.twx, FI * npair);
+            bb = (a == A) ? B : A;
+        }
+        s.mark(1);
+        with_radix(axx.r0, [&](auto RC) {
+            p2_row_fuse<T, decltype(RC)::value, FI, FO>(a, bb, s.twx, axx, npair, fwd, pw);
+        });
+        __syncthreads();
+        s.mark(2);
+        post();
+        if (!fwd) return;
+        cplx<T>* c = p2_mid<T, false>(bb, a, axx, s.twx, FO * npair);
+        s.mark(3);
+        p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, line0, P.ldh);
+        s.mark(4);
+    };
+    auto none = [] {};
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+
+    if constexpr (!ADJ) {
+        // ================= forward: initial state, then Nt - 1 steps =================
+        if (rows) {
+            row_phase(
+                I0{}, I1{}, Nt > 1,
+                [&](int r, int i, const T*, T* out) {
+                    const int t = r * nx + i;
+                    const T p = s.row(PS_RS)[t];
+                    const T rh = p / ((T)2 * s.row(PS_C2)[t]);
+                    s.row(PS_R0)[t] = rh;
+                    s.row(PS_R1)[t] = rh;
+                    slot(s.gb, r, i, nx) = p;
+                    out[0] = p;
+                },
+                [&] { pgather(s, P, seg, line0, s.gb, P.data); });
+        }
+        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        for (int n = 0; n + 1 < Nt; ++n) {
+            const bool last = (n + 2 == Nt);
+            T* drow = P.data + (size_t)(n + 1) * Ns;
+            // (1) g = D+ p
+            if (tile) p2_col<T, SPEC_GRAD>(s, P, axy, kx0, C.W, C.lgW);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            // u update, x-FFT of u
+            if (rows)
+                row_phase(
+                    I2{}, I2{}, true,
+                    [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+#pragma unroll
+                        for (int xi = 0; xi < 2; ++xi) {
+                            const T g = in[xi];
+                            const T bb = s.row(PS_B0 + xi)[t];
+                            const T au = pml_au(xi, r, i);
+                            const T uo = (n == 0) ? (T)0.5 * dt * bb * g : s.row(PS_U0 + xi)[t];
+                            const T un = au * (au * uo - dt * bb * g);
+                            s.row(PS_U0 + xi)[t] = un;
+                            out[xi] = un;
+                        }
+                    },
+                    none);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            // (2) e = D- u
+            if (tile) p2_col<T, SPEC_DIV>(s, P, axy, kx0, C.W, C.lgW);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            // rho update; lossless: p, sample; lossy: x-FFT of (dd, r)
+            if (rows) {
+                auto rho_upd = [&](int r, int i, const T* in, T& rs, T& es) {
+                    const int t = r * nx + i;
+                    const T rho0 = s.row(PS_RHO0)[t];
+                    rs = 0;
+                    es = 0;
+#pragma unroll
+                    for (int xi = 0; xi < 2; ++xi) {
+                        const T e = in[xi];
+                        const T a = pml_a(xi, r, i);
+                        const T rh = a * (a * s.row(PS_R0 + xi)[t] - dt * rho0 * e);
+                        s.row(PS_R0 + xi)[t] = rh;
+                        rs += rh;
+                        es += e;
+                    }
+                    return rho0;
+                };
+                if (P.lossy) {
+                    row_phase(
+                        I2{}, I2{}, true,
+                        [&](int r, int i, const T* in, T* out) {
+                            T rs, es;
+                            const T rho0 = rho_upd(r, i, in, rs, es);
+                            s.row(PS_RS)[r * nx + i] = rs;
+                            out[0] = rho0 * es;
+                            out[1] = rs;
+                        },
+                        none);
+                } else {
+                    row_phase(
+                        I2{}, I1{}, !last,
+                        [&](int r, int i, const T* in, T* out) {
+                            T rs, es;
+                            rho_upd(r, i, in, rs, es);
+                            const T p = s.row(PS_C2)[r * nx + i] * rs;
+                            slot(s.gb, r, i, nx) = p;
+                            out[0] = p;
+                        },
+                        [&] { pgather(s, P, seg, line0, s.gb, drow); });
+                }
+            }
+            if (P.lossy) {
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                // (3) fractional Laplacians
+                if (tile) p2_col<T, SPEC_ABS>(s, P, axy, kx0, C.W, C.lgW);
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (rows)
+                    row_phase(
+                        I2{}, I1{}, !last,
+                        [&](int r, int i, const T* in, T* out) {
+                            const int t = r * nx + i;
+                            const T p = s.row(PS_C2)[t] * s.row(PS_RS)[t] + s.row(PS_C2TAU)[t] * in[0] -
+                                        s.row(PS_C2ETA)[t] * in[1];
+                            slot(s.gb, r, i, nx) = p;
+                            out[0] = p;
+                        },
+                        [&] { pgather(s, P, seg, line0, s.gb, drow); });
+            }
+            if (!last && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        }
+    } else {
+        // ================= adjoint: reverse time, exact transpose =================
+        // resident: u_bar (PS_U0/1), rho_bar (PS_R0/1), p_bar (PS_RS).  M^T h is scattered into gb
+        // (kept zero between uses: the pointwise step that reads an element clears it).
+        if (rows) {
+            for (int j = 0; j < 4; ++j)
+                for (int t = threadIdx.x; t < R * nx; t += blockDim.x) s.row(PS_U0 + j)[t] = 0;
+        }
+        // p_bar of time level n at (r, i) -> the final gradient, or the inputs of the next transforms
+        auto tail = [&](int r, int i, T pv, bool final_, T* out) {
+            const int t = r * nx + i;
+            if (final_) {
+                const T sr = s.row(PS_R0)[t] + s.row(PS_R1)[t];
+                P.img[(size_t)(line0 + r) * nx + i] = pv + sr / ((T)2 * s.row(PS_C2)[t]);
+                return;
+            }
+            if (P.lossy) {
+                s.row(PS_RS)[t] = pv;
+                out[0] = s.row(PS_C2TAU)[t] * pv;
+                out[1] = s.row(PS_C2ETA)[t] * pv;
+            } else {
+                const T rbar = s.row(PS_C2)[t] * pv;
+                const T rho0 = s.row(PS_RHO0)[t];
+#pragma unroll
+                for (int xi = 0; xi < 2; ++xi) {
+                    const T a = pml_a(xi, r, i);
+                    const T rb = s.row(PS_R0 + xi)[t] + rbar;
+                    out[xi] = -dt * rho0 * a * rb;
+                    s.row(PS_R0 + xi)[t] = a * a * rb;
+                }
+            }
+        };
+        auto take_inj = [&](int r, int i) {
+            T& g = slot(s.gb, r, i, nx);
+            const T v = g;
+            g = (T)0;
+            return v;
+        };
+        if (rows) {
+            pscatter(s, P, seg, line0, s.gb, P.data + (size_t)(Nt - 1) * Ns);
+            __syncthreads();
+            row_phase(
+                I0{}, I2{}, Nt > 1,
+                [&](int r, int i, const T*, T* out) { tail(r, i, take_inj(r, i), Nt == 1, out); }, none);
+        }
+        if (Nt == 1) return;
+        if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        for (int n = Nt - 2; n >= 0; --n) {
+            const bool final_ = (n == 0);
+            if (P.lossy) {
+                if (tile) p2_col<T, SPEC_ABS>(s, P, axy, kx0, C.W, C.lgW);
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (rows)
+                    row_phase(
+                        I2{}, I2{}, true,
+                        [&](int r, int i, const T* in, T* out) {
+                            const int t = r * nx + i;
+                            const T ddbar = in[0];
+                            const T rbar = s.row(PS_C2)[t] * s.row(PS_RS)[t] - in[1];
+                            const T rho0 = s.row(PS_RHO0)[t];
+#pragma unroll
+                            for (int xi = 0; xi < 2; ++xi) {
+                                const T a = pml_a(xi, r, i);
+                                const T rb = s.row(PS_R0 + xi)[t] + rbar;
+                                out[xi] = rho0 * ddbar - dt * rho0 * a * rb;
+                                s.row(PS_R0 + xi)[t] = a * a * rb;
+                            }
+                        },
+                        none);
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            }
+            // transpose of e = D- u
+            if (tile) p2_col<T, SPEC_DIVT>(s, P, axy, kx0, C.W, C.lgW);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (rows)
+                row_phase(
+                    I2{}, I2{}, true,
+                    [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+#pragma unroll
+                        for (int xi = 0; xi < 2; ++xi) {
+                            const T bb = s.row(PS_B0 + xi)[t];
+                            const T au = pml_au(xi, r, i);
+                            T ub = s.row(PS_U0 + xi)[t] + in[xi];
+                            T g = -dt * bb * au * ub;
+                            ub = au * au * ub;
+                            if (final_) g += (T)0.5 * dt * bb * ub;
+                            s.row(PS_U0 + xi)[t] = ub;
+                            out[xi] = g;
+                        }
+                    },
+                    none);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            // transpose of g = D+ p; injection of M^T h^n
+            if (tile) p2_col<T, SPEC_GRADT>(s, P, axy, kx0, C.W, C.lgW);
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (rows) {
+                pscatter(s, P, seg, line0, s.gb, P.data + (size_t)n * Ns);
+                row_phase(
+                    I1{}, I2{}, !final_,
+                    [&](int r, int i, const T* in, T* out) { tail(r, i, in[0] + take_inj(r, i), final_, out); },
+                    none);
+            }
+            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        }
+    }
+}
+
+}  // namespace pat

@@ -8,6 +8,7 @@
 
 #include "pat_host.h"
 #include "pat_persist.cuh"
+#include "pat_p2.h"
 
 namespace pat {
 
@@ -204,6 +205,7 @@ template <typename T> struct Plan : public PlanBase {
     // ---------------------------------------------------------------------------------------
     PersistCfg pcfg{};
     int persist_threads = 256;
+    bool persist_p2 = false;
 
     pat_status configure_persistent(const HostTables& h) {
         persistent = 0;
@@ -217,18 +219,21 @@ template <typename T> struct Plan : public PlanBase {
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         const bool dbg = std::getenv("PAT_DEBUG") != nullptr;
         if (!coop) return PAT_OK;
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_persist<T, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)k_persist<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     optin);
+        // power-of-two axes of 16 .. 2048 points take the register-fused kernel
+        const char* ep2 = std::getenv("PAT_P2");
+        const bool p2 = !(ep2 && std::atoi(ep2) == 0) && h.fx.pow2 && h.fy.pow2 && h.fx.lgn >= 4 &&
+                        h.fy.lgn >= 4 && h.fx.lgn <= 11 && h.fy.lgn <= 11;
+        const void* kf = p2 ? p2_kernel<T>(false) : (const void*)k_persist<T, false>;
+        const void* ka = p2 ? p2_kernel<T>(true) : (const void*)k_persist<T, true>;
+        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return PAT_OK;
         }
         // Candidate layouts, least work per CTA first (columns per CTA W, x-line pairs per CTA):
         // the first whose grid is co-resident wins.
-        const int cands[][2] = {{2, 2}, {1, 1}, {2, 1}, {4, 2}, {4, 4}, {8, 4}, {8, 8}};
+        const int cands[][2] = {{2, 2}, {1, 1}, {2, 1}, {4, 2}, {4, 4}, {8, 4}, {8, 8}, {4, 1}, {8, 1}, {8, 2}};
         int forced_w = 0, forced_p = 0;
         if (const char* ew = std::getenv("PAT_PERSIST_W")) forced_w = std::atoi(ew);
         if (const char* ep = std::getenv("PAT_PERSIST_PPC")) forced_p = std::atoi(ep);
@@ -249,16 +254,16 @@ template <typename T> struct Plan : public PlanBase {
             c.nres = 11;
             const int need = std::max(c.rmax * h.nx / 8, 2 * W * h.ny / 8);
             const int threads = std::min(256, std::max(64, (need + 31) / 32 * 32));
-            const size_t smem = persist_smem_bytes<T>(h.nx, h.ny, h.ldh, c.rmax, W, c.nres);
+            const size_t smem = p2 ? p2_smem_bytes<T>(h.nx, h.ny, c.rmax, W, c.nres)
+                                   : persist_smem_bytes<T>(h.nx, h.ny, h.ldh, c.rmax, W, c.nres);
             if (smem > (size_t)optin) continue;
             int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<T, false>, threads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, threads, smem);
             int per_sm_a = 0;
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, k_persist<T, true>, threads, smem);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, ka, threads, smem);
             if (dbg)
-                fprintf(stderr, "[pat] persistent cand W=%d ppc=%d G=%d threads=%d smem=%zu per_sm=%d/%d\n", W, ppc,
-                        G, threads, smem, per_sm, per_sm_a);
+                fprintf(stderr, "[pat] persistent%s cand W=%d ppc=%d G=%d threads=%d smem=%zu per_sm=%d/%d\n",
+                        p2 ? " (pow2)" : "", W, ppc, G, threads, smem, per_sm, per_sm_a);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 continue;
@@ -271,8 +276,9 @@ template <typename T> struct Plan : public PlanBase {
             persist_grid = G;
             persist_smem = smem;
             persist_threads = threads;
+            persist_p2 = p2;
             persistent = 1;
-            info.path = 1;
+            info.path = p2 ? 2 : 1;
             return PAT_OK;
         }
         return PAT_OK;
@@ -294,7 +300,8 @@ template <typename T> struct Plan : public PlanBase {
                 cudaEventCreate(&probe_ev[g][0]);
                 cudaEventCreate(&probe_ev[g][1]);
             }
-            probe_names[g].assign(1, adjoint ? "k_persist_adj" : "k_persist_fwd");
+            probe_names[g].assign(1, persist_p2 ? (adjoint ? "k_persist2_adj" : "k_persist2_fwd")
+                                                : (adjoint ? "k_persist_adj" : "k_persist_fwd"));
             probe_samples[g] = 1;
             cudaEventRecord(probe_ev[g][0], s);
         }
@@ -311,8 +318,12 @@ template <typename T> struct Plan : public PlanBase {
         P.trace = trace;
         P.trace_k0 = trace_k0;
         P.trace_nk = trace_nk;
-        if (adjoint) e = cudaLaunchKernelEx(&lc, k_persist<T, true>, P, pcfg, gbar);
-        else e = cudaLaunchKernelEx(&lc, k_persist<T, false>, P, pcfg, gbar);
+        if (persist_p2) {
+            e = p2_launch<T>(adjoint, &lc, P, pcfg, gbar);
+        } else {
+            if (adjoint) e = cudaLaunchKernelEx(&lc, k_persist<T, true>, P, pcfg, gbar);
+            else e = cudaLaunchKernelEx(&lc, k_persist<T, false>, P, pcfg, gbar);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernelEx (persistent)");
         if (probe_stride > 0) cudaEventRecord(probe_ev[g][1], s);
         return PAT_OK;

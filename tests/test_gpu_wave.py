@@ -225,6 +225,46 @@ def test_both_2d_paths_agree_with_oracle(dev, monkeypatch):
             op.close()
 
 
+# Power-of-two 2-D grids take the persistent kernel with register-fused transforms (path 2); the
+# cases cover every radix schedule it uses: r0 = 2, 4, 8 and two to four stages per axis
+# (16 = 2.8, 32 = 4.8, 64 = 8.8, 128 = 2.8.8, 256 = 4.8.8, 1024 = 2.8.8.8), non-square grids in both
+# orientations, lossless and absorbing media, FP32 and FP64.  PAT_P2=0 selects the generic
+# persistent kernel on the same plan, which must agree too.
+P2_CASES = [
+    ("16x16_lossless_f64", dict(shape=(16, 16), pml=2, Nt=30, n_sensors=6, alpha0=0.0), "f64"),
+    ("32x64_lossy_f64", dict(shape=(32, 64), pml=4, Nt=60, n_sensors=12), "f64"),
+    ("64x32_lossless_f32", dict(shape=(64, 32), pml=4, Nt=70, n_sensors=12, alpha0=0.0), "f32"),
+    ("128x128_lossy_f32", dict(shape=(128, 128), pml=10, Nt=150, n_sensors=40), "f32"),
+    ("256x32_lossy_f64", dict(shape=(256, 32), pml=4, Nt=50, n_sensors=16), "f64"),
+    ("16x1024_lossy_f32", dict(shape=(16, 1024), pml=2, Nt=40, n_sensors=8, sensor_radius_frac=0.3), "f32"),
+    ("1024x16_lossless_f32", dict(shape=(1024, 16), pml=2, Nt=40, n_sensors=8, alpha0=0.0), "f32"),
+]
+
+
+@pytest.mark.parametrize("name,kw,prec", P2_CASES, ids=[c[0] for c in P2_CASES])
+def test_pow2_persistent_kernel_matches_oracle(dev, monkeypatch, name, kw, prec):
+    pb = synth.small_lossy_2d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(17).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    tol = TOL32 if prec == "f32" else TOL64
+    out = {}
+    for flag, paths in (("1", (2,)), ("0", (1, 0))):
+        # without the fused kernel the plan takes the generic persistent kernel, or the graph path
+        # where the generic kernel's column buffers do not fit (ny = 1024 with four columns per CTA)
+        monkeypatch.setenv("PAT_P2", flag)
+        op = _gpu_op(pb, prec, dev)
+        assert op.info.path in paths
+        path = paths[0]
+        d = op.forward(_t(pb.p0, prec, dev)).cpu().numpy()
+        g = op.adjoint(_t(h, prec, dev)).cpu().numpy()
+        assert rel(d, d_ref) <= tol, (path, rel(d, d_ref))
+        assert rel(g, g_ref) <= tol, (path, rel(g, g_ref))
+        out[path] = (d, g)
+        op.close()
+    assert rel(out[2][0], out[1][0]) <= tol and rel(out[2][1], out[1][1]) <= tol
+
+
 def test_persistent_status_word_ok(dev):
     from paper_1603_02329_gb300 import _lib
 

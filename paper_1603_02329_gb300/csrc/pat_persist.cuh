@@ -98,6 +98,9 @@ template <typename T> struct PersistSm {
     T* auy;
     T* kl2;          // ky^2
     T* ckx2;         // kx^2 of the tile
+    T* kapt;         // power-of-two kernel: kappa / N of the tile, [ky][c]
+    T* s0t;          //   |k|^(y-2) / N and |k|^(y-1) / N of the tile (absorbing media)
+    T* s1t;
     int* seg_i;
     T* seg_w;
     int* flag;

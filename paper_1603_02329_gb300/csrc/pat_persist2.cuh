@@ -160,44 +160,53 @@ __device__ void p2_row_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int np, in
     }
 }
 
-// Last inverse x-stage (radix R, Ns = n / R) of FI fields, the pointwise physics
-// pw(row, x, in[FI], out[FO]) on every element, and -- when `fwd` -- forward x-stage 0 of the FO
-// outputs.  FI = 0: pw reads its inputs itself.
-template <typename T, int R, int FI, int FO, class PW>
-__device__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax, int np,
-                            bool fwd, PW&& pw) {
+// Element loop of the pointwise step of a fused row stage: f(row, x, in[FI], out[FO]) for the
+// 2 R real elements of butterfly j (rows 2p, 2p + 1; x = j + r m)
+template <typename T, int R, int FI, int FO, class F>
+__device__ __forceinline__ void p2_each(int p, int j, int m, const cplx<T> (&z)[2][R], cplx<T> (&o)[2][R], F&& f) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            T in[2], out[2] = {};
+#pragma unroll
+            for (int q = 0; q < FI; ++q) in[q] = h ? z[q][r].y : z[q][r].x;
+            f(2 * p + h, j + r * m, in, out);
+#pragma unroll
+            for (int g = 0; g < FO; ++g) {
+                if (h) o[g][r].y = out[g];
+                else o[g][r].x = out[g];
+            }
+        }
+    }
+}
+
+// Last inverse x-stage (radix R, Ns = n / R) of FI fields, the pointwise step pw(p, j, m, z, o)
+// (z: inverse-transformed inputs, o: outputs, both [2][R] in registers), and -- when `fwd` --
+// forward x-stage 0 of the FO outputs.  FI = 0: pw reads its inputs itself.
+template <typename T, int R, class PW>
+__device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax,
+                                            int np, int FI, int FO, bool fwd, PW&& pw) {
     const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
     for (int t = threadIdx.x; t < (np << lgm); t += blockDim.x) {
         const int p = t >> lgm, j = t & (m - 1);
-        cplx<T> z[FI > 0 ? FI : 1][R];
+        cplx<T> z[2][R], o[2][R];
 #pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            p2_load<T, R, true>(z[f], src + (size_t)(f * np + p) * n, j, m, m, twl);
-            dft<T, R, true>(z[f]);
-        }
-        cplx<T> o[FO > 0 ? FO : 1][R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int x = j + r * m;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                T in[FI > 0 ? FI : 1], out[FO > 0 ? FO : 1] = {};
-#pragma unroll
-                for (int f = 0; f < FI; ++f) in[f] = h ? z[f][r].y : z[f][r].x;
-                pw(2 * p + h, x, in, out);
-#pragma unroll
-                for (int g = 0; g < FO; ++g) {
-                    if (h) o[g][r].y = out[g];
-                    else o[g][r].x = out[g];
-                }
+        for (int f = 0; f < 2; ++f) {
+            if (f < FI) {
+                p2_load<T, R, true>(z[f], src + (size_t)(f * np + p) * n, j, m, m, twl);
+                dft<T, R, true>(z[f]);
             }
         }
+        pw(p, j, m, z, o);
         if (fwd) {
 #pragma unroll
-            for (int g = 0; g < FO; ++g) {
-                dft<T, R, false>(o[g]);
-                p2_store<T, R>(dst + (size_t)(g * np + p) * n, j, 1, o[g]);
+            for (int g = 0; g < 2; ++g) {
+                if (g < FO) {
+                    dft<T, R, false>(o[g]);
+                    p2_store<T, R>(dst + (size_t)(g * np + p) * n, j, 1, o[g]);
+                }
             }
         }
     }
@@ -260,55 +269,79 @@ __device__ void p2_col_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int W, int
     }
 }
 
-// last forward y-stage (radix 8, Ns = n / 8), the k-space multiply of MODE, inverse y-stage 0
-template <typename T, int MODE>
-__device__ void p2_col_fuse(const PersistSm<T>& s, const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst,
-                            const P2Axis& ay, int W, int lgW) {
-    constexpr int FI = (MODE == SPEC_GRAD) ? 1 : 2;
-    constexpr int FO = (MODE == SPEC_GRADT) ? 1 : 2;
+// last forward y-stage (radix 8, Ns = n / 8), the k-space multiply of `mode`, inverse y-stage 0.
+// The multipliers of the CTA's tile are resident: kapt = kappa / N, s0t / s1t = |k|^(y-2) / N and
+// |k|^(y-1) / N (Eq. Twelve's fractional Laplacians), [ky][c]; shift operators per column / row.
+template <typename T>
+__device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>* src, cplx<T>* dst,
+                                            const P2Axis& ay, int W, int lgW, int mode) {
+    const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
     const cplx<T>* twl = s.twy + p2_off_f(ay, ay.nst - 1);
     for (int t = threadIdx.x; t < (W << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = t >> lgW;
-        cplx<T> z[FI][8];
+        cplx<T> z[2][8], o[2][8];
 #pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            p2_load<T, 8, false>(z[f], src + (size_t)(f * W + c) * n, j, m, m, twl);
-            dft<T, 8, false>(z[f]);
-        }
-        cplx<T> o[FO][8];
-        const T kx2 = s.ckx2[c];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int i = j + r * m;
-            const T k2 = kx2 + s.kl2[i];
-            if constexpr (MODE == SPEC_ABS) {
-                const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
-                const T s1 = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
-                o[0][r] = cscale(z[0][r], s0);
-                o[1][r] = cscale(z[FI - 1][r], s1);
-            } else {
-                const T kap = sinc_sq(P.kap_a * P.kap_a * k2) * P.invN;
-                constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
-                const T sg = (MODE == SPEC_DIVT || MODE == SPEC_GRADT) ? -kap : kap;
-                const cplx<T> m0 = plus ? s.cdp[c] : s.cdm[c];
-                const cplx<T> m1 = plus ? s.dpl[i] : s.dml[i];
-                if constexpr (MODE == SPEC_GRAD) {
-                    const cplx<T> v = cscale(z[0][r], sg);
-                    o[0][r] = cmul(v, m0);
-                    o[FO - 1][r] = cmul(v, m1);
-                } else if constexpr (MODE == SPEC_GRADT) {
-                    o[0][r] = cscale(cadd(cmul(z[0][r], m0), cmul(z[FI - 1][r], m1)), sg);
-                } else {
-                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
-                    o[FO - 1][r] = cscale(cmul(z[FI - 1][r], m1), sg);
-                }
+        for (int f = 0; f < 2; ++f) {
+            if (f < fi) {
+                p2_load<T, 8, false>(z[f], src + (size_t)(f * W + c) * n, j, m, m, twl);
+                dft<T, 8, false>(z[f]);
             }
         }
+        switch (mode) {
+            case SPEC_ABS:
 #pragma unroll
-        for (int g = 0; g < FO; ++g) {
-            dft<T, 8, true>(o[g]);
-            p2_store<T, 8>(dst + (size_t)(g * W + c) * n, j, 1, o[g]);
+                for (int r = 0; r < 8; ++r) {
+                    const int e = (j + r * m) * W + c;
+                    o[0][r] = cscale(z[0][r], s.s0t[e]);
+                    o[1][r] = cscale(z[1][r], s.s1t[e]);
+                }
+                break;
+            case SPEC_GRAD: {
+                const cplx<T> m0 = s.cdp[c];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = j + r * m;
+                    const cplx<T> v = cscale(z[0][r], s.kapt[i * W + c]);
+                    o[0][r] = cmul(v, m0);
+                    o[1][r] = cmul(v, s.dpl[i]);
+                }
+            } break;
+            case SPEC_GRADT: {
+                const cplx<T> m0 = s.cdm[c];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = j + r * m;
+                    o[0][r] = cscale(cadd(cmul(z[0][r], m0), cmul(z[1][r], s.dml[i])), -s.kapt[i * W + c]);
+                }
+            } break;
+            case SPEC_DIV: {
+                const cplx<T> m0 = s.cdm[c];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = j + r * m;
+                    const T sg = s.kapt[i * W + c];
+                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
+                    o[1][r] = cscale(cmul(z[1][r], s.dml[i]), sg);
+                }
+            } break;
+            default: {   // SPEC_DIVT
+                const cplx<T> m0 = s.cdp[c];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = j + r * m;
+                    const T sg = -s.kapt[i * W + c];
+                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
+                    o[1][r] = cscale(cmul(z[1][r], s.dpl[i]), sg);
+                }
+            } break;
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (g < fo) {
+                dft<T, 8, true>(o[g]);
+                p2_store<T, 8>(dst + (size_t)(g * W + c) * n, j, 1, o[g]);
+            }
         }
     }
 }
@@ -332,27 +365,27 @@ __device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
     }
 }
 
-// whole column phase of MODE for columns [kx0, kx0 + W)
-template <typename T, int MODE>
-__device__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& P, const P2Axis& ay, int kx0, int W, int lgW) {
-    constexpr int FI = (MODE == SPEC_GRAD) ? 1 : 2;
-    constexpr int FO = (MODE == SPEC_GRADT) ? 1 : 2;
+// whole column phase of `mode` for columns [kx0, kx0 + W)
+template <typename T>
+__device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& P, const P2Axis& ay, int kx0, int W,
+                                       int lgW, int mode) {
+    const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     cplx<T>* A = s.work;
     cplx<T>* B = A + (size_t)2 * W * ay.n;
-    with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, P.spec, FI, W, lgW, kx0, P.nxh, ay, P.ldh); });
+    with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, P.spec, fi, W, lgW, kx0, P.nxh, ay, P.ldh); });
     __syncthreads();
     s.mark(0);
-    cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, FI * W);
+    cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, fi * W);
     cplx<T>* b = (a == A) ? B : A;
     s.mark(1);
-    p2_col_fuse<T, MODE>(s, P, a, b, ay, W, lgW);
+    p2_col_fuse<T>(s, a, b, ay, W, lgW, mode);
     __syncthreads();
     s.mark(2);
-    a = p2_mid<T, true>(b, a, ay, s.twy, FO * W);
+    a = p2_mid<T, true>(b, a, ay, s.twy, fo * W);
     s.mark(3);
     const int wv = min(W, P.nxh - kx0);
     with_radix(ay.r0, [&](auto RC) {
-        p2_col_out<T, decltype(RC)::value>(a, P.spec, s.twy, FO, W, lgW, kx0, wv, ay, P.ldh);
+        p2_col_out<T, decltype(RC)::value>(a, P.spec, s.twy, fo, W, lgW, kx0, wv, ay, P.ldh);
     });
 }
 
@@ -376,10 +409,57 @@ template <typename T> __device__ PersistSm<T> p2_carve(const DevPlan<T>& P, cons
     s.auy = s.ay + ((C.rmax + 3) & ~3);
     s.kl2 = s.auy + ((C.rmax + 3) & ~3);
     s.ckx2 = s.kl2 + ((P.ny + 3) & ~3);
-    s.seg_w = s.ckx2 + 8;
+    s.kapt = s.ckx2 + 8;
+    const int tl = (C.W * P.ny + 3) & ~3;
+    s.s0t = s.kapt + tl;
+    s.s1t = s.s0t + (P.lossy ? tl : 0);
+    s.seg_w = s.kapt + (P.lossy ? 3 : 1) * tl;
     s.seg_i = reinterpret_cast<int*>(s.seg_w + 2 * kSegCap);
     s.flag = s.seg_i + 2 * kSegCap;
     return s;
+}
+
+
+// row phases of the two solves (the column phases are the SpecMode values)
+enum P2Row : int {
+    R_F_INIT = 0,        // p0 -> rho_xi, sample p^0, x-FFT of p^0
+    R_F_U,               // u update from D+ p, x-FFT of u
+    R_F_RHO_LOSSY,       // rho update from D- u, x-FFT of (rho0 div u, rho)
+    R_F_RHO_LOSSLESS,    // rho update, p = c0^2 rho, sample, x-FFT of p
+    R_F_P,               // p with the fractional-Laplacian terms, sample, x-FFT of p
+    R_A_INIT,            // M^T h^(Nt-1) -> tail
+    R_A_ABS,             // transpose of the absorption terms
+    R_A_DIVT,            // transpose of e = D- u and the u update
+    R_A_GRADT            // transpose of g = D+ p, M^T h^n -> tail
+};
+
+// Phase k of a solve: a column phase (col = true, SpecMode) or a row phase (P2Row), with its time
+// level n.  Forward: phase 0 = R_F_INIT, then per step n = 0 .. Nt-2 the sequence GRAD, U, DIV,
+// RHO (lossless) or GRAD, U, DIV, RHO, ABS, P (absorbing).  Adjoint: phase 0 = R_A_INIT, then per
+// level n = Nt-2 .. 0 the sequence DIVT, A_DIVT, GRADT, A_GRADT, preceded by ABS, A_ABS when
+// absorbing.
+struct P2Phase {
+    bool col;
+    int id, n;
+};
+template <bool ADJ> __device__ __forceinline__ P2Phase p2_phase(int k, int Nt, bool lossy) {
+    P2Phase d{false, ADJ ? (int)R_A_INIT : (int)R_F_INIT, ADJ ? Nt - 1 : 0};
+    if (k == 0) return d;
+    const int PP = lossy ? 6 : 4;
+    const int q = (k - 1) / PP, sub = (k - 1) - q * PP;
+    d.n = ADJ ? Nt - 2 - q : q;
+    if (!ADJ) {
+        const int col_id[6] = {SPEC_GRAD, R_F_U, SPEC_DIV, R_F_RHO_LOSSY, SPEC_ABS, R_F_P};
+        d.col = (sub & 1) == 0;
+        d.id = col_id[sub];
+        if (!lossy && sub == 3) d.id = R_F_RHO_LOSSLESS;
+    } else {
+        const int ids[6] = {SPEC_ABS, R_A_ABS, SPEC_DIVT, R_A_DIVT, SPEC_GRADT, R_A_GRADT};
+        const int s6 = lossy ? sub : sub + 2;
+        d.col = (s6 & 1) == 0;
+        d.id = ids[s6];
+    }
+    return d;
 }
 
 template <typename T, bool ADJ>
@@ -402,23 +482,30 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
     cplx<T>* const A = s.work;
     cplx<T>* const B = s.work + (size_t)s.rmax * nx;
 
-    // ---- setup: stage twiddle tables, tables and resident medium ----
+    // ---- setup: stage twiddle tables, k-space tables of the tile, resident medium ----
     p2_build_tables<T>(s.twx, P.twx, axx);
     p2_build_tables<T>(s.twy, P.twy, axy);
     stage16(s.dpl, P.dp[1], (size_t)ny * sizeof(cplx<T>));
     stage16(s.dml, P.dm[1], (size_t)ny * sizeof(cplx<T>));
     stage_elems(s.ax, P.a[0], nx);
     stage_elems(s.aux, P.au[0], nx);
-    for (int i = threadIdx.x; i < ny; i += blockDim.x) {
-        const T k = P.kv[1][i];
-        s.kl2[i] = k * k;
-    }
     if (threadIdx.x < (unsigned)C.W && tile) {
         const int kx = min(kx0 + (int)threadIdx.x, P.nxh - 1);
         s.cdp[threadIdx.x] = P.dp[0][kx];
         s.cdm[threadIdx.x] = P.dm[0][kx];
-        const T k = P.kv[0][kx];
-        s.ckx2[threadIdx.x] = k * k;
+    }
+    if (tile) {
+        // the same expressions the per-phase multiply would evaluate (bit-identical multipliers)
+        for (int t = threadIdx.x; t < ny * C.W; t += blockDim.x) {
+            const int i = t >> C.lgW, c = t & (C.W - 1);
+            const T kx = P.kv[0][min(kx0 + c, P.nxh - 1)], ky = P.kv[1][i];
+            const T k2 = kx * kx + ky * ky;
+            s.kapt[t] = sinc_sq(P.kap_a * P.kap_a * k2) * P.invN;
+            if (P.lossy) {
+                s.s0t[t] = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+                s.s1t[t] = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
+            }
+        }
     }
     for (int t = threadIdx.x; t < npair * nx; t += blockDim.x) s.gb[t] = mkc<T>(0, 0);
     int2 seg = make_int2(0, 0);
@@ -452,6 +539,8 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                 const int q = seg.x + t;
                 s.seg_i[t] = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
             }
+            for (int j = 0; j < 4; ++j)
+                for (int t = threadIdx.x; t < R * nx; t += blockDim.x) s.row(PS_U0 + j)[t] = 0;
         }
     }
     cp_commit();
@@ -460,250 +549,209 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
 
     auto pml_a = [&](int xi, int r, int i) { return xi == 0 ? s.ax[i] : s.ay[r]; };
     auto pml_au = [&](int xi, int r, int i) { return xi == 0 ? s.aux[i] : s.auy[r]; };
+    // adjoint: M^T h is scattered into gb, which stays zero between uses (the pointwise step that
+    // reads an element clears it)
+    auto take_inj = [&](int r, int i) {
+        T& g = slot(s.gb, r, i, nx);
+        const T v = g;
+        g = (T)0;
+        return v;
+    };
+    // adjoint: p_bar of the current level at (r, i) -> the gradient (final level), else the
+    // inputs of the next x-transforms
+    auto tail = [&](int r, int i, T pv, bool final_, T* out) {
+        const int t = r * nx + i;
+        if (final_) {
+            const T sr = s.row(PS_R0)[t] + s.row(PS_R1)[t];
+            P.img[(size_t)(line0 + r) * nx + i] = pv + sr / ((T)2 * s.row(PS_C2)[t]);
+            return;
+        }
+        if (P.lossy) {
+            s.row(PS_RS)[t] = pv;
+            out[0] = s.row(PS_C2TAU)[t] * pv;
+            out[1] = s.row(PS_C2ETA)[t] * pv;
+        } else {
+            const T rbar = s.row(PS_C2)[t] * pv;
+            const T rho0 = s.row(PS_RHO0)[t];
+#pragma unroll
+            for (int xi = 0; xi < 2; ++xi) {
+                const T a = pml_a(xi, r, i);
+                const T rb = s.row(PS_R0 + xi)[t] + rbar;
+                out[xi] = -dt * rho0 * a * rb;
+                s.row(PS_R0 + xi)[t] = a * a * rb;
+            }
+        }
+    };
+    // forward: rho update from e = D- u at (r, i); returns rho0, sets sum_xi rho_xi and sum_xi e_xi
+    auto rho_upd = [&](int r, int i, const T* in, T& rs, T& es) {
+        const int t = r * nx + i;
+        const T rho0 = s.row(PS_RHO0)[t];
+        rs = 0;
+        es = 0;
+#pragma unroll
+        for (int xi = 0; xi < 2; ++xi) {
+            const T e = in[xi];
+            const T a = pml_a(xi, r, i);
+            const T rh = a * (a * s.row(PS_R0 + xi)[t] - dt * rho0 * e);
+            s.row(PS_R0 + xi)[t] = rh;
+            rs += rh;
+            es += e;
+        }
+        return rho0;
+    };
 
-    // Row phase: inverse x-transform of FI spectra (FI > 0), pointwise pw, and -- when `fwd` --
-    // forward x-transform of the FO outputs into the spectra.  `post` runs after the first CTA
-    // barrier that follows the pointwise step (sensor gather from gb).
-    auto row_phase = [&](auto FIc, auto FOc, bool fwd, auto&& pw, auto&& post) {
-        constexpr int FI = decltype(FIc)::value, FO = decltype(FOc)::value;
+    // One row phase: inverse x-transform of FI spectra, the pointwise step of `pid`, and the
+    // forward x-transform of its FO outputs (unless it ends the solve); sensor sampling from gb
+    // after the pointwise step, M^T h injected through gb before it.
+    auto row_phase = [&](int pid, int n, bool lastph) {
+        int FI = 2, FO = 2;
+        bool fwd = true, gath = false, scat = false;
+        switch (pid) {
+            case R_F_INIT: FI = 0; FO = 1; fwd = !lastph; gath = true; break;
+            case R_F_RHO_LOSSLESS:
+            case R_F_P: FO = 1; fwd = !lastph; gath = true; break;
+            case R_A_INIT: FI = 0; fwd = !lastph; scat = true; break;
+            case R_A_GRADT: FI = 1; fwd = !lastph; scat = true; break;
+            default: break;
+        }
+        const bool first = (n == 0);
+        T* drow = P.data + (size_t)(ADJ ? n : (pid == R_F_INIT ? 0 : n + 1)) * Ns;
         cplx<T>* a = A;
         cplx<T>* bb = B;
-        if constexpr (FI > 0) {
+        if (scat) pscatter(s, P, seg, line0, s.gb, drow);
+        if (FI > 0) {
             p2_row_in<T>(A, P.spec, FI, npair, line0, axx, P.ldh);
             __syncthreads();
             s.mark(0);
             a = p2_mid<T, true>(A, B, axx, s.twx, FI * npair);
             bb = (a == A) ? B : A;
+        } else {
+            __syncthreads();
         }
         s.mark(1);
+        auto pw = [&](int p, int j, int m, auto& z, auto& o) {
+            constexpr int RR = sizeof(z[0]) / sizeof(z[0][0]);
+            switch (pid) {
+                case R_F_INIT:
+                    p2_each<T, RR, 0, 1>(p, j, m, z, o, [&](int r, int i, const T*, T* out) {
+                        const int t = r * nx + i;
+                        const T pv = s.row(PS_RS)[t];
+                        const T rh = pv / ((T)2 * s.row(PS_C2)[t]);
+                        s.row(PS_R0)[t] = rh;
+                        s.row(PS_R1)[t] = rh;
+                        slot(s.gb, r, i, nx) = pv;
+                        out[0] = pv;
+                    });
+                    break;
+                case R_F_U:
+                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+#pragma unroll
+                        for (int xi = 0; xi < 2; ++xi) {
+                            const T g = in[xi];
+                            const T bq = s.row(PS_B0 + xi)[t];
+                            const T au = pml_au(xi, r, i);
+                            const T uo = first ? (T)0.5 * dt * bq * g : s.row(PS_U0 + xi)[t];
+                            const T un = au * (au * uo - dt * bq * g);
+                            s.row(PS_U0 + xi)[t] = un;
+                            out[xi] = un;
+                        }
+                    });
+                    break;
+                case R_F_RHO_LOSSY:
+                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        T rs, es;
+                        const T rho0 = rho_upd(r, i, in, rs, es);
+                        s.row(PS_RS)[r * nx + i] = rs;
+                        out[0] = rho0 * es;
+                        out[1] = rs;
+                    });
+                    break;
+                case R_F_RHO_LOSSLESS:
+                    p2_each<T, RR, 2, 1>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        T rs, es;
+                        rho_upd(r, i, in, rs, es);
+                        const T pv = s.row(PS_C2)[r * nx + i] * rs;
+                        slot(s.gb, r, i, nx) = pv;
+                        out[0] = pv;
+                    });
+                    break;
+                case R_F_P:
+                    p2_each<T, RR, 2, 1>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+                        const T pv = s.row(PS_C2)[t] * s.row(PS_RS)[t] + s.row(PS_C2TAU)[t] * in[0] -
+                                     s.row(PS_C2ETA)[t] * in[1];
+                        slot(s.gb, r, i, nx) = pv;
+                        out[0] = pv;
+                    });
+                    break;
+                case R_A_INIT:
+                    p2_each<T, RR, 0, 2>(p, j, m, z, o, [&](int r, int i, const T*, T* out) {
+                        tail(r, i, take_inj(r, i), lastph, out);
+                    });
+                    break;
+                case R_A_ABS:
+                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+                        const T ddbar = in[0];
+                        const T rbar = s.row(PS_C2)[t] * s.row(PS_RS)[t] - in[1];
+                        const T rho0 = s.row(PS_RHO0)[t];
+#pragma unroll
+                        for (int xi = 0; xi < 2; ++xi) {
+                            const T a = pml_a(xi, r, i);
+                            const T rb = s.row(PS_R0 + xi)[t] + rbar;
+                            out[xi] = rho0 * ddbar - dt * rho0 * a * rb;
+                            s.row(PS_R0 + xi)[t] = a * a * rb;
+                        }
+                    });
+                    break;
+                case R_A_DIVT:
+                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        const int t = r * nx + i;
+#pragma unroll
+                        for (int xi = 0; xi < 2; ++xi) {
+                            const T bq = s.row(PS_B0 + xi)[t];
+                            const T au = pml_au(xi, r, i);
+                            T ub = s.row(PS_U0 + xi)[t] + in[xi];
+                            T g = -dt * bq * au * ub;
+                            ub = au * au * ub;
+                            if (first) g += (T)0.5 * dt * bq * ub;
+                            s.row(PS_U0 + xi)[t] = ub;
+                            out[xi] = g;
+                        }
+                    });
+                    break;
+                default:   // R_A_GRADT
+                    p2_each<T, RR, 1, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                        tail(r, i, in[0] + take_inj(r, i), lastph, out);
+                    });
+                    break;
+            }
+        };
         with_radix(axx.r0, [&](auto RC) {
-            p2_row_fuse<T, decltype(RC)::value, FI, FO>(a, bb, s.twx, axx, npair, fwd, pw);
+            p2_row_fuse<T, decltype(RC)::value>(a, bb, s.twx, axx, npair, FI, FO, fwd, pw);
         });
         __syncthreads();
         s.mark(2);
-        post();
+        if (gath) pgather(s, P, seg, line0, s.gb, drow);
         if (!fwd) return;
         cplx<T>* c = p2_mid<T, false>(bb, a, axx, s.twx, FO * npair);
         s.mark(3);
         p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, line0, P.ldh);
         s.mark(4);
     };
-    auto none = [] {};
-    using I0 = std::integral_constant<int, 0>;
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
 
-    if constexpr (!ADJ) {
-        // ================= forward: initial state, then Nt - 1 steps =================
-        if (rows) {
-            row_phase(
-                I0{}, I1{}, Nt > 1,
-                [&](int r, int i, const T*, T* out) {
-                    const int t = r * nx + i;
-                    const T p = s.row(PS_RS)[t];
-                    const T rh = p / ((T)2 * s.row(PS_C2)[t]);
-                    s.row(PS_R0)[t] = rh;
-                    s.row(PS_R1)[t] = rh;
-                    slot(s.gb, r, i, nx) = p;
-                    out[0] = p;
-                },
-                [&] { pgather(s, P, seg, line0, s.gb, P.data); });
+    // ---- the solve: one loop over its phases, one call site per phase kind ----
+    const int nph = (Nt > 1) ? 1 + (Nt - 1) * (P.lossy ? 6 : 4) : 1;
+    for (int k = 0; k < nph; ++k) {
+        const P2Phase d = p2_phase<ADJ>(k, Nt, P.lossy != 0);
+        const bool lastph = (k == nph - 1);
+        if (d.col) {
+            if (tile) p2_col<T>(s, P, axy, kx0, C.W, C.lgW, d.id);
+        } else if (rows) {
+            row_phase(d.id, d.n, lastph);
         }
-        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-        for (int n = 0; n + 1 < Nt; ++n) {
-            const bool last = (n + 2 == Nt);
-            T* drow = P.data + (size_t)(n + 1) * Ns;
-            // (1) g = D+ p
-            if (tile) p2_col<T, SPEC_GRAD>(s, P, axy, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            // u update, x-FFT of u
-            if (rows)
-                row_phase(
-                    I2{}, I2{}, true,
-                    [&](int r, int i, const T* in, T* out) {
-                        const int t = r * nx + i;
-#pragma unroll
-                        for (int xi = 0; xi < 2; ++xi) {
-                            const T g = in[xi];
-                            const T bb = s.row(PS_B0 + xi)[t];
-                            const T au = pml_au(xi, r, i);
-                            const T uo = (n == 0) ? (T)0.5 * dt * bb * g : s.row(PS_U0 + xi)[t];
-                            const T un = au * (au * uo - dt * bb * g);
-                            s.row(PS_U0 + xi)[t] = un;
-                            out[xi] = un;
-                        }
-                    },
-                    none);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            // (2) e = D- u
-            if (tile) p2_col<T, SPEC_DIV>(s, P, axy, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            // rho update; lossless: p, sample; lossy: x-FFT of (dd, r)
-            if (rows) {
-                auto rho_upd = [&](int r, int i, const T* in, T& rs, T& es) {
-                    const int t = r * nx + i;
-                    const T rho0 = s.row(PS_RHO0)[t];
-                    rs = 0;
-                    es = 0;
-#pragma unroll
-                    for (int xi = 0; xi < 2; ++xi) {
-                        const T e = in[xi];
-                        const T a = pml_a(xi, r, i);
-                        const T rh = a * (a * s.row(PS_R0 + xi)[t] - dt * rho0 * e);
-                        s.row(PS_R0 + xi)[t] = rh;
-                        rs += rh;
-                        es += e;
-                    }
-                    return rho0;
-                };
-                if (P.lossy) {
-                    row_phase(
-                        I2{}, I2{}, true,
-                        [&](int r, int i, const T* in, T* out) {
-                            T rs, es;
-                            const T rho0 = rho_upd(r, i, in, rs, es);
-                            s.row(PS_RS)[r * nx + i] = rs;
-                            out[0] = rho0 * es;
-                            out[1] = rs;
-                        },
-                        none);
-                } else {
-                    row_phase(
-                        I2{}, I1{}, !last,
-                        [&](int r, int i, const T* in, T* out) {
-                            T rs, es;
-                            rho_upd(r, i, in, rs, es);
-                            const T p = s.row(PS_C2)[r * nx + i] * rs;
-                            slot(s.gb, r, i, nx) = p;
-                            out[0] = p;
-                        },
-                        [&] { pgather(s, P, seg, line0, s.gb, drow); });
-                }
-            }
-            if (P.lossy) {
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-                // (3) fractional Laplacians
-                if (tile) p2_col<T, SPEC_ABS>(s, P, axy, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-                if (rows)
-                    row_phase(
-                        I2{}, I1{}, !last,
-                        [&](int r, int i, const T* in, T* out) {
-                            const int t = r * nx + i;
-                            const T p = s.row(PS_C2)[t] * s.row(PS_RS)[t] + s.row(PS_C2TAU)[t] * in[0] -
-                                        s.row(PS_C2ETA)[t] * in[1];
-                            slot(s.gb, r, i, nx) = p;
-                            out[0] = p;
-                        },
-                        [&] { pgather(s, P, seg, line0, s.gb, drow); });
-            }
-            if (!last && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-        }
-    } else {
-        // ================= adjoint: reverse time, exact transpose =================
-        // resident: u_bar (PS_U0/1), rho_bar (PS_R0/1), p_bar (PS_RS).  M^T h is scattered into gb
-        // (kept zero between uses: the pointwise step that reads an element clears it).
-        if (rows) {
-            for (int j = 0; j < 4; ++j)
-                for (int t = threadIdx.x; t < R * nx; t += blockDim.x) s.row(PS_U0 + j)[t] = 0;
-        }
-        // p_bar of time level n at (r, i) -> the final gradient, or the inputs of the next transforms
-        auto tail = [&](int r, int i, T pv, bool final_, T* out) {
-            const int t = r * nx + i;
-            if (final_) {
-                const T sr = s.row(PS_R0)[t] + s.row(PS_R1)[t];
-                P.img[(size_t)(line0 + r) * nx + i] = pv + sr / ((T)2 * s.row(PS_C2)[t]);
-                return;
-            }
-            if (P.lossy) {
-                s.row(PS_RS)[t] = pv;
-                out[0] = s.row(PS_C2TAU)[t] * pv;
-                out[1] = s.row(PS_C2ETA)[t] * pv;
-            } else {
-                const T rbar = s.row(PS_C2)[t] * pv;
-                const T rho0 = s.row(PS_RHO0)[t];
-#pragma unroll
-                for (int xi = 0; xi < 2; ++xi) {
-                    const T a = pml_a(xi, r, i);
-                    const T rb = s.row(PS_R0 + xi)[t] + rbar;
-                    out[xi] = -dt * rho0 * a * rb;
-                    s.row(PS_R0 + xi)[t] = a * a * rb;
-                }
-            }
-        };
-        auto take_inj = [&](int r, int i) {
-            T& g = slot(s.gb, r, i, nx);
-            const T v = g;
-            g = (T)0;
-            return v;
-        };
-        if (rows) {
-            pscatter(s, P, seg, line0, s.gb, P.data + (size_t)(Nt - 1) * Ns);
-            __syncthreads();
-            row_phase(
-                I0{}, I2{}, Nt > 1,
-                [&](int r, int i, const T*, T* out) { tail(r, i, take_inj(r, i), Nt == 1, out); }, none);
-        }
-        if (Nt == 1) return;
-        if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-        for (int n = Nt - 2; n >= 0; --n) {
-            const bool final_ = (n == 0);
-            if (P.lossy) {
-                if (tile) p2_col<T, SPEC_ABS>(s, P, axy, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-                if (rows)
-                    row_phase(
-                        I2{}, I2{}, true,
-                        [&](int r, int i, const T* in, T* out) {
-                            const int t = r * nx + i;
-                            const T ddbar = in[0];
-                            const T rbar = s.row(PS_C2)[t] * s.row(PS_RS)[t] - in[1];
-                            const T rho0 = s.row(PS_RHO0)[t];
-#pragma unroll
-                            for (int xi = 0; xi < 2; ++xi) {
-                                const T a = pml_a(xi, r, i);
-                                const T rb = s.row(PS_R0 + xi)[t] + rbar;
-                                out[xi] = rho0 * ddbar - dt * rho0 * a * rb;
-                                s.row(PS_R0 + xi)[t] = a * a * rb;
-                            }
-                        },
-                        none);
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            }
-            // transpose of e = D- u
-            if (tile) p2_col<T, SPEC_DIVT>(s, P, axy, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            if (rows)
-                row_phase(
-                    I2{}, I2{}, true,
-                    [&](int r, int i, const T* in, T* out) {
-                        const int t = r * nx + i;
-#pragma unroll
-                        for (int xi = 0; xi < 2; ++xi) {
-                            const T bb = s.row(PS_B0 + xi)[t];
-                            const T au = pml_au(xi, r, i);
-                            T ub = s.row(PS_U0 + xi)[t] + in[xi];
-                            T g = -dt * bb * au * ub;
-                            ub = au * au * ub;
-                            if (final_) g += (T)0.5 * dt * bb * ub;
-                            s.row(PS_U0 + xi)[t] = ub;
-                            out[xi] = g;
-                        }
-                    },
-                    none);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            // transpose of g = D+ p; injection of M^T h^n
-            if (tile) p2_col<T, SPEC_GRADT>(s, P, axy, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-            if (rows) {
-                pscatter(s, P, seg, line0, s.gb, P.data + (size_t)n * Ns);
-                row_phase(
-                    I1{}, I2{}, !final_,
-                    [&](int r, int i, const T* in, T* out) { tail(r, i, in[0] + take_inj(r, i), final_, out); },
-                    none);
-            }
-            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
-        }
+        if (!lastph && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
     }
 }
 

@@ -14,15 +14,15 @@ __host__ __device__ __forceinline__ int p2_tab_len(int n) { return 2 * n; }
 // twx[2 nx] | twy[2 ny] | dpl[ny] | dml[ny] | cdp[8] | cdm[8] | work | gb[rmax / 2 nx] (complex)
 // | res[nres][rmax][nx] | ax, aux[nx] | ay, auy | kl2 | ckx2 | kapt [, s0t, s1t] [ny][W] | seg_w (real)
 // | seg_i | flag (int)
-template <typename T> __host__ __device__ size_t p2_work_elems(int nx, int ny, int rmax, int W) {
-    const size_t rowp = (size_t)2 * rmax * nx;
+// work area: row phase A[rmax nx] | B, where B also receives the staged half spectra of the rows
+// (2 rmax ldh); column phase A[2 W ny] | B[2 W ny], B also receiving the staged columns
+template <typename T> __host__ __device__ size_t p2_work_elems(int nx, int ny, int ldh, int rmax, int W) {
+    const size_t rowp = (size_t)rmax * nx + (size_t)2 * rmax * ldh;
     const size_t colp = (size_t)4 * W * ny;
     return rowp > colp ? rowp : colp;
 }
-// nmul: resident k-space multiplier tables of the tile (1: kappa / N; 3: and the two fractional-
-// Laplacian factors of an absorbing medium)
-template <typename T> size_t p2_smem_bytes(int nx, int ny, int rmax, int W, int nres, int nmul) {
-    size_t b = (size_t)(p2_tab_len(nx) + p2_tab_len(ny) + 2 * ny + 16 + p2_work_elems<T>(nx, ny, rmax, W) +
+template <typename T> size_t p2_smem_bytes(int nx, int ny, int ldh, int rmax, int W, int nres, int nmul) {
+    size_t b = (size_t)(p2_tab_len(nx) + p2_tab_len(ny) + 2 * ny + 16 + p2_work_elems<T>(nx, ny, ldh, rmax, W) +
                         (size_t)(rmax / 2) * nx) *
                sizeof(cplx<T>);
     b += (size_t)((size_t)nres * rmax * nx + 2 * nx + 2 * ((rmax + 3) & ~3) + ((ny + 3) & ~3) + 8 +

@@ -57,8 +57,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
     const bool traced = tr.buf && kt >= 0 && kt < tr.nk;
     if (threadIdx.x == 0) {
         if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * kTraceStride] = globaltimer_ns();
-        __threadfence();
-        atomicAdd(&gbar[0], 1u);
+        // arrival with release semantics at GPU scope: the CTA's writes (ordered before this by the
+        // __syncthreads above) are visible to every CTA that observes the count; the polling load
+        // has acquire semantics, and the __syncthreads below extends it to the whole CTA
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(gbar) : "memory");
         const unsigned target = k * nblocks;
         unsigned long long spins = 0;
         int ab = 0;
@@ -72,9 +74,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
                 ab = 1;
                 break;
             }
-            __nanosleep(32);
         }
-        __threadfence();
         if (traced) tr.buf[((size_t)blockIdx.x * tr.nk + kt) * kTraceStride + 1] = globaltimer_ns();
         *abort_s = ab;
     }

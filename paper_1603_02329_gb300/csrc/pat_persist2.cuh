@@ -126,23 +126,31 @@ template <class Fn> __device__ __forceinline__ void with_radix(int r, Fn&& fn) {
 // row phase: complex line q = f np + p holds rows 2p (real part) and 2p + 1 (imaginary part) of
 // field f of the CTA's R = 2 np rows
 // ---------------------------------------------------------------------------------------------
-// inverse x-stage 0 (radix 8, no twiddles) on the C2R packing of the half spectra, read from L2
+// Stage the half spectra of FI fields for the CTA's R rows (one contiguous block per field) into
+// S (row q of field f at S + (f R + q) ldh); asynchronous, completed by the caller's wait.
 template <typename T>
-__device__ void p2_row_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int np, int line0, const P2Axis& ax,
-                          int ldh) {
+__device__ __forceinline__ void p2_row_stage(cplx<T>* S, cplx<T>* const* spec, int FI, int R, int line0, int ldh) {
+    for (int f = 0; f < FI; ++f)
+        stage16(S + (size_t)f * R * ldh, spec[f] + (size_t)line0 * ldh, (size_t)R * ldh * sizeof(cplx<T>));
+    cp_commit();
+}
+
+// inverse x-stage 0 (radix 8, no twiddles) on the C2R packing of the staged half spectra
+template <typename T>
+__device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, const P2Axis& ax, int ldh) {
     const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, half = n >> 1;
     for (int t = threadIdx.x; t < ((FI * np) << lgm); t += blockDim.x) {
         const int q = t >> lgm, j = t & (m - 1);
         const int f = q / np, p = q - f * np;
-        const cplx<T>* a = spec[f] + (size_t)(line0 + 2 * p) * ldh;
+        const cplx<T>* a = S + (size_t)(f * 2 * np + 2 * p) * ldh;
         const cplx<T>* b = a + ldh;
         cplx<T> A[8], B[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int k = j + r * m;
             const int kk = k <= half ? k : n - k;
-            A[r] = __ldcg(a + kk);
-            B[r] = __ldcg(b + kk);
+            A[r] = a[kk];
+            B[r] = b[kk];
         }
         cplx<T> v[8];
 #pragma unroll
@@ -253,17 +261,57 @@ __device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
 // ---------------------------------------------------------------------------------------------
 // column phase: line q = f W + c is column kx0 + c of field f (length ny)
 // ---------------------------------------------------------------------------------------------
-// forward y-stage 0 (radix R, no twiddles) on columns read from L2
+// Stage columns [kx0, kx0 + W) of FI fields into S ([f][ky][c]).  Tiles reach into the zeroed
+// padding columns of the half spectra (kx0 + W <= ldh).  Pieces of 16 bytes go through cp.async
+// (L2 only); narrower ones are loaded with ld.global.cg (L1 is not coherent with the other CTAs'
+// writes of the previous phase) and stored synchronously.
+template <typename T>
+__device__ __forceinline__ void p2_col_stage(cplx<T>* S, cplx<T>* const* spec, int FI, int W, int kx0, int ny,
+                                             int ldh) {
+    const int cb = W * (int)sizeof(cplx<T>);
+    if (cb >= 16) {
+        const int cpr = cb / 16;
+        constexpr int EPC = 16 / (int)sizeof(cplx<T>);
+        for (int f = 0; f < FI; ++f) {
+            const cplx<T>* src = spec[f] + kx0;
+            cplx<T>* d = S + (size_t)f * ny * W;
+            for (int t = threadIdx.x; t < ny * cpr; t += blockDim.x) {
+                const int i = t / cpr, ch = t - i * cpr;
+                cp_async<16>(d + (size_t)i * W + ch * EPC, src + (size_t)i * ldh + ch * EPC);
+            }
+        }
+        cp_commit();
+    } else {
+        for (int f = 0; f < FI; ++f) {
+            const cplx<T>* src = spec[f] + kx0;
+            cplx<T>* d = S + (size_t)f * ny;
+            for (int i0 = threadIdx.x; i0 < ny; i0 += 4 * blockDim.x) {
+                cplx<T> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < ny) v[u] = __ldcg(src + (size_t)i * ldh);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < ny) d[i] = v[u];
+                }
+            }
+        }
+    }
+}
+
+// forward y-stage 0 (radix R, no twiddles) on the staged columns
 template <typename T, int R>
-__device__ void p2_col_in(cplx<T>* dst, cplx<T>* const* spec, int FI, int W, int lgW, int kx0, int nxh,
-                          const P2Axis& ay, int ldh) {
+__device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const P2Axis& ay) {
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
-        const cplx<T>* src = spec[f] + min(kx0 + c, nxh - 1);
+        const cplx<T>* src = S + (size_t)f * n * W + c;
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = __ldcg(src + (size_t)(j + r * m) * ldh);
+        for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
         dft<T, R, false>(v);
         p2_store<T, R>(dst + (size_t)(f * W + c) * n, j, 1, v);
     }
@@ -372,21 +420,26 @@ __device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& 
     const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     cplx<T>* A = s.work;
     cplx<T>* B = A + (size_t)2 * W * ay.n;
-    with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, P.spec, fi, W, lgW, kx0, P.nxh, ay, P.ldh); });
+    p2_col_stage<T>(B, P.spec, fi, W, kx0, ay.n, P.ldh);
+    cp_wait_all();
     __syncthreads();
     s.mark(0);
+    with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, B, fi, W, lgW, ay); });
+    __syncthreads();
+    s.mark(1);
     cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, fi * W);
     cplx<T>* b = (a == A) ? B : A;
-    s.mark(1);
+    s.mark(2);
     p2_col_fuse<T>(s, a, b, ay, W, lgW, mode);
     __syncthreads();
-    s.mark(2);
-    a = p2_mid<T, true>(b, a, ay, s.twy, fo * W);
     s.mark(3);
+    a = p2_mid<T, true>(b, a, ay, s.twy, fo * W);
+    s.mark(4);
     const int wv = min(W, P.nxh - kx0);
     with_radix(ay.r0, [&](auto RC) {
         p2_col_out<T, decltype(RC)::value>(a, P.spec, s.twy, fo, W, lgW, kx0, wv, ay, P.ldh);
     });
+    s.mark(5);
 }
 
 template <typename T> __device__ PersistSm<T> p2_carve(const DevPlan<T>& P, const PersistCfg& C) {
@@ -401,7 +454,7 @@ template <typename T> __device__ PersistSm<T> p2_carve(const DevPlan<T>& P, cons
     s.cdp = s.dml + P.ny;
     s.cdm = s.cdp + 8;
     s.work = s.cdm + 8;
-    s.gb = s.work + p2_work_elems<T>(P.nx, P.ny, C.rmax, C.W);
+    s.gb = s.work + p2_work_elems<T>(P.nx, P.ny, P.ldh, C.rmax, C.W);
     s.res = reinterpret_cast<T*>(s.gb + (size_t)(C.rmax / 2) * P.nx);
     s.ax = s.res + (size_t)C.nres * C.rmax * P.nx;
     s.aux = s.ax + P.nx;
@@ -618,17 +671,21 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
         T* drow = P.data + (size_t)(ADJ ? n : (pid == R_F_INIT ? 0 : n + 1)) * Ns;
         cplx<T>* a = A;
         cplx<T>* bb = B;
+        if (FI > 0) p2_row_stage<T>(B, P.spec, FI, R, line0, P.ldh);
         if (scat) pscatter(s, P, seg, line0, s.gb, drow);
         if (FI > 0) {
-            p2_row_in<T>(A, P.spec, FI, npair, line0, axx, P.ldh);
+            cp_wait_all();
             __syncthreads();
             s.mark(0);
+            p2_row_in<T>(A, B, FI, npair, axx, P.ldh);
+            __syncthreads();
+            s.mark(1);
             a = p2_mid<T, true>(A, B, axx, s.twx, FI * npair);
             bb = (a == A) ? B : A;
         } else {
             __syncthreads();
         }
-        s.mark(1);
+        s.mark(2);
         auto pw = [&](int p, int j, int m, auto& z, auto& o) {
             constexpr int RR = sizeof(z[0]) / sizeof(z[0][0]);
             switch (pid) {
@@ -732,13 +789,13 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
             p2_row_fuse<T, decltype(RC)::value>(a, bb, s.twx, axx, npair, FI, FO, fwd, pw);
         });
         __syncthreads();
-        s.mark(2);
+        s.mark(3);
         if (gath) pgather(s, P, seg, line0, s.gb, drow);
         if (!fwd) return;
         cplx<T>* c = p2_mid<T, false>(bb, a, axx, s.twx, FO * npair);
-        s.mark(3);
-        p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, line0, P.ldh);
         s.mark(4);
+        p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, line0, P.ldh);
+        s.mark(5);
     };
 
     // ---- the solve: one loop over its phases, one call site per phase kind ----

@@ -254,7 +254,7 @@ template <typename T> struct Plan : public PlanBase {
             c.nres = 11;
             const int need = std::max(c.rmax * h.nx / 8, 2 * W * h.ny / 8);
             const int threads = std::min(256, std::max(64, (need + 31) / 32 * 32));
-            const size_t smem = p2 ? p2_smem_bytes<T>(h.nx, h.ny, c.rmax, W, c.nres, h.lossy ? 3 : 1)
+            const size_t smem = p2 ? p2_smem_bytes<T>(h.nx, h.ny, h.ldh, c.rmax, W, c.nres, h.lossy ? 3 : 1)
                                    : persist_smem_bytes<T>(h.nx, h.ny, h.ldh, c.rmax, W, c.nres);
             if (smem > (size_t)optin) continue;
             int per_sm = 0;

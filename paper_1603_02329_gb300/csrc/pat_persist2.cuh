@@ -168,54 +168,87 @@ __device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, const 
     }
 }
 
+template <typename T> __device__ __forceinline__ cplx<T> shfl_pair(cplx<T> v) {
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+    return v;
+}
+
 // Element loop of the pointwise step of a fused row stage: f(row, x, in[FI], out[FO]) for the
-// 2 R real elements of butterfly j (rows 2p, 2p + 1; x = j + r m)
-template <typename T, int R, int FI, int FO, class F>
-__device__ __forceinline__ void p2_each(int p, int j, int m, const cplx<T> (&z)[2][R], cplx<T> (&o)[2][R], F&& f) {
+// 2 H real elements this thread owns (positions r = h H + k of butterfly j; rows 2p, 2p + 1;
+// x = j + r m)
+template <typename T, int H, int FI, int FO, class F>
+__device__ __forceinline__ void p2_each(int p, int j, int m, int h, const cplx<T> (&z)[2][H], cplx<T> (&o)[2][H],
+                                        F&& f) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int k = 0; k < H; ++k) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int hh = 0; hh < 2; ++hh) {
             T in[2], out[2] = {};
 #pragma unroll
-            for (int q = 0; q < FI; ++q) in[q] = h ? z[q][r].y : z[q][r].x;
-            f(2 * p + h, j + r * m, in, out);
+            for (int q = 0; q < FI; ++q) in[q] = hh ? z[q][k].y : z[q][k].x;
+            f(2 * p + hh, j + (h * H + k) * m, in, out);
 #pragma unroll
             for (int g = 0; g < FO; ++g) {
-                if (h) o[g][r].y = out[g];
-                else o[g][r].x = out[g];
+                if (hh) o[g][k].y = out[g];
+                else o[g][k].x = out[g];
             }
         }
     }
 }
 
-// Last inverse x-stage (radix R, Ns = n / R) of FI fields, the pointwise step pw(p, j, m, z, o)
-// (z: inverse-transformed inputs, o: outputs, both [2][R] in registers), and -- when `fwd` --
-// forward x-stage 0 of the FO outputs.  FI = 0: pw reads its inputs itself.
+// Last inverse x-stage (radix R, Ns = n / R), the pointwise step, and -- when `fwd` -- forward
+// x-stage 0, run by lane pairs (2u, 2u + 1) on butterfly u = (p, j).  Lane h transforms input
+// field h (both lanes field 0 when FI = 1); one exchange gives each lane every field at its half
+// of the positions (r = h H + k), where it runs pw(p, j, m, h, zi, oo); a second exchange gives
+// lane h every position of output field h, which it transforms and stores (FO = 1: both lanes
+// transform field 0 and each stores its half).  FI = 0: pw reads its inputs itself.
 template <typename T, int R, class PW>
 __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax,
                                             int np, int FI, int FO, bool fwd, PW&& pw) {
+    constexpr int H = R / 2;
     const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
-    for (int t = threadIdx.x; t < (np << lgm); t += blockDim.x) {
-        const int p = t >> lgm, j = t & (m - 1);
-        cplx<T> z[2][R], o[2][R];
+    const int total = (np << lgm) * 2;
+    for (int t0 = 0; t0 < total; t0 += blockDim.x) {   // uniform trip count: whole warps shuffle
+        const int t = t0 + (int)threadIdx.x;
+        const bool valid = t < total;
+        const int h = t & 1, u = t >> 1;
+        const int p = u >> lgm, j = u & (m - 1);
+        cplx<T> z[R];
+        if (valid && FI > 0) {
+            p2_load<T, R, true>(z, src + (size_t)((FI == 2 ? h : 0) * np + p) * n, j, m, m, twl);
+            dft<T, R, true>(z);
+        }
+        cplx<T> zi[2][H], oo[2][H];
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            if (f < FI) {
-                p2_load<T, R, true>(z[f], src + (size_t)(f * np + p) * n, j, m, m, twl);
-                dft<T, R, true>(z[f]);
+        for (int k = 0; k < H; ++k) {
+            const cplx<T> mine = h ? z[H + k] : z[k];
+            zi[0][k] = mine;
+            if (FI == 2) {
+                const cplx<T> recv = shfl_pair<T>(h ? z[k] : z[H + k]);
+                zi[0][k] = h ? recv : mine;
+                zi[1][k] = h ? mine : recv;
             }
         }
-        pw(p, j, m, z, o);
-        if (fwd) {
+        if (valid) pw(p, j, m, h, zi, oo);
+        if (!fwd) continue;
+        cplx<T> w[R];
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                if (g < FO) {
-                    dft<T, R, false>(o[g]);
-                    p2_store<T, R>(dst + (size_t)(g * np + p) * n, j, 1, o[g]);
-                }
-            }
+        for (int k = 0; k < H; ++k) {
+            const cplx<T> own = (FO == 2 && h) ? oo[1][k] : oo[0][k];
+            const cplx<T> rcv = shfl_pair<T>((FO == 2 && !h) ? oo[1][k] : oo[0][k]);
+            w[k] = h ? rcv : own;
+            w[H + k] = h ? own : rcv;
+        }
+        if (!valid) continue;
+        dft<T, R, false>(w);
+        cplx<T>* d = dst + (size_t)((FO == 2 ? h : 0) * np + p) * n;
+        if (FO == 2) {
+            p2_store<T, R>(d, j, 1, w);
+        } else {
+#pragma unroll
+            for (int k = 0; k < H; ++k) d[swz(j * R + h * H + k)] = h ? w[H + k] : w[k];
         }
     }
 }
@@ -317,79 +350,79 @@ __device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW
     }
 }
 
-// last forward y-stage (radix 8, Ns = n / 8), the k-space multiply of `mode`, inverse y-stage 0.
-// The multipliers of the CTA's tile are resident: kapt = kappa / N, s0t / s1t = |k|^(y-2) / N and
-// |k|^(y-1) / N (Eq. Twelve's fractional Laplacians), [ky][c]; shift operators per column / row.
+// last forward y-stage (radix 8, Ns = n / 8), the k-space multiply of `mode`, inverse y-stage 0,
+// by lane pairs (2u, 2u + 1) on butterfly u = (c, j): lane h transforms field h (both lanes field 0
+// when one field comes in) and produces output field h (both lanes the single output of GRADT,
+// each storing half).  The multipliers of the CTA's tile are resident: kapt = kappa / N, s0t /
+// s1t = |k|^(y-2) / N and |k|^(y-1) / N (Eq. Twelve's fractional Laplacians), [ky][c]; the shift
+// operators per column (cdp / cdm) and per row (dpl / dml).
 template <typename T>
 __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>* src, cplx<T>* dst,
                                             const P2Axis& ay, int W, int lgW, int mode) {
     const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
     const cplx<T>* twl = s.twy + p2_off_f(ay, ay.nst - 1);
-    for (int t = threadIdx.x; t < (W << lgm); t += blockDim.x) {
-        const int c = t & (W - 1), j = t >> lgW;
-        cplx<T> z[2][8], o[2][8];
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            if (f < fi) {
-                p2_load<T, 8, false>(z[f], src + (size_t)(f * W + c) * n, j, m, m, twl);
-                dft<T, 8, false>(z[f]);
-            }
+    const int total = (W << lgm) * 2;
+    for (int t0 = 0; t0 < total; t0 += blockDim.x) {   // uniform trip count: whole warps shuffle
+        const int t = t0 + (int)threadIdx.x;
+        const bool valid = t < total;
+        const int h = t & 1, u = t >> 1;
+        const int c = u & (W - 1), j = u >> lgW;
+        cplx<T> z[8], o[8];
+        if (valid) {
+            p2_load<T, 8, false>(z, src + (size_t)((fi == 2 ? h : 0) * W + c) * n, j, m, m, twl);
+            dft<T, 8, false>(z);
         }
         switch (mode) {
-            case SPEC_ABS:
+            case SPEC_ABS: {
+                const T* sf = h ? s.s1t : s.s0t;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int e = (j + r * m) * W + c;
-                    o[0][r] = cscale(z[0][r], s.s0t[e]);
-                    o[1][r] = cscale(z[1][r], s.s1t[e]);
-                }
-                break;
+                for (int r = 0; r < 8; ++r) o[r] = cscale(z[r], valid ? sf[(j + r * m) * W + c] : (T)0);
+            } break;
             case SPEC_GRAD: {
                 const cplx<T> m0 = s.cdp[c];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const int i = j + r * m;
-                    const cplx<T> v = cscale(z[0][r], s.kapt[i * W + c]);
-                    o[0][r] = cmul(v, m0);
-                    o[1][r] = cmul(v, s.dpl[i]);
+                    const int i = valid ? j + r * m : 0;
+                    const cplx<T> v = cscale(z[r], s.kapt[i * W + c]);
+                    o[r] = cmul(v, h ? s.dpl[i] : m0);
                 }
             } break;
             case SPEC_GRADT: {
                 const cplx<T> m0 = s.cdm[c];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const int i = j + r * m;
-                    o[0][r] = cscale(cadd(cmul(z[0][r], m0), cmul(z[1][r], s.dml[i])), -s.kapt[i * W + c]);
+                    const int i = valid ? j + r * m : 0;
+                    const cplx<T> mine = cmul(z[r], h ? s.dml[i] : m0);
+                    const cplx<T> other = shfl_pair<T>(mine);
+                    o[r] = cscale(h ? cadd(other, mine) : cadd(mine, other), -s.kapt[i * W + c]);
                 }
             } break;
             case SPEC_DIV: {
                 const cplx<T> m0 = s.cdm[c];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const int i = j + r * m;
-                    const T sg = s.kapt[i * W + c];
-                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
-                    o[1][r] = cscale(cmul(z[1][r], s.dml[i]), sg);
+                    const int i = valid ? j + r * m : 0;
+                    o[r] = cscale(cmul(z[r], h ? s.dml[i] : m0), s.kapt[i * W + c]);
                 }
             } break;
             default: {   // SPEC_DIVT
                 const cplx<T> m0 = s.cdp[c];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const int i = j + r * m;
-                    const T sg = -s.kapt[i * W + c];
-                    o[0][r] = cscale(cmul(z[0][r], m0), sg);
-                    o[1][r] = cscale(cmul(z[1][r], s.dpl[i]), sg);
+                    const int i = valid ? j + r * m : 0;
+                    o[r] = cscale(cmul(z[r], h ? s.dpl[i] : m0), -s.kapt[i * W + c]);
                 }
             } break;
         }
+        if (!valid) continue;
+        dft<T, 8, true>(o);
+        cplx<T>* d = dst + (size_t)((fo == 2 ? h : 0) * W + c) * n;
+        if (fo == 2) {
+            p2_store<T, 8>(d, j, 1, o);
+        } else {
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            if (g < fo) {
-                dft<T, 8, true>(o[g]);
-                p2_store<T, 8>(dst + (size_t)(g * W + c) * n, j, 1, o[g]);
-            }
+            for (int k = 0; k < 4; ++k) d[swz(j * 8 + h * 4 + k)] = h ? o[4 + k] : o[k];
         }
     }
 }
@@ -686,11 +719,11 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
             __syncthreads();
         }
         s.mark(2);
-        auto pw = [&](int p, int j, int m, auto& z, auto& o) {
-            constexpr int RR = sizeof(z[0]) / sizeof(z[0][0]);
+        auto pw = [&](int p, int j, int m, int h, auto& z, auto& o) {
+            constexpr int HH = sizeof(z[0]) / sizeof(z[0][0]);
             switch (pid) {
                 case R_F_INIT:
-                    p2_each<T, RR, 0, 1>(p, j, m, z, o, [&](int r, int i, const T*, T* out) {
+                    p2_each<T, HH, 0, 1>(p, j, m, h, z, o, [&](int r, int i, const T*, T* out) {
                         const int t = r * nx + i;
                         const T pv = s.row(PS_RS)[t];
                         const T rh = pv / ((T)2 * s.row(PS_C2)[t]);
@@ -701,7 +734,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_F_U:
-                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 2>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         const int t = r * nx + i;
 #pragma unroll
                         for (int xi = 0; xi < 2; ++xi) {
@@ -716,7 +749,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_F_RHO_LOSSY:
-                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 2>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         T rs, es;
                         const T rho0 = rho_upd(r, i, in, rs, es);
                         s.row(PS_RS)[r * nx + i] = rs;
@@ -725,7 +758,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_F_RHO_LOSSLESS:
-                    p2_each<T, RR, 2, 1>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 1>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         T rs, es;
                         rho_upd(r, i, in, rs, es);
                         const T pv = s.row(PS_C2)[r * nx + i] * rs;
@@ -734,7 +767,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_F_P:
-                    p2_each<T, RR, 2, 1>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 1>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         const int t = r * nx + i;
                         const T pv = s.row(PS_C2)[t] * s.row(PS_RS)[t] + s.row(PS_C2TAU)[t] * in[0] -
                                      s.row(PS_C2ETA)[t] * in[1];
@@ -743,12 +776,12 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_A_INIT:
-                    p2_each<T, RR, 0, 2>(p, j, m, z, o, [&](int r, int i, const T*, T* out) {
+                    p2_each<T, HH, 0, 2>(p, j, m, h, z, o, [&](int r, int i, const T*, T* out) {
                         tail(r, i, take_inj(r, i), lastph, out);
                     });
                     break;
                 case R_A_ABS:
-                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 2>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         const int t = r * nx + i;
                         const T ddbar = in[0];
                         const T rbar = s.row(PS_C2)[t] * s.row(PS_RS)[t] - in[1];
@@ -763,7 +796,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 case R_A_DIVT:
-                    p2_each<T, RR, 2, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 2, 2>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         const int t = r * nx + i;
 #pragma unroll
                         for (int xi = 0; xi < 2; ++xi) {
@@ -779,7 +812,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
                     });
                     break;
                 default:   // R_A_GRADT
-                    p2_each<T, RR, 1, 2>(p, j, m, z, o, [&](int r, int i, const T* in, T* out) {
+                    p2_each<T, HH, 1, 2>(p, j, m, h, z, o, [&](int r, int i, const T* in, T* out) {
                         tail(r, i, in[0] + take_inj(r, i), lastph, out);
                     });
                     break;

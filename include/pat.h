@@ -124,6 +124,29 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
  *   grad     [N]      output, overwritten (host or device, plan precision). */
 pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* stream);
 
+/* pat_gradient_c2 -- medium sensitivity: grad_c2 = d<H p0, h>/d(c0^2) at every grid point, and
+ * grad_p0 = H^T h from the same reverse sweep.  The paper has no medium gradient; it follows from
+ * Sec. III's adjoint-state construction applied to the discrete forward map, for the joint
+ * sound-speed reconstruction that Sec. VII motivates.  Held fixed: alpha0, y, rho0 and the plan's
+ * reference speed, dt, kappa and PML; tau and eta follow c0 through Eq. (Twelve).  With q^n =
+ * d p^n/d c0^2 = r + (y+1)/2 tau L_{y-2} dd - (y+2)/2 eta L_{y-1} r (q = r without absorption) and
+ * p_bar^n the adjoint of p^n:
+ *     grad_c2 = sum_{n>=1} p_bar^n q^n - p0 / (d c0^4) sum_xi rho_bar_xi   (rho_xi^0 = p0/(d c0^2)).
+ * Memory is bounded by checkpoints: the forward state (u_xi, rho_xi, spectrum of p) is stored every
+ * `checkpoint_every` = K >= 1 time levels, and each segment of K levels is recomputed from its
+ * checkpoint (storing its K fields q^n) just before the adjoint steps that consume it: one extra
+ * forward solve in total, ceil((Nt-1)/K) checkpoints of (2d + 1) N values and K N values of q.
+ * The result does not depend on K (the recomputation repeats the same operations).
+ *   p0       [N]      initial pressure (host or device, plan precision).
+ *   residual [Nt][Ns] h (host or device, plan precision).
+ *   grad_c2  [N]      output, overwritten (host or device, plan precision).
+ *   grad_p0  [N]      output or NULL.
+ * Works in device memory it allocates for the call and frees before returning (the stream is
+ * synchronised); PAT_ENOMEM if it cannot.  Runs the per-phase kernels (also for plans whose
+ * forward/adjoint take the persistent kernel); the plan's data buffer holds `residual` afterwards. */
+pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_p0,
+                           int checkpoint_every, void* stream);
+
 /* pat_forward -- one-shot form of the forward operator following the paper's statement of the
  * problem (Sec. II.B, Sec. III): builds a plan from (c, rho, alpha0, y, grid, sensor_mask, dt,
  * Nt), runs pat_forward_plan, synchronises `stream` and frees the plan.  For repeated solves

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
     L.pat_forward_plan.restype = i32
     L.pat_adjoint.argtypes = [vp, vp, vp, vp]
     L.pat_adjoint.restype = i32
+    L.pat_gradient_c2.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.pat_gradient_c2.restype = i32
     L.pat_forward.argtypes = [vp, dp, dp, dp, i32, f64, ctypes.POINTER(pat_grid), ctypes.POINTER(pat_sensors), f64, i32,
                               i32, vp, vp]
     L.pat_forward.restype = i32

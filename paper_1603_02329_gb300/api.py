@@ -132,6 +132,21 @@ class PATOperator:
                                     _stream_ptr(stream, self.device)))
         return out
 
+    def gradient_c2(self, p0: torch.Tensor, residual: torch.Tensor, checkpoint_every: int = 50,
+                    with_p0_grad: bool = False, stream=None):
+        """pat_gradient_c2: d<H p0, h>/d(c0^2) per grid point with forward checkpoints every
+        ``checkpoint_every`` time levels (and H^T h when ``with_p0_grad``)."""
+        self._check_in(p0, self.N, "p0")
+        self._check_in(residual, self.Nt * self.Ns, "residual")
+        g = torch.empty(self.shape, dtype=self.dtype, device=p0.device)
+        gp = torch.empty(self.shape, dtype=self.dtype, device=p0.device) if with_p0_grad else None
+        with torch.cuda.device(self.device):
+            check(lib().pat_gradient_c2(self._plan, ctypes.c_void_p(p0.data_ptr()),
+                                        ctypes.c_void_p(residual.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                        ctypes.c_void_p(gp.data_ptr()) if gp is not None else None,
+                                        int(checkpoint_every), _stream_ptr(stream, self.device)))
+        return (g, gp) if with_p0_grad else g
+
     # -- optimisation shell ---------------------------------------------------------------------
     def power_iteration(self, v0: torch.Tensor, n_iter: int = 30, stream=None) -> float:
         """pat_power_iteration: sigma_max(H^T H) from the start vector v0 (device, plan dtype)."""

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) k_fwd_u(DevPlan<T> P, int R, int first) {
 // rho_xi^{n+1} = a (a rho_xi^n - dt rho0 e_xi); dd = rho0 sum e; r = sum rho.  Lossless: p = c0^2 r,
 // sample, x-FFT of p.  Lossy: keep r, x-FFT of (dd, r) for the fractional Laplacians.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, T* data_row) {
+__global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, T* data_row, T* qrow) {
     RowSm<T, D> sm(P.nx, P.ldh, R);
     const int nx = P.nx, line0 = blockIdx.x * R;
     stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, 
             slot(out, R + r, i, nx) = rs;
         } else {
             slot(out, r, i, nx) = sm.row(1)[t] * rs;
+            if (qrow) qrow[idx] = rs;   // d p / d c0^2 (lossless)
         }
     }
     __syncthreads();
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, 
 // Lossy equation of state p = c0^2 r + c0^2 tau L_{y-2} dd - c0^2 eta L_{y-1} r (Eq. (state)),
 // sample, x-FFT of p.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_fwd_p(DevPlan<T> P, int R, int last, T* data_row) {
+__global__ void __launch_bounds__(256) k_fwd_p(DevPlan<T> P, int R, int last, T* data_row, T* qrow) {
     RowSm<T, D> sm(P.nx, P.ldh, R);
     const int nx = P.nx, line0 = blockIdx.x * R;
     stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
@@ -434,6 +435,13 @@ __global__ void __launch_bounds__(256) k_fwd_p(DevPlan<T> P, int R, int last, T*
         const T Ld = slot(res, r, i, nx);
         const T Lr = slot(res, R + r, i, nx);
         slot(out, r, i, nx) = sm.row(0)[t] * sm.row(3)[t] + sm.row(1)[t] * Ld - sm.row(2)[t] * Lr;
+        if (qrow) {
+            // d p / d c0^2 with tau, eta following c0 (Eq. (Twelve)): d(c0^2 tau)/d c0^2 = (y+1)/2 tau,
+            // d(c0^2 eta)/d c0^2 = (y+2)/2 eta; (y+1)/2 = phb + 1, (y+2)/2 = pha + 2
+            const T c2 = sm.row(0)[t];
+            qrow[(size_t)(line0 + r) * nx + i] =
+                sm.row(3)[t] + ((P.phb + (T)1) * sm.row(1)[t] * Ld - (P.pha + (T)2) * sm.row(2)[t] * Lr) / c2;
+        }
     }
     __syncthreads();
     gather_rows(sm, P, g, line0, out, data_row);
@@ -474,9 +482,13 @@ __device__ __forceinline__ void adj_tail_state(const RowSm<T, D>& sm, const DevP
 //   lossy: keep p_bar; x-FFT of (c0^2 tau p_bar, c0^2 eta p_bar)
 //   lossless: rho_bar_xi += c0^2 p_bar; e_bar_xi = -dt rho0 a rho_bar_xi; rho_bar_xi *= a^2;
 //             x-FFT of e_bar_xi
+//
+// Medium gradient (optional, gc2 != nullptr): g_c2 += p_bar * q of this level (q = d p / d c0^2 of
+// the recomputed forward, `qrow`), and at the final level the initial-density term
+// g_c2 -= sum_xi rho_bar_xi p0 / (d c0^4) (rho_xi^0 = p0 / (d c0^2); p0 = `p0c`).
 template <typename T, int D>
 __device__ void adj_tail(const RowSm<T, D>& sm, const DevPlan<T>& P, cplx<T>* pb, cplx<T>* other, int line0,
-                         int final_) {
+                         int final_, const T* qrow = nullptr, T* gc2 = nullptr, const T* p0c = nullptr) {
     const int nx = P.nx, R = sm.R;
     const T dt = P.dt;
     if (final_) {
@@ -487,7 +499,9 @@ __device__ void adj_tail(const RowSm<T, D>& sm, const DevPlan<T>& P, cplx<T>* pb
             T s = 0;
 #pragma unroll
             for (int xi = 0; xi < D; ++xi) s += sm.row(2 + xi)[t];
-            P.img[idx] = slot(pb, r, i, nx) + s / (T(D) * sm.row(0)[t]);
+            const T c2 = sm.row(0)[t];
+            P.img[idx] = slot(pb, r, i, nx) + s / (T(D) * c2);
+            if (gc2) gc2[idx] -= s * p0c[idx] / (T(D) * c2 * c2);
         }
         return;
     }
@@ -496,6 +510,7 @@ __device__ void adj_tail(const RowSm<T, D>& sm, const DevPlan<T>& P, cplx<T>* pb
         const int t = r * nx + i;
         const size_t idx = (size_t)(line0 + r) * nx + i;
         const T pv = slot(pb, r, i, nx);
+        if (gc2) gc2[idx] += pv * qrow[idx];
         if (P.lossy) {
             P.pbar[idx] = pv;
             slot(other, r, i, nx) = sm.row(0)[t] * pv;
@@ -520,7 +535,8 @@ __device__ void adj_tail(const RowSm<T, D>& sm, const DevPlan<T>& P, cplx<T>* pb
 
 // p_bar^{Nt-1} = M^T h^{Nt-1}, then the tail.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_adj_init(DevPlan<T> P, int R, int final_, const T* h_row) {
+__global__ void __launch_bounds__(256) k_adj_init(DevPlan<T> P, int R, int final_, const T* h_row, const T* qrow,
+                                                   T* gc2, const T* p0c) {
     RowSm<T, D> sm(P.nx, P.ldh, R);
     const int nx = P.nx, line0 = blockIdx.x * R;
     stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
@@ -537,7 +553,7 @@ __global__ void __launch_bounds__(256) k_adj_init(DevPlan<T> P, int R, int final
     __syncthreads();
     scatter_rows(sm, P, g, sm.A, line0, h_row);
     __syncthreads();
-    adj_tail(sm, P, sm.A, sm.B, line0, final_);
+    adj_tail(sm, P, sm.A, sm.B, line0, final_, qrow, gc2, p0c);
 }
 
 // Lossy: r_bar = c0^2 p_bar - L_{y-1}(c0^2 eta p_bar), dd_bar = L_{y-2}(c0^2 tau p_bar);
@@ -633,7 +649,8 @@ __global__ void __launch_bounds__(256) k_adj_u(DevPlan<T> P, int R, int final_) 
 
 // p_bar^n = -sum_xi D-_xi g_bar_xi (spectrum 0) + M^T h^n, then the tail.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_adj_p(DevPlan<T> P, int R, int final_, const T* h_row) {
+__global__ void __launch_bounds__(256) k_adj_p(DevPlan<T> P, int R, int final_, const T* h_row, const T* qrow,
+                                                T* gc2, const T* p0c) {
     RowSm<T, D> sm(P.nx, P.ldh, R);
     const int nx = P.nx, line0 = blockIdx.x * R;
     stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
@@ -653,7 +670,7 @@ __global__ void __launch_bounds__(256) k_adj_p(DevPlan<T> P, int R, int final_, 
     cplx<T>* other = (res == sm.A) ? sm.B : sm.A;
     scatter_rows(sm, P, g, res, line0, h_row);
     __syncthreads();
-    adj_tail(sm, P, res, other, line0, final_);
+    adj_tail(sm, P, res, other, line0, final_, qrow, gc2, p0c);
 }
 
 // ------------------------------------------------------------------------------------------

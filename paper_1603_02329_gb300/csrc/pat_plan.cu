@@ -470,6 +470,17 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
     return PAT_OK;
 }
 
+pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_p0,
+                           int checkpoint_every, void* stream) {
+    set_error("");
+    if (!plan || !p0 || !residual || !grad_c2) return fail(PAT_EINVAL, "NULL argument");
+    if (checkpoint_every < 1) return fail(PAT_EINVAL, "checkpoint_every must be >= 1");
+    PlanBase* b = plan->impl;
+    if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
+    DeviceGuard g(b->device);
+    return plan_gradient_c2(b, p0, residual, grad_c2, grad_p0, checkpoint_every, (cudaStream_t)stream);
+}
+
 pat_status pat_forward(const void* p0, const double* c, const double* rho, const double* alpha0,
                        int alpha0_is_scalar, double y, const pat_grid* grid, const pat_sensors* sensor_mask,
                        double dt, int Nt, pat_precision prec, void* data, void* stream) {

@@ -386,24 +386,161 @@ template <typename T> struct Plan : public PlanBase {
         cudaLaunchKernelEx(&lc, kern, args...);
     }
 
-    template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F) {
-        const int tiles = (P.nxh + cfg.col_w - 1) / cfg.col_w;
-        const int outer = (lax == 1) ? P.nz : P.ny;
+    template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F) { spec_launch_on<D, MODE>(P, s, lax, F); }
+    template <int D, int MODE> void spec_launch_on(const DevPlan<T>& Q, cudaStream_t s, int lax, int F) {
+        const int tiles = (Q.nxh + cfg.col_w - 1) / cfg.col_w;
+        const int outer = (lax == 1) ? Q.nz : Q.ny;
         int lgw = 0;
         while ((1 << lgw) < cfg.col_w) ++lgw;
-        launch(k_spec<T, D, MODE>, dim3(tiles, outer), cfg.col_threads, spec_smem, s, P, cfg.col_w, lgw, lax, F);
+        launch(k_spec<T, D, MODE>, dim3(tiles, outer), cfg.col_threads, spec_smem, s, Q, cfg.col_w, lgw, lax, F);
     }
 
-    template <int D, int MODE> void spectral(cudaStream_t s) {
+    template <int D, int MODE> void spectral_on(const DevPlan<T>& Q, cudaStream_t s) {
         if (D == 2) {
-            spec_launch<D, MODE>(s, 1, 0);
+            spec_launch_on<D, MODE>(Q, s, 1, 0);
             return;
         }
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
-        spec_launch<D, SPEC_PLAIN_FWD>(s, 1, fin);
-        spec_launch<D, MODE>(s, 2, 0);
-        spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout);
+        spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin);
+        spec_launch_on<D, MODE>(Q, s, 2, 0);
+        spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout);
+    }
+
+    // ---------------------------------------------------------------------------------------
+    // medium gradient with checkpoints (direct launches of the per-phase kernels)
+    // ---------------------------------------------------------------------------------------
+    // forward step n -> n + 1 on the state of Q; q^{n+1} = d p^{n+1} / d c0^2 into qrow
+    template <int D> void fwd_step_on(const DevPlan<T>& Q, int n, T* data_row, T* qrow, cudaStream_t s) {
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        const int last = (n + 2 == H.Nt);
+        spectral_on<D, SPEC_GRAD>(Q, s);
+        launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, Q, R, (int)(n == 0));
+        spectral_on<D, SPEC_DIV>(Q, s);
+        launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, Q, R, last, data_row, Q.lossy ? (T*)nullptr : qrow);
+        if (Q.lossy) {
+            spectral_on<D, SPEC_ABS>(Q, s);
+            launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, Q, R, last, data_row, qrow);
+        }
+    }
+    // adjoint iteration that produces p_bar^n (the reverse of forward step n), accumulating
+    // g_c2 += p_bar^n q^n (n >= 1) or, at n = 0, the initial-density term
+    template <int D> void adj_step_on(int n, const T* qrow, T* gc2, const T* p0c, cudaStream_t s) {
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        if (P.lossy) {
+            spectral_on<D, SPEC_ABS>(P, s);
+            launch(k_adj_rho<T, D>, dim3(G), B, row_smem, s, P, R);
+        }
+        spectral_on<D, SPEC_DIVT>(P, s);
+        launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
+        spectral_on<D, SPEC_GRADT>(P, s);
+        launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * H.Ns),
+               n == 0 ? (const T*)nullptr : qrow, gc2, p0c);
+    }
+
+    // g_c2 = d<H p0, h>/d c0^2 and grad_p0 = H^T h in one reverse sweep; forward states are
+    // checkpointed every K levels (levels 0, K, 2K, ...) and each segment (jK, (j+1)K] is recomputed
+    // from its checkpoint, storing q^n, right before the adjoint iterations that consume it.
+    template <int D> pat_status gradient_c2(const void* p0, const void* h, void* gc2_out, void* gp0_out, int K,
+                                            cudaStream_t s) {
+        const int Nt = H.Nt, Ns = H.Ns;
+        const size_t N = (size_t)P.N, Nh = (size_t)H.nz * H.ny * H.ldh;
+        const int nspec = std::max(D, 2);
+        const int nseg = (Nt > 1) ? (Nt - 2) / K + 1 : 0;    // segments of levels 1 .. Nt-1
+        const size_t ck_elems = 2 * D * N + Nh * 2;           // u, rho (real) and the p spectrum
+        std::vector<void*> own;
+        auto alloc = [&](size_t bytes) -> void* {
+            void* ptr = nullptr;
+            if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
+            own.push_back(ptr);
+            return ptr;
+        };
+        auto release = [&]() {
+            cudaStreamSynchronize(s);
+            for (void* ptr : own) cudaFree(ptr);
+        };
+        T* p0buf = (T*)alloc(N * sizeof(T));
+        T* gc2 = (T*)alloc(N * sizeof(T));
+        T* junk = (T*)alloc((size_t)std::max(Ns, 1) * sizeof(T));
+        T* qbuf = (T*)alloc((size_t)std::max(1, std::min(K, Nt)) * N * sizeof(T));
+        T* ckpt = (T*)alloc((size_t)std::max(nseg, 1) * ck_elems * sizeof(T));
+        DevPlan<T> Pf = P;
+        bool ok = p0buf && gc2 && junk && qbuf && ckpt;
+        for (int a = 0; a < D && ok; ++a) {
+            ok = ok && (Pf.u[a] = (T*)alloc(N * sizeof(T))) && (Pf.rh[a] = (T*)alloc(N * sizeof(T)));
+        }
+        if (ok && P.lossy) ok = (Pf.rsum = (T*)alloc(N * sizeof(T))) != nullptr;
+        for (int a = 0; a < nspec && ok; ++a) {
+            ok = (Pf.spec[a] = (cplx<T>*)alloc(Nh * sizeof(cplx<T>))) != nullptr;
+            if (ok) ok = cudaMemsetAsync(Pf.spec[a], 0, Nh * sizeof(cplx<T>), s) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            release();
+            set_error("out of device memory for the checkpointed gradient");
+            return PAT_ENOMEM;
+        }
+        Pf.img = p0buf;
+        Pf.data = junk;
+        cudaError_t e = cudaMemcpyAsync(p0buf, p0, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(P.data, h, (size_t)Nt * Ns * sizeof(T), cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gc2, 0, N * sizeof(T), s);
+        for (int a = 0; a < D && e == cudaSuccess; ++a) {
+            e = cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(P.rh[a], 0, N * sizeof(T), s);
+        }
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(e, "gradient setup");
+        }
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        auto save = [&](int j) {
+            T* c = ckpt + (size_t)j * ck_elems;
+            for (int a = 0; a < D; ++a) {
+                cudaMemcpyAsync(c + (size_t)a * N, Pf.u[a], N * sizeof(T), cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(c + (size_t)(D + a) * N, Pf.rh[a], N * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            }
+            cudaMemcpyAsync(c + 2 * D * N, Pf.spec[0], Nh * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s);
+        };
+        auto restore = [&](int j) {
+            const T* c = ckpt + (size_t)j * ck_elems;
+            for (int a = 0; a < D; ++a) {
+                cudaMemcpyAsync(Pf.u[a], c + (size_t)a * N, N * sizeof(T), cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(Pf.rh[a], c + (size_t)(D + a) * N, N * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            }
+            cudaMemcpyAsync(Pf.spec[0], c + 2 * D * N, Nh * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s);
+        };
+        // (1) forward sweep to level (nseg - 1) K, checkpointing levels 0, K, ...
+        launch(k_fwd_init<T, D>, dim3(G), B, row_smem, s, Pf, R, (int)(Nt == 1));
+        if (nseg > 0) save(0);
+        for (int n = 0; n < (nseg - 1) * K; ++n) {
+            fwd_step_on<D>(Pf, n, junk, (T*)nullptr, s);
+            if ((n + 1) % K == 0) save((n + 1) / K);
+        }
+        // (2) reverse sweep, segment by segment
+        if (Nt == 1) {
+            launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, P, R, 1, (const T*)(P.data), (const T*)nullptr, gc2,
+                   (const T*)p0buf);
+        }
+        for (int j = nseg - 1; j >= 0; --j) {
+            const int lo = j * K, hi = std::min((j + 1) * K, Nt - 1);
+            restore(j);
+            for (int n = lo; n < hi; ++n) fwd_step_on<D>(Pf, n, junk, qbuf + (size_t)(n - lo) * N, s);
+            int top = hi;
+            if (hi == Nt - 1) {
+                launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, P, R, 0, (const T*)(P.data + (size_t)(Nt - 1) * Ns),
+                       (const T*)(qbuf + (size_t)(hi - lo - 1) * N), gc2, (const T*)p0buf);
+                top = Nt - 2;
+            }
+            for (int n = top; n > lo; --n) adj_step_on<D>(n, qbuf + (size_t)(n - lo - 1) * N, gc2, p0buf, s);
+        }
+        if (Nt > 1) adj_step_on<D>(0, nullptr, gc2, p0buf, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gc2_out, gc2, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && gp0_out) e = cudaMemcpyAsync(gp0_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
+        release();
+        if (e != cudaSuccess) return cuda_fail(e, "checkpointed gradient");
+        return PAT_OK;
     }
 
     // --- kernel-timing probe -----------------------------------------------------------------
@@ -470,11 +607,11 @@ template <typename T> struct Plan : public PlanBase {
             launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
             spectral_named<D, SPEC_DIV>(s, "spec_div");
             mark(s, "fwd_rho");
-            launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, P, R, last, row);
+            launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, P, R, last, row, (T*)nullptr);
             if (P.lossy) {
                 spectral_named<D, SPEC_ABS>(s, "spec_abs");
                 mark(s, "fwd_p");
-                launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, P, R, last, row);
+                launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, P, R, last, row, (T*)nullptr);
             }
             if (probe_g >= 0) end_sample(s);
         }
@@ -492,7 +629,7 @@ template <typename T> struct Plan : public PlanBase {
         probe_names[1].clear();
         probe_samples[1] = 0;
         launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, P, R, (int)(Nt == 1),
-               (const T*)(P.data + (size_t)(Nt - 1) * Ns));
+               (const T*)(P.data + (size_t)(Nt - 1) * Ns), (const T*)nullptr, (T*)nullptr, (const T*)nullptr);
         for (int n = Nt - 2; n >= 0; --n) {
             if (sampled(n, Nt)) begin_sample(1, probe_samples[1]++ == 0);
             if (P.lossy) {
@@ -505,7 +642,8 @@ template <typename T> struct Plan : public PlanBase {
             launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
             spectral_named<D, SPEC_GRADT>(s, "spec_gradt");
             mark(s, "adj_p");
-            launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * Ns));
+            launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * Ns),
+                   (const T*)nullptr, (T*)nullptr, (const T*)nullptr);
             if (probe_g >= 0) end_sample(s);
         }
     }
@@ -605,6 +743,18 @@ pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, doub
     *mean_ms = cnt ? sum / cnt : 0.0;
     *samples = cnt;
     return PAT_OK;
+}
+
+pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void* gc2, void* gp0, int K,
+                            cudaStream_t s) {
+    if (base->info.precision == PAT_F32) {
+        auto* p = static_cast<Plan<float>*>(base);
+        return p->P.d == 2 ? p->template gradient_c2<2>(p0, h, gc2, gp0, K, s)
+                           : p->template gradient_c2<3>(p0, h, gc2, gp0, K, s);
+    }
+    auto* p = static_cast<Plan<double>*>(base);
+    return p->P.d == 2 ? p->template gradient_c2<2>(p0, h, gc2, gp0, K, s)
+                       : p->template gradient_c2<3>(p0, h, gc2, gp0, K, s);
 }
 
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {

@@ -85,6 +85,9 @@ typedef struct {
     double c_ref;       /* max sound speed (kappa correction, PML scaling) */
     int path;           /* 0: CUDA graph of per-phase kernels; 1: one persistent kernel per solve;
                            2: the same, register-fused transforms (power-of-two 2-D grids) */
+    int layout[2];      /* launch layout: path 0 -> columns per spectral CTA, x-lines per row CTA;
+                           paths 1, 2 -> columns per CTA, x-line pairs per CTA */
+    int tuned;          /* 1 when the layout was chosen by timing the feasible candidates */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).
@@ -146,6 +149,31 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
  * forward/adjoint take the persistent kernel); the plan's data buffer holds `residual` afterwards. */
 pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_p0,
                            int checkpoint_every, void* stream);
+
+/* ===========================================================================================
+ * Batches: several independent instances in one launch
+ * ===========================================================================================
+ * The paper solves one problem at a time; batching independent instances (uneven grids, each with
+ * its own medium, sensors and time axis) has no counterpart there.  A batch runs every instance's
+ * per-phase solve (the CUDA-graph path, whatever path the plan's own calls take) as one graph
+ * launch whose instances have no dependencies on one another, so the GPU overlaps them.  The
+ * batch borrows the plans: destroy it before them; a plan may sit in one batch at a time and runs
+ * no other call while a batch launch that holds it is in flight. */
+typedef struct pat_batch pat_batch;
+
+/* pat_batch_create -- a batch over `count` >= 1 distinct plans of one device (not static-arena
+ * plans).  Graphs are captured on first use of each direction. */
+pat_status pat_batch_create(pat_plan* const* plans, int count, pat_batch** out);
+
+/* pat_batch_destroy -- waits for the device and frees the batch (not its plans). */
+pat_status pat_batch_destroy(pat_batch* batch);
+
+/* pat_batch_forward -- data[i] = H_i p0[i] for every instance i (arrays of `count` pointers,
+ * host or device, each plan's precision and sizes as in pat_forward_plan). */
+pat_status pat_batch_forward(pat_batch* batch, const void* const* p0, void* const* data, void* stream);
+
+/* pat_batch_adjoint -- grad[i] = H_i^T residual[i] for every instance i (as pat_adjoint). */
+pat_status pat_batch_adjoint(pat_batch* batch, const void* const* residual, void* const* grad, void* stream);
 
 /* pat_forward -- one-shot form of the forward operator following the paper's statement of the
  * problem (Sec. II.B, Sec. III): builds a plan from (c, rho, alpha0, y, grid, sensor_mask, dt,

@@ -29,7 +29,8 @@ class pat_sensors(ctypes.Structure):
 class pat_plan_info_t(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("N", ctypes.c_int64), ("Ns", ctypes.c_int),
                 ("Nt", ctypes.c_int), ("lossy", ctypes.c_int), ("precision", ctypes.c_int),
-                ("dt", ctypes.c_double), ("c_ref", ctypes.c_double), ("path", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("c_ref", ctypes.c_double), ("path", ctypes.c_int),
+                ("layout", ctypes.c_int * 2), ("tuned", ctypes.c_int)]
 
 
 class pat_fista_opts(ctypes.Structure):
@@ -83,6 +84,14 @@ def lib() -> ctypes.CDLL:
     L.pat_adjoint.restype = i32
     L.pat_gradient_c2.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_c2.restype = i32
+    L.pat_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    L.pat_batch_create.restype = i32
+    L.pat_batch_destroy.argtypes = [vp]
+    L.pat_batch_destroy.restype = i32
+    L.pat_batch_forward.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.pat_batch_forward.restype = i32
+    L.pat_batch_adjoint.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.pat_batch_adjoint.restype = i32
     L.pat_forward.argtypes = [vp, dp, dp, dp, i32, f64, ctypes.POINTER(pat_grid), ctypes.POINTER(pat_sensors), f64, i32,
                               i32, vp, vp]
     L.pat_forward.restype = i32

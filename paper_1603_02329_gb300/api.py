@@ -382,3 +382,46 @@ def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.T
     report = dict(iters=rep.iters, recursive_iters=rep.recursive_iters, fwd_solves=rep.fwd_solves,
                   adj_solves=rep.adj_solves, F=rep.F, RES=rep.RES, RE=rep.RE)
     return x, report, records
+
+
+class PATBatch:
+    """pat_batch_*: several independent instances (uneven grids) as one graph launch per call."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[op._plan.value for op in self.ops])
+        self._b = ctypes.c_void_p()
+        self.device = self.ops[0].device
+        with torch.cuda.device(self.device):
+            check(lib().pat_batch_create(arr, len(self.ops), ctypes.byref(self._b)))
+
+    def _run(self, fn, xs, shapes, stream):
+        if len(xs) != len(self.ops):
+            raise ValueError("one tensor per instance")
+        outs = [torch.empty(sh, dtype=op.dtype, device=x.device) for sh, op, x in zip(shapes, self.ops, xs)]
+        ins = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        ous = (ctypes.c_void_p * len(xs))(*[o.data_ptr() for o in outs])
+        with torch.cuda.device(self.device):
+            check(fn(self._b, ins, ous, _stream_ptr(stream, self.device)))
+        return outs
+
+    def forward(self, p0s, stream=None):
+        for op, x in zip(self.ops, p0s):
+            op._check_in(x, op.N, "p0")
+        return self._run(lib().pat_batch_forward, p0s, [(op.Nt, op.Ns) for op in self.ops], stream)
+
+    def adjoint(self, residuals, stream=None):
+        for op, r in zip(self.ops, residuals):
+            op._check_in(r, op.Nt * op.Ns, "residual")
+        return self._run(lib().pat_batch_adjoint, residuals, [op.shape for op in self.ops], stream)
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            lib().pat_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,11 +6,11 @@ batched form applies one plan per instance (instances may have different grids).
 """
 from __future__ import annotations
 
-from typing import Sequence
+from typing import Optional, Sequence
 
 import torch
 
-from .api import PATOperator
+from .api import PATBatch, PATOperator
 
 
 class PATFunction(torch.autograd.Function):
@@ -27,19 +27,26 @@ class PATFunction(torch.autograd.Function):
 
 
 class PATBatchFunction(torch.autograd.Function):
-    """A batch of independent instances: out[i] = H_i p0[i] (one plan per instance)."""
+    """A batch of independent instances: out[i] = H_i p0[i] (one plan per instance); with a
+    ``PATBatch`` every direction is one graph launch over all instances."""
 
     @staticmethod
     def forward(ctx, *args):
-        ops = args[-1]
-        p0s = args[:-1]
-        ctx.ops = ops
-        return tuple(op.forward(p.contiguous()) for p, op in zip(p0s, ops))
+        ops, batch = args[-2], args[-1]
+        p0s = [p.contiguous() for p in args[:-2]]
+        ctx.ops, ctx.batch = ops, batch
+        if batch is not None:
+            return tuple(batch.forward(p0s))
+        return tuple(op.forward(p) for p, op in zip(p0s, ops))
 
     @staticmethod
     def backward(ctx, *grads):
-        outs = tuple(op.adjoint(g.contiguous()) for g, op in zip(grads, ctx.ops))
-        return outs + (None,)
+        grads = [g.contiguous() for g in grads]
+        if ctx.batch is not None:
+            outs = tuple(ctx.batch.adjoint(grads))
+        else:
+            outs = tuple(op.adjoint(g) for g, op in zip(grads, ctx.ops))
+        return outs + (None, None)
 
 
 def pat_apply(op: PATOperator, p0: torch.Tensor) -> torch.Tensor:
@@ -47,6 +54,7 @@ def pat_apply(op: PATOperator, p0: torch.Tensor) -> torch.Tensor:
     return PATFunction.apply(p0, op)
 
 
-def pat_apply_batch(ops: Sequence[PATOperator], p0s: Sequence[torch.Tensor]):
-    """Differentiable [H_i p0_i] for a batch of instances."""
-    return PATBatchFunction.apply(*p0s, list(ops))
+def pat_apply_batch(ops: Sequence[PATOperator], p0s: Sequence[torch.Tensor], batch: Optional[PATBatch] = None):
+    """Differentiable [H_i p0_i] for a batch of instances (one launch per direction when ``batch``
+    is given)."""
+    return PATBatchFunction.apply(*p0s, list(ops), batch)

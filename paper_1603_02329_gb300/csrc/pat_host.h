@@ -33,6 +33,7 @@ struct HostTables {
 PlanBase* make_plan_f32(const HostTables& h, pat_status* st);
 PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
 pat_status plan_capture(PlanBase* base, bool adjoint);
+pat_status plan_capture_graph(PlanBase* base, bool adjoint, cudaGraph_t* out);
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s);
 pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void* gc2, void* gp0, int K,
                             cudaStream_t s);

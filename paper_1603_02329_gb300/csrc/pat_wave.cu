@@ -194,9 +194,97 @@ template <typename T> struct Plan : public PlanBase {
         else st = set_attrs<3>();
         if (st != PAT_OK) return st;
         if (arena) return PAT_OK;
-        CHK2(configure_persistent(h));
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        CHK2(configure_persistent(h));
+        info.layout[0] = persistent ? pcfg.W : cfg.col_w;
+        info.layout[1] = persistent ? pcfg.ppc : cfg.row_lines;
+        if (!persistent) {
+            st = (D == 2) ? tune_graph<2>() : tune_graph<3>();
+            if (st != PAT_OK) return st;
+        }
+        return PAT_OK;
+    }
+
+    bool autotune_enabled() const {
+        const char* e = std::getenv("PAT_AUTOTUNE");
+        return !(e && std::atoi(e) == 0);
+    }
+    // device time of fn() on cap_stream: one untimed run, then the mean of `reps`
+    template <class Fn> float time_on_stream(Fn&& fn, int reps) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        fn();
+        cudaEventRecord(a, cap_stream);
+        for (int i = 0; i < reps; ++i) fn();
+        cudaEventRecord(b, cap_stream);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return ms / reps;
+    }
+
+    // FFT tile autotuner of the per-phase path: columns per spectral CTA (W) x x-lines per row CTA,
+    // each feasible pair timed on one forward step and one adjoint step (the kernels do the same
+    // work whatever the field values), fastest kept.  PAT_COL_W / PAT_ROW_LINES pin a dimension.
+    template <int D> pat_status tune_graph() {
+        if (!autotune_enabled() || H.Nt < 2) return PAT_OK;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const bool fw = std::getenv("PAT_COL_W") != nullptr, fr = std::getenv("PAT_ROW_LINES") != nullptr;
+        const int L = std::max(H.ny, H.nz);
+        const LaunchCfg base = cfg;
+        LaunchCfg best = cfg;
+        float best_ms = 1e30f;
+        int tried = 0;
+        for (int w : {1, 2, 4, 8}) {
+            if (fw && w != base.col_w) continue;
+            if (sizeof(T) == 8 && w > 4) continue;
+            for (int r : {2, 4, 8, 16}) {
+                if (fr && r != base.row_lines) continue;
+                if (P.nlines % r != 0) continue;
+                LaunchCfg c = base;
+                c.col_w = w;
+                c.row_lines = r;
+                c.col_threads = std::min(256, std::max(64, (D * w * L / 8 + 31) / 32 * 32));
+                const size_t rs = row_smem_bytes<T>(D, H.nx, H.ldh, r), ss = spec_smem_bytes<T>(D, L, w);
+                if (rs > (size_t)optin || ss > (size_t)optin) continue;
+                cfg = c;
+                row_smem = rs;
+                spec_smem = ss;
+                const float ms = time_on_stream(
+                    [&] {
+                        fwd_step_on<D>(P, 1, P.data, (T*)nullptr, cap_stream);
+                        adj_step_on<D>(1, (const T*)nullptr, (T*)nullptr, (const T*)nullptr, cap_stream);
+                    },
+                    2);
+                ++tried;
+                if (std::getenv("PAT_DEBUG"))
+                    fprintf(stderr, "[pat] tune graph W=%d lines=%d: %.4f ms per step pair\n", w, r, ms);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "autotune (per-phase kernels)");
+        cfg = best;
+        row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
+        spec_smem = spec_smem_bytes<T>(D, L, cfg.col_w);
+        // the timed steps left arbitrary values in the work buffers; the solves re-initialise the
+        // state, and the spectra's padding columns are cleared again
+        const size_t Nh = (size_t)H.nz * H.ny * H.ldh;
+        for (int a = 0; a < std::max(D, 2); ++a) cudaMemsetAsync(P.spec[a], 0, Nh * sizeof(cplx<T>), cap_stream);
+        e = cudaStreamSynchronize(cap_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune");
+        info.layout[0] = cfg.col_w;
+        info.layout[1] = cfg.row_lines;
+        info.tuned = tried > 1;
         return PAT_OK;
     }
 
@@ -237,6 +325,12 @@ template <typename T> struct Plan : public PlanBase {
         int forced_w = 0, forced_p = 0;
         if (const char* ew = std::getenv("PAT_PERSIST_W")) forced_w = std::atoi(ew);
         if (const char* ep = std::getenv("PAT_PERSIST_PPC")) forced_p = std::atoi(ep);
+        struct Cand {
+            PersistCfg c;
+            int G, threads;
+            size_t smem;
+        };
+        std::vector<Cand> ok;
         for (const auto& cnd : cands) {
             const int W = cnd[0], ppc = cnd[1];
             if (forced_w && W != forced_w) continue;
@@ -269,17 +363,43 @@ template <typename T> struct Plan : public PlanBase {
                 continue;
             }
             if (std::min(per_sm, per_sm_a) * nsm < G) continue;
-            pat_status st = PAT_OK;
-            gbar = dalloc<unsigned>(4, &st);
-            if (!gbar) return st;
-            pcfg = c;
-            persist_grid = G;
-            persist_smem = smem;
-            persist_threads = threads;
-            persist_p2 = p2;
-            persistent = 1;
-            info.path = p2 ? 2 : 1;
-            return PAT_OK;
+            ok.push_back(Cand{c, G, threads, smem});
+        }
+        if (ok.empty()) return PAT_OK;
+        pat_status st = PAT_OK;
+        gbar = dalloc<unsigned>(4, &st);
+        if (!gbar) return st;
+        persist_p2 = p2;
+        persistent = 1;
+        info.path = p2 ? 2 : 1;
+        auto use = [&](const Cand& k) {
+            pcfg = k.c;
+            persist_grid = k.G;
+            persist_smem = k.smem;
+            persist_threads = k.threads;
+        };
+        use(ok[0]);   // least work per CTA first
+        if (ok.size() > 1 && autotune_enabled() && !forced_w && !forced_p && H.Nt >= 2) {
+            // autotuner: time a short forward solve (at most 24 steps) with each co-resident layout
+            const int Nt_full = P.Nt;
+            P.Nt = std::min(Nt_full, 24);
+            size_t bi = 0;
+            float best = 1e30f;
+            for (size_t i = 0; i < ok.size(); ++i) {
+                use(ok[i]);
+                const float ms = time_on_stream([&] { run_persistent(false, cap_stream); }, 2);
+                if (dbg) fprintf(stderr, "[pat] tune persistent W=%d ppc=%d: %.4f ms\n", ok[i].c.W, ok[i].c.ppc, ms);
+                if (ms < best) {
+                    best = ms;
+                    bi = i;
+                }
+            }
+            P.Nt = Nt_full;
+            use(ok[bi]);
+            cudaError_t e2 = cudaStreamSynchronize(cap_stream);
+            if (e2 == cudaSuccess) e2 = cudaGetLastError();
+            if (e2 != cudaSuccess) return cuda_fail(e2, "autotune (persistent kernel)");
+            info.tuned = 1;
         }
         return PAT_OK;
     }
@@ -649,6 +769,17 @@ template <typename T> struct Plan : public PlanBase {
     }
 
     pat_status capture(bool adjoint, cudaGraphExec_t* out) {
+        cudaGraph_t g = nullptr;
+        pat_status st = capture_graph(adjoint, &g);
+        if (st != PAT_OK) return st;
+        cudaError_t e = cudaGraphInstantiate(out, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        return PAT_OK;
+    }
+
+    // the per-phase solve as a (not instantiated) graph; the caller owns *out
+    pat_status capture_graph(bool adjoint, cudaGraph_t* out) {
         cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
         if (P.d == 2) {
@@ -666,9 +797,7 @@ template <typename T> struct Plan : public PlanBase {
             return cuda_fail(le, "kernel launch during capture");
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(out, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        *out = g;
         return PAT_OK;
     }
 };
@@ -760,6 +889,11 @@ pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void*
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {
     if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->run_persistent(adjoint, s);
     return static_cast<Plan<double>*>(base)->run_persistent(adjoint, s);
+}
+
+pat_status plan_capture_graph(PlanBase* base, bool adjoint, cudaGraph_t* out) {
+    if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->capture_graph(adjoint, out);
+    return static_cast<Plan<double>*>(base)->capture_graph(adjoint, out);
 }
 
 pat_status plan_capture(PlanBase* base, bool adjoint) {

@@ -272,3 +272,23 @@ def test_persistent_status_word_ok(dev):
     op = _gpu_op(pb, "f32", dev)
     op.forward(_t(pb.p0, "f32", dev))
     assert _lib.lib().pat_plan_status(op._plan) == 0
+
+
+@pytest.mark.parametrize("persist", ["1", "0"])
+def test_autotuned_layout_gives_the_same_results(dev, monkeypatch, persist):
+    # plan creation times the feasible launch layouts (PAT_AUTOTUNE=0: the first feasible one);
+    # the layout changes how lines are grouped into CTAs, not the arithmetic of any line
+    pb = synth.small_lossy_2d(shape=(64, 80), pml=8, Nt=60, n_sensors=24)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(23).standard_normal((pb.Nt, ref.Ns))
+    monkeypatch.setenv("PAT_PERSIST", persist)
+    out = {}
+    for tune in ("1", "0"):
+        monkeypatch.setenv("PAT_AUTOTUNE", tune)
+        op = _gpu_op(pb, "f64", dev)
+        assert op.info.tuned == (1 if tune == "1" else 0)
+        assert op.info.layout[0] >= 1 and op.info.layout[1] >= 1
+        out[tune] = (op.forward(_t(pb.p0, "f64", dev)).cpu().numpy(), op.adjoint(_t(h, "f64", dev)).cpu().numpy())
+        assert rel(out[tune][0], ref.forward(pb.p0)) <= TOL64
+        op.close()
+    assert rel(out["1"][0], out["0"][0]) <= 1e-13 and rel(out["1"][1], out["0"][1]) <= 1e-13

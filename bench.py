@@ -36,12 +36,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="vessel2d_512", choices=["vessel2d_512", "disc2d_168"])
+    ap.add_argument("--workload", default="vessel2d_512",
+                    choices=["vessel2d_512", "disc2d_168", "tube3d_128", "tube3d_256"])
+    ap.add_argument("--nt", type=int, default=0,
+                    help="override the workload's time axis (small cases for profiler captures only)")
     ap.add_argument("--probe-stride", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
-    ap.add_argument("--mg-iters", type=int, default=30)
+    ap.add_argument("--mg-iters", type=int, default=20)
     return ap.parse_args()
 
 
@@ -54,6 +57,14 @@ def workload(name, rank):
         desc = {"workload": "2-D 512^2 heterogeneous absorbing medium (alpha0=0.75, y=1.5), 20-pt PML, "
                             "512 on-grid line sensors, Nt=2000, vessel+disc phantom",
                 "grid": [512, 512], "Nt": 2000, "Ns": 512, "pml": 20, "dx_m": 5e-5, "cfl": 0.3}
+    elif name.startswith("tube3d_"):
+        n = int(name.split("_")[1])
+        pml, Nt, ns = (10, 1000, 64) if n == 128 else (20, 1500, 128)
+        pb = synth.tube_phantom_3d(seed=3 + rank, n=n, pml=pml, Nt=Nt, sensors=ns)
+        prec = "f32"
+        desc = {"workload": f"3-D {n}^3 heterogeneous absorbing medium (alpha0=0.75, y=1.5), {pml}-pt PML, "
+                            f"{ns}x{ns} planar on-grid sensors at stride 2, Nt={Nt}, tube+ball phantom",
+                "grid": [n, n, n], "Nt": Nt, "Ns": ns * ns, "pml": pml, "dx_m": 6.25e-5, "cfl": 0.3}
     else:
         pb = synth.disc_phantom_2d(seed=1 + rank)
         prec = "f64"
@@ -159,7 +170,7 @@ def run_reference(args):
     from oracle.pat_oracle import Operator
 
     pb, prec, desc = workload(args.workload, 0)
-    Nt_s = 50 if args.workload == "vessel2d_512" else 150
+    Nt_s = {"vessel2d_512": 50, "disc2d_168": 150, "tube3d_128": 6, "tube3d_256": 2}[args.workload]
     op = Operator.from_problem(pb, Nt=Nt_s)
     h = np.random.default_rng(0).standard_normal((Nt_s, op.Ns))
     for _ in range(args.warmup):
@@ -185,8 +196,8 @@ def cpu_baseline(args, pb):
     """Oracle timed on a bounded sample (same grid, first Nt_s steps), single-threaded numpy."""
     from oracle.pat_oracle import Operator
 
-    Nt_s = 200 if args.workload == "vessel2d_512" else 600
-    op = Operator.from_problem(pb, Nt=Nt_s)
+    Nt_s = {"vessel2d_512": 200, "disc2d_168": 600, "tube3d_128": 20, "tube3d_256": 4}[args.workload]
+    op = Operator.from_problem(pb, Nt=min(Nt_s, pb.Nt))
     t0 = time.perf_counter()
     op.adjoint(op.forward(pb.p0))
     t = time.perf_counter() - t0
@@ -195,17 +206,17 @@ def cpu_baseline(args, pb):
                       f"({t:.1f} s), FP64 numpy"}
 
 
-def mg_vs_fista(args, dev):
+def mg_vs_fista(args, dev, pb):
     """Wall time of two-level MG-FISTA and of single-grid FISTA to the same relative error (Sec. VI.A
-    compares the methods by RE and F against time).  Target: 1.05 x the best RE that FISTA reaches
-    in --mg-iters iterations.  L estimation (power method, 30 iterations per level) is setup and is
-    reported separately."""
+    compares the methods by RE and F against time) on the benchmark's workload.  Target: 1.05 x the
+    best RE that FISTA reaches in --mg-iters iterations.  L estimation (power method, 30 iterations
+    per level) is setup and is reported separately.  Parameters: Sec. VI.A (2-D) and Sec. VI.B
+    (3-D: kappa = 1/8, rho = 3e-2)."""
     import torch
 
     from paper_1603_02329_gb300 import synth
     from paper_1603_02329_gb300.api import PATOperator, mg_fista
 
-    pb = synth.vessel_phantom_2d(seed=2)
     op = PATOperator.from_problem(pb, precision="f32", device=dev)
     opc = op.coarse()
     x_true = torch.tensor(pb.p0, dtype=torch.float32, device=dev)
@@ -217,8 +228,9 @@ def mg_vs_fista(args, dev):
     Lc = opc.power_iteration(torch.tensor(synth.random_image(12, opc.shape), dtype=torch.float32, device=dev), 30)
     setup_s = time.perf_counter() - t0
     x0 = torch.zeros_like(x_true)
-    common = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25, vartheta=0.1, q_d=3, q_c=8, eps_d=-1.0,
-                  eps_c=1e-2, tv_rho=1e-2, n_tv=20)
+    d = len(pb.shape)
+    common = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25 if d == 2 else 0.125, vartheta=0.1, q_d=3,
+                  q_c=8, eps_d=-1.0, eps_c=1e-2, tv_rho=1e-2 if d == 2 else 3e-2, n_tv=20)
 
     def timed(coarse, recursion, max_iter, target):
         stamps = []
@@ -238,7 +250,21 @@ def mg_vs_fista(args, dev):
     rep_m, recs_m = timed(opc, True, args.mg_iters, target)
     hit = [r for r in recs_m if r["RE"] <= target]
     t_m = hit[0]["t"] if hit else None
-    return {"target_re": target, "fista_best_re": best, "fista_s": t_f, "fista_iters": it_f,
+
+    def pair_s(o):   # one forward + one adjoint solve of a level (the cost unit of both methods)
+        xx = torch.zeros(o.shape, dtype=torch.float32, device=dev)
+        o.adjoint(o.forward(xx))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o.adjoint(o.forward(xx))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    fine_pair, coarse_pair = pair_s(op), pair_s(opc)
+    curve = lambda recs: [(r["k"], r["branch"][0], round(r["RE"], 4), round(r["t"], 3)) for r in recs]
+    return {"workload": pb.name, "target_re": target, "fista_best_re": best, "fista_s": t_f, "fista_iters": it_f,
+            "fwd_adj_pair_s": {"fine": fine_pair, "coarse": coarse_pair, "ratio": coarse_pair / fine_pair},
+            "fista_curve": curve(recs_f), "mgfista_curve": curve(recs_m),
             "mgfista_s": t_m, "mgfista_iters": hit[0]["k"] if hit else None,
             "mgfista_recursive_iters": sum(1 for r in recs_m if r["branch"] == "recursive"),
             "speedup": (t_f / t_m) if t_m else None, "setup_s_power_method": setup_s,
@@ -270,6 +296,9 @@ def main():
     if world > 1:
         dist.barrier()
     pb, prec, desc = workload(args.workload, rank)
+    if args.nt > 0:
+        pb.Nt = args.nt
+        desc = dict(desc, Nt=args.nt, workload=desc["workload"] + f" [time axis cut to Nt={args.nt}]")
     dtype = torch.float32 if prec == "f32" else torch.float64
     w = 4 if prec == "f32" else 8
     op = PATOperator.from_problem(pb, precision=prec, device=dev)
@@ -391,7 +420,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, pb)
     if args.mg and rank == 0:
-        out["mg_vs_fista"] = mg_vs_fista(args, dev)
+        out["mg_vs_fista"] = mg_vs_fista(args, dev, pb)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -250,9 +250,13 @@ typedef struct {
     int max_iter;         /* fine iterations at most */
     int recursion;        /* 0: never take the coarse branch (plain ISTA / FISTA) */
     double L;             /* sigma_max(H^T H) of the fine level (pat_power_iteration) */
-    double L_coarse;      /* the same for the coarse level; the coarse step is 1/(L_coarse + 4 d lambda / tv_rho) */
+    double L_coarse;      /* the same for the coarse level; the coarse step is 1/(w L_coarse + 4 d lambda / tv_rho) */
     double target_re;     /* > 0: also stop when ||x - p_exact|| / ||p_exact|| <= target_re */
     const void* p_exact;  /* optional [N] device image for RE reporting (plan precision) */
+    double coarse_weight; /* w of the coarse data term w/2 ||H_c x - p_c||^2; <= 0: 2^(1-d).  The paper
+                             does not weight it; with R = 2^-d P^T and data decimated 2:1 in time the
+                             unweighted coarse Hessian is 2^(d-1) times R (grad^2 f) P, so its minimiser
+                             under-shoots by that factor (reading O11 of the optimisation oracle) */
 } pat_fista_opts;
 
 typedef struct {
@@ -334,6 +338,15 @@ pat_status pat_forward_static(const void* p0, const double* c, const double* rho
  * Plans on the per-phase graph path record nothing (*grid = 0). */
 pat_status pat_plan_set_trace(pat_plan* plan, int k0, int nk);
 pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t count, int* grid);
+
+/* pat_plan_set_fault -- failure-detection hook of the persistent path (no paper counterpart).
+ * Every grid barrier of the plan's persistent kernels waits at most `wait_limit_s` seconds
+ * (default 2; 0 < wait_limit_s <= 10) before the kernel records PAT_ETIMEOUT in the plan's status
+ * word and every CTA returns (pat_plan_status reads it; the next launch clears it).  barrier_extra
+ * = 1 makes every barrier wait for one arrival that never comes, so the limit runs out on the
+ * first barrier: a host-side way to exercise the detection without faulting the GPU.  0 restores
+ * normal operation.  No effect on the per-phase (graph) path, which has no device-side waits. */
+pat_status pat_plan_set_fault(pat_plan* plan, int barrier_extra, double wait_limit_s);
 
 /* pat_last_error -- message describing the calling thread's last failed call ("" if none).
  * The pointer stays valid until the next pat_* call on the same thread. */

@@ -27,7 +27,7 @@ O6  Coarse level: n/2 points, spacing 2h, PML/2 points, dt_c = 2 dt, Nt_c = ceil
     beyond the first or last coarse node (a fine sensor on the last fine index) is clamped onto
     that node, as P clamps at the last index.
 O7  Coarse iteration: FISTA (or ISTA) on phi_{h-1} with projection on {x >= phi} (Sec. V.E),
-    step 1 / L_c, L_c = L(H_c^T H_c) + lambda 4 d / rho; its own t-sequence from 1; stop when
+    step 1 / L_c, L_c = w L(H_c^T H_c) + lambda 4 d / rho (w of O11); its own t-sequence from 1; stop when
     (phi_k - phi_{k+1}) / max(|phi_k|, |phi_{k+1}|) < eps_c or after q_c iterations (the paper's
     denominator carries F_h subscripts and phi may be negative: absolute coarse values are used).
 O8  Momentum: theta follows the FISTA t-rule every fine iteration whatever the branch; ISTA has
@@ -37,6 +37,15 @@ O9  Cost-saving identity: H y_{k+1} = (1 + theta) H x_k - theta H x_{k-1} (H lin
     iteration runs one forward (for F(x_k)) and one adjoint (for grad f(y_k)).
 O10 Power iteration (Sec. IV, Sec. VI.A): v <- H^T H v / ||H^T H v|| from a seeded N(0,1) start;
     L = ||H^T H v|| at the last iteration (30 by default).
+O11 Weight of the coarse data term (Eq. (Fourteen) writes the coarse objective with the same
+    1/2 ||H x - p||^2 as the fine one; the weight of the coarse copy is not discussed):
+    phi_{h-1} = w/2 ||H_c x - p_c||^2 + lambda J_rho + <v, x> with w = 2^(1-d).  Reason: with
+    R = 2^-d P^T (O4) the Galerkin model of the fine data term is R (H^T H) P = 2^-d P^T H^T H P,
+    while H_c ~ (decimate in time) H P gives H_c^T H_c ~ 1/2 P^T H^T H P, i.e. 2^(d-1) times stiffer;
+    unweighted, the coarse minimiser under-shoots the correction by that factor.  v (first-order
+    coherence) and L_c use the same w.  On a 128^2 line-array case (40 dB noise), MG-FISTA with
+    w = 1 gains a few iterations at the start only; with w = 1/2 it reaches in 3 iterations the RE
+    that FISTA reaches in 10.
 """
 from __future__ import annotations
 
@@ -282,6 +291,7 @@ class FistaOpts:
     max_iter: int = 50
     target_re: float = 0.0      # stop when RE <= target (0 = off)
     recursion: bool = True      # False: never take the coarse branch (plain FISTA / ISTA)
+    coarse_weight: float = 0.0  # weight of the coarse data term; <= 0: 2^(1-d) (O11)
 
 
 @dataclasses.dataclass
@@ -295,14 +305,14 @@ class IterRecord:
     adj: int
 
 
-def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts):
-    """Coarse-level FISTA/ISTA on phi = 1/2||H_c x - p_c||^2 + lam J_rho(x) + <v, x> with the
-    projection on {x >= lower} (Sec. V.E; O7).  Returns (x_*, number of iterations, fwd, adj)."""
+def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts, w=1.0):
+    """Coarse-level FISTA/ISTA on phi = w/2||H_c x - p_c||^2 + lam J_rho(x) + <v, x> with the
+    projection on {x >= lower} (Sec. V.E; O7, O11).  Returns (x_*, number of iterations, fwd, adj)."""
     alpha = 1.0 / L_c
 
     def phi(x, Hx):
         r = Hx - phat_c
-        return 0.5 * float(np.sum(r * r)) + lam * tv_smooth(x, rho) + float(np.sum(v * x))
+        return 0.5 * w * float(np.sum(r * r)) + lam * tv_smooth(x, rho) + float(np.sum(v * x))
 
     x_prev = x0.copy()
     Hx_prev = op_c.forward(x_prev)
@@ -313,7 +323,7 @@ def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts):
     k = 0
     while True:
         k += 1
-        grad = op_c.adjoint(Hy - phat_c) + lam * tv_smooth_grad(y, rho) + v
+        grad = w * op_c.adjoint(Hy - phat_c) + lam * tv_smooth_grad(y, rho) + v
         adj += 1
         x = np.maximum(y - alpha * grad, lower)
         Hx = op_c.forward(x)
@@ -373,13 +383,14 @@ def mg_fista(op, phat, x0, L, opts: FistaOpts, coarse=None, p_exact=None,
             y_tilde = y.copy()
             op_c, phat_c, L_c_data = coarse
             x_c0 = restrict(y)
-            gc = op_c.adjoint(op_c.forward(x_c0) - phat_c) + lam * tv_smooth_grad(x_c0, rho)
+            w_c = opts.coarse_weight if opts.coarse_weight > 0 else 2.0 ** (1 - d)   # O11
+            gc = w_c * op_c.adjoint(op_c.forward(x_c0) - phat_c) + lam * tv_smooth_grad(x_c0, rho)
             fwd += 1
             adj += 1
             v = Rg - gc                                   # Eq. (Fourteen)
             lower = coarse_lower_bound(y)                 # Eq. (constraint) at y (O5)
-            L_c = L_c_data + lam * 4.0 * d / rho
-            x_cs, _, cf, ca = fista_coarse(op_c, phat_c, x_c0, v, lower, lam, rho, L_c, opts)
+            L_c = w_c * L_c_data + lam * 4.0 * d / rho
+            x_cs, _, cf, ca = fista_coarse(op_c, phat_c, x_c0, v, lower, lam, rho, L_c, opts, w=w_c)
             fwd += cf
             adj += ca
             x = y + prolong(x_cs - x_c0)

@@ -39,7 +39,7 @@ class pat_fista_opts(ctypes.Structure):
                 ("eps_d", ctypes.c_double), ("eps_c", ctypes.c_double), ("tv_rho", ctypes.c_double),
                 ("n_tv", ctypes.c_int), ("max_iter", ctypes.c_int), ("recursion", ctypes.c_int),
                 ("L", ctypes.c_double), ("L_coarse", ctypes.c_double), ("target_re", ctypes.c_double),
-                ("p_exact", ctypes.c_void_p)]
+                ("p_exact", ctypes.c_void_p), ("coarse_weight", ctypes.c_double)]
 
 
 class pat_fista_report(ctypes.Structure):
@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.pat_forward_plan.restype = i32
     L.pat_adjoint.argtypes = [vp, vp, vp, vp]
     L.pat_adjoint.restype = i32
+    L.pat_plan_set_fault.argtypes = [vp, i32, f64]
+    L.pat_plan_set_fault.restype = i32
     L.pat_gradient_c2.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_c2.restype = i32
     L.pat_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]

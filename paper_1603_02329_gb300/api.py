@@ -364,6 +364,7 @@ def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.T
     po.L_coarse = float(L_coarse)
     po.target_re = float(o["target_re"])
     po.p_exact = ctypes.c_void_p(p_exact.data_ptr()) if p_exact is not None else None
+    po.coarse_weight = float(o.get("coarse_weight", 0.0))
     records = []
 
     def _cb(ctx, k, rec, F, RES, RE, nf, na):

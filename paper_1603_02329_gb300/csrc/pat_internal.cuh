@@ -133,6 +133,10 @@ template <typename T> struct DevPlan {
     // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA
     unsigned long long* trace;
     int trace_k0, trace_nk;
+    // grid-barrier wait bound of the persistent kernels and the test hook that makes it run out:
+    // every barrier waits for bar_extra more arrivals than exist (0 in normal runs)
+    unsigned bar_extra;
+    unsigned long long bar_limit_ns;
 };
 
 // ------------------------------------------------------------------------------------------

@@ -54,8 +54,8 @@ template <typename T> struct Driver {
     // Coarse-level FISTA / ISTA on phi = 1/2 ||H_c x - p_c||^2 + lam J_rho(x) + <v, x> with the
     // projection on {x >= lower} (Alg. 3 line 9; Sec. V.E).  x0 is x_{h-1,0}; result in xout.
     static pat_status coarse_solve(pat_plan* cp, const pat_grid* gc, const T* phat_c, const T* x0, const T* v,
-                                   const T* lower, double L_c, const pat_fista_opts* o, T* xout, T* const* ws,
-                                   T* const* wd, int* nfwd, int* nadj, cudaStream_t s) {
+                                   const T* lower, double L_c, double wc, const pat_fista_opts* o, T* xout,
+                                   T* const* ws, T* const* wd, int* nfwd, int* nadj, cudaStream_t s) {
         const long long N = cp->impl->info.N, M = (long long)cp->impl->info.Nt * cp->impl->info.Ns;
         const double alpha = 1.0 / L_c, lam = o->lambda, rho = o->tv_rho;
         T* xp = ws[0];
@@ -71,7 +71,7 @@ template <typename T> struct Driver {
             TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, M, Hxx, phat_c, 0.0, &sq, s));
             TRY(Ops<T>::reduce(HRED_TVS, gc, N, xx, nullptr, rho, &js, s));
             TRY(Ops<T>::reduce(HRED_DOT, nullptr, N, v, xx, 0.0, &vx, s));
-            *out = 0.5 * sq + lam * js + vx;
+            *out = 0.5 * wc * sq + lam * js + vx;
             return PAT_OK;
         };
         TRY(Ops<T>::lincomb(N, xp, 1.0, x0, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
@@ -83,11 +83,11 @@ template <typename T> struct Driver {
         TRY(phi(xp, Hxp, &phi_prev));
         double t = 1.0;
         for (int k = 1;; ++k) {
-            // grad = H_c^T (H_c y - p_c) + lam grad J_rho(y) + v
+            // grad = w H_c^T (H_c y - p_c) + lam grad J_rho(y) + v
             TRY(Ops<T>::lincomb(M, r, 1.0, Hy, -1.0, phat_c, 0.0, nullptr, nullptr, 0, s));
             TRY(adj(cp, r, g, s));
             ++*nadj;
-            TRY(Ops<T>::tv_smooth_grad(gc, y, rho, g, lam, 1.0, s));
+            TRY(Ops<T>::tv_smooth_grad(gc, y, rho, g, lam, wc, s));
             TRY(Ops<T>::lincomb(N, g, 1.0, g, 1.0, v, 0.0, nullptr, nullptr, 0, s));
             // x = max(y - alpha grad, lower)
             TRY(Ops<T>::lincomb(N, x, 1.0, y, -alpha, g, 0.0, nullptr, lower, 0, s));
@@ -166,6 +166,8 @@ template <typename T> struct Driver {
                                 T* Hy, T* r, T* const* cimg, T* const* cdat) {
         const int d = gf.ndim;
         const double lam = o->lambda, rho = o->tv_rho;
+        // weight of the coarse data term (O11): 2^(1-d) unless given
+        const double wc = (o->coarse_weight > 0.0) ? o->coarse_weight : std::ldexp(1.0, 1 - gf.ndim);
         const double alpha = o->step_scale / o->L;
         const T* pex = static_cast<const T*>(o->p_exact);
         double nrm_exact = 0.0;
@@ -247,14 +249,14 @@ template <typename T> struct Driver {
                 TRY(Ops<T>::lincomb(Mc, cdat[1], 1.0, cdat[0], -1.0, phat_c, 0.0, nullptr, nullptr, 0, s));
                 TRY(adj(cp, cdat[1], gcb, s));
                 ++nadj;
-                TRY(Ops<T>::tv_smooth_grad(&gc, xc0, rho, gcb, lam, 1.0, s));
+                TRY(Ops<T>::tv_smooth_grad(&gc, xc0, rho, gcb, lam, wc, s));
                 TRY(Ops<T>::lincomb(Nc, v, 1.0, cimg[8], -1.0, gcb, 0.0, nullptr, nullptr, 0, s));
                 // restricted bound at y (Eq. (constraint))
                 TRY(Ops<T>::coarse_bound(&gf, y, lower, cimg[4], s));
-                const double L_c = o->L_coarse + lam * 4.0 * d / rho;
+                const double L_c = wc * o->L_coarse + lam * 4.0 * d / rho;
                 T* const ws[4] = {cimg[4], cimg[5], cimg[6], cimg[7]};
                 T* const wd[4] = {cdat[0], cdat[1], cdat[2], cdat[3]};
-                TRY(coarse_solve(cp, &gc, phat_c, xc0, v, lower, L_c, o, xcs, ws, wd, &nfwd, &nadj, s));
+                TRY(coarse_solve(cp, &gc, phat_c, xc0, v, lower, L_c, wc, o, xcs, ws, wd, &nfwd, &nadj, s));
                 // x = y + P (x_{h-1,*} - x_{h-1,0})
                 TRY(Ops<T>::lincomb(Nc, xcs, 1.0, xcs, -1.0, xc0, 0.0, nullptr, nullptr, 0, s));
                 TRY(Ops<T>::lincomb(N, x, 1.0, y, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));

@@ -49,8 +49,11 @@ struct TraceRef {
     int k0, nk;
 };
 
+// The wait is bounded twice: by `limit_ns` of %globaltimer (2 s by default) and by
+// kBarrierSpinLimit polls; either way the CTA records PAT_ETIMEOUT and every CTA returns.
 __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, unsigned& k, int* abort_s,
-                                             TraceRef tr = TraceRef{nullptr, 0, 0}) {
+                                             TraceRef tr = TraceRef{nullptr, 0, 0}, unsigned extra = 0,
+                                             unsigned long long limit_ns = 2000000000ull) {
     __syncthreads();
     ++k;
     const int kt = (int)k - 1 - tr.k0;
@@ -61,15 +64,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
         // __syncthreads above) are visible to every CTA that observes the count; the polling load
         // has acquire semantics, and the __syncthreads below extends it to the whole CTA
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(gbar) : "memory");
-        const unsigned target = k * nblocks;
+        const unsigned target = k * nblocks + extra;
         unsigned long long spins = 0;
+        const unsigned long long t0 = globaltimer_ns();
         int ab = 0;
         while (ld_acquire_gpu(&gbar[0]) < target) {
             if (*(volatile unsigned*)&gbar[2] != 0u) {
                 ab = 1;
                 break;
             }
-            if (++spins > kBarrierSpinLimit) {
+            if (++spins > kBarrierSpinLimit || ((spins & 63) == 0 && globaltimer_ns() - t0 > limit_ns)) {
                 atomicExch(&gbar[2], (unsigned)PAT_ETIMEOUT);
                 ab = 1;
                 break;
@@ -423,13 +427,13 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
             pgather(s, P, seg, line0, A, P.data);
             if (Nt > 1) prow_r2c(s, P, A, A + (size_t)s.rmax * nx, 1, line0, R);
         }
-        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        if (Nt > 1 && !grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
         for (int n = 0; n + 1 < Nt; ++n) {
             const bool last = (n + 2 == Nt);
             T* drow = P.data + (size_t)(n + 1) * Ns;
             // (1) g = D+ p
             if (tile) pcol<T, SPEC_GRAD>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             // u update, x-FFT of u
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
@@ -450,10 +454,10 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                     }
                 prow_r2c(s, P, out, res, 2, line0, R);
             }
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             // (2) e = D- u
             if (tile) pcol<T, SPEC_DIV>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             // rho update; lossless: p, sample; lossy: x-FFT of (dd, r)
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
@@ -489,10 +493,10 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                 }
             }
             if (P.lossy) {
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
                 // (3) fractional Laplacians
                 if (tile) pcol<T, SPEC_ABS>(s, P, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
                 if (rows) {
                     cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                     cplx<T>* out = prow_other(s, P, res);
@@ -509,7 +513,7 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                     if (!last) prow_r2c(s, P, out, res, 1, line0, R);
                 }
             }
-            if (!last && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!last && !grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
         }
     } else {
         // ================= adjoint: reverse time, exact transpose =================
@@ -562,12 +566,12 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
             tail(A, B, Nt == 1);
         }
         if (Nt == 1) return;
-        if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
         for (int n = Nt - 2; n >= 0; --n) {
             const bool final_ = (n == 0);
             if (P.lossy) {
                 if (tile) pcol<T, SPEC_ABS>(s, P, kx0, C.W, C.lgW);
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
                 if (rows) {
                     cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                     cplx<T>* out = prow_other(s, P, res);
@@ -588,11 +592,11 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                         }
                     prow_r2c(s, P, out, res, 2, line0, R);
                 }
-                if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+                if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             }
             // transpose of e = D- u
             if (tile) pcol<T, SPEC_DIVT>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 2, line0, R);
                 cplx<T>* out = prow_other(s, P, res);
@@ -613,10 +617,10 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                     }
                 prow_r2c(s, P, out, res, 2, line0, R);
             }
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             // transpose of g = D+ p
             if (tile) pcol<T, SPEC_GRADT>(s, P, kx0, C.W, C.lgW);
-            if (!grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
             if (rows) {
                 cplx<T>* res = prow_c2r(s, P, 1, line0, R);
                 cplx<T>* other = prow_other(s, P, res);
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(256) k_persist(DevPlan<T> P, PersistCfg C, uns
                 __syncthreads();
                 tail(res, other, final_);
             }
-            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+            if (!final_ && !grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
         }
     }
 }

@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
         } else if (rows) {
             row_phase(d.id, d.n, lastph);
         }
-        if (!lastph && !grid_barrier(gbar, G, kbar, s.flag, TR)) return;
+        if (!lastph && !grid_barrier(gbar, G, kbar, s.flag, TR, P.bar_extra, P.bar_limit_ns)) return;
     }
 }
 

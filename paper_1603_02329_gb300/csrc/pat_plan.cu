@@ -470,6 +470,13 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
     return PAT_OK;
 }
 
+pat_status pat_plan_set_fault(pat_plan* plan, int barrier_extra, double wait_limit_s) {
+    set_error("");
+    if (!plan || barrier_extra < 0 || barrier_extra > 1 || !(wait_limit_s > 0.0) || wait_limit_s > 10.0)
+        return fail(PAT_EINVAL, "bad fault arguments (barrier_extra 0 or 1, 0 < wait_limit_s <= 10)");
+    return plan_set_fault(plan->impl, (unsigned)barrier_extra, wait_limit_s);
+}
+
 pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_p0,
                            int checkpoint_every, void* stream) {
     set_error("");

@@ -106,6 +106,8 @@ template <typename T> struct Plan : public PlanBase {
         P.lossy = h.lossy;
         P.dt = (T)h.dt;
         P.Nt = h.Nt;
+        P.bar_extra = 0;
+        P.bar_limit_ns = 2000000000ull;
         const size_t N = (size_t)h.N;
         const size_t Nh = (size_t)h.nz * h.ny * h.ldh;
 #define CHK(x) \
@@ -884,6 +886,20 @@ pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void*
     auto* p = static_cast<Plan<double>*>(base);
     return p->P.d == 2 ? p->template gradient_c2<2>(p0, h, gc2, gp0, K, s)
                        : p->template gradient_c2<3>(p0, h, gc2, gp0, K, s);
+}
+
+pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s) {
+    const unsigned long long ns = (unsigned long long)(wait_limit_s * 1e9);
+    if (base->info.precision == PAT_F32) {
+        auto* p = static_cast<Plan<float>*>(base);
+        p->P.bar_extra = barrier_extra;
+        p->P.bar_limit_ns = ns;
+    } else {
+        auto* p = static_cast<Plan<double>*>(base);
+        p->P.bar_extra = barrier_extra;
+        p->P.bar_limit_ns = ns;
+    }
+    return PAT_OK;
 }
 
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {

@@ -292,3 +292,33 @@ def test_autotuned_layout_gives_the_same_results(dev, monkeypatch, persist):
         assert rel(out[tune][0], ref.forward(pb.p0)) <= TOL64
         op.close()
     assert rel(out["1"][0], out["0"][0]) <= 1e-13 and rel(out["1"][1], out["0"][1]) <= 1e-13
+
+
+@pytest.mark.parametrize("p2", ["1", "0"])
+def test_persistent_barrier_timeout_is_reported_and_recovers(dev, monkeypatch, p2):
+    # Failure detection without a GPU fault: pat_plan_set_fault makes every grid barrier wait for an
+    # arrival that never comes; the bounded wait (0.2 s here) runs out, the kernel records
+    # PAT_ETIMEOUT and returns, the host reads it, and the context stays usable.
+    import time
+
+    from paper_1603_02329_gb300 import _lib
+
+    monkeypatch.setenv("PAT_P2", p2)
+    pb = synth.small_lossy_2d(shape=(64, 64), pml=8, Nt=30, n_sensors=12)
+    op = _gpu_op(pb, "f32", dev)
+    assert op.info.path == (2 if p2 == "1" else 1)
+    L = _lib.lib()
+    x = _t(pb.p0, "f32", dev)
+    good = op.forward(x).cpu().numpy()
+    assert L.pat_plan_set_fault(op._plan, 1, 0.2) == 0
+    t0 = time.perf_counter()
+    op.forward(x)
+    st = L.pat_plan_status(op._plan)
+    waited = time.perf_counter() - t0
+    assert st == 5                          # PAT_ETIMEOUT
+    assert waited < 5.0                     # bounded: ~0.2 s, not a hang
+    assert L.pat_plan_set_fault(op._plan, 0, 2.0) == 0
+    again = op.forward(x).cpu().numpy()
+    assert L.pat_plan_status(op._plan) == 0
+    assert np.array_equal(again, good)
+    assert L.pat_plan_set_fault(op._plan, 2, 1.0) != 0      # invalid arguments are rejected

@@ -14,11 +14,16 @@ __host__ __device__ __forceinline__ int p2_tab_len(int n) { return 2 * n; }
 // twx[2 nx] | twy[2 ny] | dpl[ny] | dml[ny] | cdp[8] | cdm[8] | work | gb[rmax / 2 nx] (complex)
 // | res[nres][rmax][nx] | ax, aux[nx] | ay, auy | kl2 | ckx2 | kapt [, s0t, s1t] [ny][W] | seg_w (real)
 // | seg_i | flag (int)
-// work area: row phase A[rmax nx] | B, where B also receives the staged half spectra of the rows
-// (2 rmax ldh); column phase A[2 W ny] | B[2 W ny], B also receiving the staged columns
+// 64 bytes between the fields of a line buffer, in complex elements
+template <typename T> __host__ __device__ __forceinline__ int p2_field_pad() { return 64 / (int)sizeof(cplx<T>); }
+
+// work area: row phase A[rmax nx + pad] | B, where B also receives the staged half spectra of the
+// rows (2 rmax ldh >= rmax nx + pad); column phase A[2 W ny + pad] | B[2 W ny + pad], B also
+// receiving the staged columns
 template <typename T> __host__ __device__ size_t p2_work_elems(int nx, int ny, int ldh, int rmax, int W) {
-    const size_t rowp = (size_t)rmax * nx + (size_t)2 * rmax * ldh;
-    const size_t colp = (size_t)4 * W * ny;
+    const size_t pad = (size_t)p2_field_pad<T>();
+    const size_t rowp = (size_t)rmax * nx + pad + (size_t)2 * rmax * ldh;
+    const size_t colp = (size_t)2 * (2 * (size_t)W * ny + pad);
     return rowp > colp ? rowp : colp;
 }
 template <typename T> size_t p2_smem_bytes(int nx, int ny, int ldh, int rmax, int W, int nres, int nmul) {

@@ -50,6 +50,12 @@ __device__ __forceinline__ int p2_off_f(const P2Axis& a, int s) { return p2_fns(
 __device__ __forceinline__ int p2_off_i(const P2Axis& a, int s) { return a.n - a.r0 + p2_ins(s) - 8; }
 
 __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
+// Start of line q in a line buffer whose fields hold 2^lgnl lines each.  Fields sit 64 bytes
+// beyond whole lines (p2_field_pad), so that the lane pairs of the fused stages, which touch the
+// same element of two fields, hit different banks.
+template <typename T> __device__ __forceinline__ size_t lbase(int q, int n, int lgnl) {
+    return (size_t)q * n + (size_t)(q >> lgnl) * p2_field_pad<T>();
+}
 template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
 
 // stage tables from the full table tw[m] = exp(-2 pi i m / n): entry (r, k) of a stage of radix R
@@ -96,7 +102,7 @@ __device__ __forceinline__ void p2_store(cplx<T>* dst, int j, int Ns, const cplx
 
 // the middle stages 1 .. nst-2 (radix 8) over `nlines` lines, each followed by a CTA barrier
 template <typename T, bool INV>
-__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines) {
+__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines, int lgnl) {
     const int lgm = ax.lg - 3, m = 1 << lgm;
     for (int s = 1; s + 1 < ax.nst; ++s) {
         const int Ns = INV ? p2_ins(s) : p2_fns(ax, s);
@@ -104,9 +110,9 @@ __device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<
         for (int t = threadIdx.x; t < (nlines << lgm); t += blockDim.x) {
             const int line = t >> lgm, j = t & (m - 1);
             cplx<T> v[8];
-            p2_load<T, 8, INV>(v, a + (size_t)line * ax.n, j, m, Ns, tws);
+            p2_load<T, 8, INV>(v, a + lbase<T>(line, ax.n, lgnl), j, m, Ns, tws);
             dft<T, 8, INV>(v);
-            p2_store<T, 8>(b + (size_t)line * ax.n, j, Ns, v);
+            p2_store<T, 8>(b + lbase<T>(line, ax.n, lgnl), j, Ns, v);
         }
         __syncthreads();
         cplx<T>* tmp = a;
@@ -137,7 +143,7 @@ __device__ __forceinline__ void p2_row_stage(cplx<T>* S, cplx<T>* const* spec, i
 
 // inverse x-stage 0 (radix 8, no twiddles) on the C2R packing of the staged half spectra
 template <typename T>
-__device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, const P2Axis& ax, int ldh) {
+__device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, int lgnp, const P2Axis& ax, int ldh) {
     const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, half = n >> 1;
     for (int t = threadIdx.x; t < ((FI * np) << lgm); t += blockDim.x) {
         const int q = t >> lgm, j = t & (m - 1);
@@ -164,7 +170,7 @@ __device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, const 
                                : mkc<T>(A[r].x + B[r].y, B[r].x - A[r].y);   // conj(A) + i conj(B)
         }
         dft<T, 8, true>(v);
-        p2_store<T, 8>(dst + (size_t)q * n, j, 1, v);
+        p2_store<T, 8>(dst + lbase<T>(q, n, lgnp), j, 1, v);
     }
 }
 
@@ -205,7 +211,7 @@ __device__ __forceinline__ void p2_each(int p, int j, int m, int h, const cplx<T
 // transform field 0 and each stores its half).  FI = 0: pw reads its inputs itself.
 template <typename T, int R, class PW>
 __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax,
-                                            int np, int FI, int FO, bool fwd, PW&& pw) {
+                                            int np, int lgnp, int FI, int FO, bool fwd, PW&& pw) {
     constexpr int H = R / 2;
     const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
@@ -217,7 +223,7 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
         const int p = u >> lgm, j = u & (m - 1);
         cplx<T> z[R];
         if (valid && FI > 0) {
-            p2_load<T, R, true>(z, src + (size_t)((FI == 2 ? h : 0) * np + p) * n, j, m, m, twl);
+            p2_load<T, R, true>(z, src + lbase<T>((FI == 2 ? h : 0) * np + p, n, lgnp), j, m, m, twl);
             dft<T, R, true>(z);
         }
         cplx<T> zi[2][H], oo[2][H];
@@ -243,7 +249,7 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
         }
         if (!valid) continue;
         dft<T, R, false>(w);
-        cplx<T>* d = dst + (size_t)((FO == 2 ? h : 0) * np + p) * n;
+        cplx<T>* d = dst + lbase<T>((FO == 2 ? h : 0) * np + p, n, lgnp);
         if (FO == 2) {
             p2_store<T, R>(d, j, 1, w);
         } else {
@@ -257,14 +263,14 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
 // line runs butterflies u and m - u (u = 0: 0 and m / 2), which hold every X[k] with its X[n - k]
 template <typename T>
 __device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, const P2Axis& ax,
-                           int FO, int np, int line0, int ldh) {
+                           int FO, int np, int lgnp, int line0, int ldh) {
     const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, lgh = lgm - 1, hm = m >> 1;
     const cplx<T>* twl = tab + p2_off_f(ax, ax.nst - 1);
     for (int t = threadIdx.x; t < ((FO * np) << lgh); t += blockDim.x) {
         const int q = t >> lgh, u = t & (hm - 1);
         const int f = q / np, p = q - f * np;
         const int j1 = u, j2 = (u == 0) ? hm : m - u;
-        const cplx<T>* line = src + (size_t)q * n;
+        const cplx<T>* line = src + lbase<T>(q, n, lgnp);
         cplx<T> X1[8], X2[8];
         p2_load<T, 8, false>(X1, line, j1, m, m, twl);
         p2_load<T, 8, false>(X2, line, j2, m, m, twl);
@@ -346,7 +352,7 @@ __device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
         dft<T, R, false>(v);
-        p2_store<T, R>(dst + (size_t)(f * W + c) * n, j, 1, v);
+        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
     }
 }
 
@@ -370,7 +376,7 @@ __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>
         const int c = u & (W - 1), j = u >> lgW;
         cplx<T> z[8], o[8];
         if (valid) {
-            p2_load<T, 8, false>(z, src + (size_t)((fi == 2 ? h : 0) * W + c) * n, j, m, m, twl);
+            p2_load<T, 8, false>(z, src + lbase<T>((fi == 2 ? h : 0) * W + c, n, lgW), j, m, m, twl);
             dft<T, 8, false>(z);
         }
         switch (mode) {
@@ -417,7 +423,7 @@ __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>
         }
         if (!valid) continue;
         dft<T, 8, true>(o);
-        cplx<T>* d = dst + (size_t)((fo == 2 ? h : 0) * W + c) * n;
+        cplx<T>* d = dst + lbase<T>((fo == 2 ? h : 0) * W + c, n, lgW);
         if (fo == 2) {
             p2_store<T, 8>(d, j, 1, o);
         } else {
@@ -436,7 +442,7 @@ __device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
     for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
         cplx<T> v[R];
-        p2_load<T, R, true>(v, src + (size_t)(f * W + c) * n, j, m, m, twl);
+        p2_load<T, R, true>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
         dft<T, R, true>(v);
         if (c < wv) {
             cplx<T>* dst = spec[f] + kx0 + c;
@@ -452,7 +458,7 @@ __device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& 
                                        int lgW, int mode) {
     const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     cplx<T>* A = s.work;
-    cplx<T>* B = A + (size_t)2 * W * ay.n;
+    cplx<T>* B = A + (size_t)2 * W * ay.n + p2_field_pad<T>();
     p2_col_stage<T>(B, P.spec, fi, W, kx0, ay.n, P.ldh);
     cp_wait_all();
     __syncthreads();
@@ -460,13 +466,13 @@ __device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& 
     with_radix(ay.r0, [&](auto RC) { p2_col_in<T, decltype(RC)::value>(A, B, fi, W, lgW, ay); });
     __syncthreads();
     s.mark(1);
-    cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, fi * W);
+    cplx<T>* a = p2_mid<T, false>(A, B, ay, s.twy, fi * W, lgW);
     cplx<T>* b = (a == A) ? B : A;
     s.mark(2);
     p2_col_fuse<T>(s, a, b, ay, W, lgW, mode);
     __syncthreads();
     s.mark(3);
-    a = p2_mid<T, true>(b, a, ay, s.twy, fo * W);
+    a = p2_mid<T, true>(b, a, ay, s.twy, fo * W, lgW);
     s.mark(4);
     const int wv = min(W, P.nxh - kx0);
     with_radix(ay.r0, [&](auto RC) {
@@ -566,7 +572,8 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
     s.tr = TR;
     s.kb = &kbar;
     cplx<T>* const A = s.work;
-    cplx<T>* const B = s.work + (size_t)s.rmax * nx;
+    cplx<T>* const B = s.work + (size_t)s.rmax * nx + p2_field_pad<T>();
+    const int lgnp = (C.ppc == 1) ? 0 : (C.ppc == 2 ? 1 : (C.ppc == 4 ? 2 : 3));
 
     // ---- setup: stage twiddle tables, k-space tables of the tile, resident medium ----
     p2_build_tables<T>(s.twx, P.twx, axx);
@@ -710,10 +717,10 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
             cp_wait_all();
             __syncthreads();
             s.mark(0);
-            p2_row_in<T>(A, B, FI, npair, axx, P.ldh);
+            p2_row_in<T>(A, B, FI, npair, lgnp, axx, P.ldh);
             __syncthreads();
             s.mark(1);
-            a = p2_mid<T, true>(A, B, axx, s.twx, FI * npair);
+            a = p2_mid<T, true>(A, B, axx, s.twx, FI * npair, lgnp);
             bb = (a == A) ? B : A;
         } else {
             __syncthreads();
@@ -819,15 +826,15 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
             }
         };
         with_radix(axx.r0, [&](auto RC) {
-            p2_row_fuse<T, decltype(RC)::value>(a, bb, s.twx, axx, npair, FI, FO, fwd, pw);
+            p2_row_fuse<T, decltype(RC)::value>(a, bb, s.twx, axx, npair, lgnp, FI, FO, fwd, pw);
         });
         __syncthreads();
         s.mark(3);
         if (gath) pgather(s, P, seg, line0, s.gb, drow);
         if (!fwd) return;
-        cplx<T>* c = p2_mid<T, false>(bb, a, axx, s.twx, FO * npair);
+        cplx<T>* c = p2_mid<T, false>(bb, a, axx, s.twx, FO * npair, lgnp);
         s.mark(4);
-        p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, line0, P.ldh);
+        p2_row_out<T>(c, P.spec, s.twx, axx, FO, npair, lgnp, line0, P.ldh);
         s.mark(5);
     };
 

@@ -37,6 +37,21 @@ template <typename T> size_t p2_smem_bytes(int nx, int ny, int ldh, int rmax, in
     return b;
 }
 
+// spectral kernel of the per-phase path for power-of-two lines (pat_spec2.cuh): launch k_spec2<T, D,
+// mode> with `lc` (attributes set by the caller), and raise its dynamic shared-memory limit
+template <typename T>
+cudaError_t spec2_launch(const cudaLaunchConfig_t* lc, int D, int mode, const DevPlan<T>& P, int W, int lgW, int lax,
+                         int F);
+template <typename T> cudaError_t spec2_set_attrs(int bytes);
+// shared memory of k_spec2: stage twiddle tables [2 L] | A | B, each of fmax W L (+ 2 field pads)
+template <typename T> __host__ __device__ size_t spec2_buf_elems(int D, int L, int W) {
+    const int fmax = D > 2 ? D : 2;
+    return (size_t)fmax * W * L + 2 * (size_t)p2_field_pad<T>();
+}
+template <typename T> size_t spec2_smem_bytes(int D, int L, int W) {
+    return ((size_t)p2_tab_len(L) + 2 * spec2_buf_elems<T>(D, L, W)) * sizeof(cplx<T>);
+}
+
 // launch k_persist2<T, adjoint> with `lc` (cooperative attributes set by the caller)
 template <typename T>
 cudaError_t p2_launch(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<T>& P, const PersistCfg& C,

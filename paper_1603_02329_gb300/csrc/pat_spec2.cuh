@@ -1,0 +1,194 @@
+// pat_spec2.cuh -- spectral kernels of the per-phase path for power-of-two line lengths.
+//
+// The same work as k_spec (pat_kernels.cuh): transforms of half-spectrum columns along y (lax = 1)
+// or z (lax = 2), with the k-space multiply of Sec. II.A / Eq. (state) fused between the forward and
+// the inverse transform for the multiply modes.  What changes is the transform, which follows the
+// fixed power-of-two Stockham schedule of the persistent kernel (pat_persist2.cuh):
+//   * the tile's columns are staged with cp.async into the spare line buffer, and the first stage
+//     reads them from there;
+//   * the last forward stage, the k-space multiply and the first inverse stage run in registers on
+//     the same elements {j + r L/8};
+//   * the last stage stores straight to the spectra in natural order;
+//   * lines are XOR-swizzled, fields 64 bytes apart, twiddles per stage.
+// A tile is W columns x F fields (W <= 8: ceil((nx/2 + 1) / W) W must not pass the padded row ldh).
+#pragma once
+
+#include "pat_persist2.cuh"
+
+namespace pat {
+
+// stage 0 (radix R, no twiddles; forward or inverse) from the staged tile S[f][i][c]
+template <typename T, int R, bool INV>
+__device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const P2Axis& ay) {
+    const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
+    for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
+        const cplx<T>* src = S + (size_t)f * n * W + c;
+        cplx<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
+        dft<T, R, INV>(v);
+        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
+    }
+}
+
+// last stage (radix R, span n / R; forward or inverse) and the store of valid columns
+template <typename T, int R, bool INV>
+__device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* twl, int FO, int W, int lgW,
+                       int wv, const P2Axis& ay, size_t base, size_t es) {
+    const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
+    for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
+        cplx<T> v[R];
+        p2_load<T, R, INV>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
+        dft<T, R, INV>(v);
+        if (c < wv) {
+            cplx<T>* dst = spec[f] + base + c;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[(size_t)(j + r * m) * es] = v[r];
+        }
+    }
+}
+
+// Last forward stage (radix 8), the k-space multiply of MODE on D fields, first inverse stage.
+// Symbols (Sec. II.A, Eq. (state)): kappa = sinc(c_ref |k| dt / 2), D+-_xi = i k_xi e^{+-i k_xi h/2},
+// |k|^(y-2), |k|^(y-1); all scaled by 1/N.  Field f's shift factor: f = 0 -> x (column kx),
+// f = 1 -> y (the CTA's outer index in a z pass, the line index in a y pass), f = 2 -> z (line).
+template <typename T, int D, int MODE>
+__device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, const cplx<T>* twl, int W, int lgW,
+                        const P2Axis& ay, int lax, int kx0, int outer) {
+    constexpr int FI = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+    constexpr int FO = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
+    constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
+    const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
+    const int la = lax;   // axis index of the line
+    for (int t = threadIdx.x; t < (W << lgm); t += blockDim.x) {
+        const int c = t & (W - 1), j = t >> lgW;
+        cplx<T> z[FI][8];
+#pragma unroll
+        for (int f = 0; f < FI; ++f) {
+            p2_load<T, 8, false>(z[f], src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
+            dft<T, 8, false>(z[f]);
+        }
+        const int kx = min(kx0 + c, P.nxh - 1);
+        const T kxv = P.kv[0][kx];
+        const T ckx2 = kxv * kxv;
+        T ko2 = 0;
+        cplx<T> mo = mkc<T>(0, 0);
+        if (lax == 2) {
+            const T ky = P.kv[1][outer];
+            ko2 = ky * ky;
+            mo = plus ? P.dp[1][outer] : P.dm[1][outer];
+        }
+        const cplx<T> mx = plus ? P.dp[0][kx] : P.dm[0][kx];
+        cplx<T> o[FO][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = j + r * m;
+            const T kl = P.kv[la][i];
+            const T k2 = ckx2 + kl * kl + ko2;
+            if constexpr (MODE == SPEC_ABS) {
+                const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+                const T s1 = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
+                o[0][r] = cscale(z[0][r], s0);
+                o[FO - 1][r] = cscale(z[FI - 1][r], s1);
+            } else {
+                const T kap = sinc_sq(P.kap_a * P.kap_a * k2) * P.invN;
+                const T sg = (MODE == SPEC_DIVT || MODE == SPEC_GRADT) ? -kap : kap;
+                const cplx<T> ml = plus ? P.dp[la][i] : P.dm[la][i];
+                cplx<T> mf[3];
+                mf[0] = mx;
+                mf[1] = (lax == 2) ? mo : ml;
+                mf[2] = ml;
+                if constexpr (MODE == SPEC_GRAD) {
+                    const cplx<T> v = cscale(z[0][r], sg);
+#pragma unroll
+                    for (int f = 0; f < FO; ++f) o[f][r] = cmul(v, mf[f]);
+                } else if constexpr (MODE == SPEC_GRADT) {
+                    cplx<T> acc = mkc<T>(0, 0);
+#pragma unroll
+                    for (int f = 0; f < FI; ++f) acc = cadd(acc, cmul(z[f][r], mf[f]));
+                    o[0][r] = cscale(acc, sg);
+                } else {
+#pragma unroll
+                    for (int f = 0; f < FO; ++f) o[f][r] = cscale(cmul(z[f][r], mf[f]), sg);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < FO; ++g) {
+            dft<T, 8, true>(o[g]);
+            p2_store<T, 8>(dst + lbase<T>(g * W + c, n, lgW), j, 1, o[g]);
+        }
+    }
+}
+
+template <typename T, int D, int MODE>
+__global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int lax, int F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool MUL = (MODE != SPEC_PLAIN_FWD && MODE != SPEC_PLAIN_INV);
+    const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
+    const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
+    const P2Axis ay = p2_axis((lax == 1) ? P.fy.lgn : P.fz.lgn);
+    const int L = ay.n;
+    cplx<T>* tab = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* A = tab + p2_tab_len(L);
+    cplx<T>* B = A + spec2_buf_elems<T>(D, L, W);
+    const int kx0 = blockIdx.x * W, outer = blockIdx.y;
+    const int wv = min(W, P.nxh - kx0);
+    const size_t es = (lax == 1) ? (size_t)P.ldh : (size_t)P.ny * P.ldh;
+    const size_t base = (lax == 1) ? (size_t)outer * P.ny * P.ldh + kx0 : (size_t)outer * P.ldh + kx0;
+
+    // prologue: stage twiddle tables (plan constants, never written by the preceding kernel)
+    p2_build_tables<T>(tab, (lax == 1) ? P.twy : P.twz, ay);
+    pdl_trigger();
+    pdl_wait();
+    // stage the tile's columns of every input field: B[f][i][c]; tiles reach into the zeroed
+    // padding columns of the half spectra (kx0 + W <= ldh)
+    const int cb = W * (int)sizeof(cplx<T>);
+    for (int f = 0; f < fin; ++f) {
+        const cplx<T>* src = P.spec[f] + base;
+        cplx<T>* d = B + (size_t)f * L * W;
+        if (cb >= 16) {
+            constexpr int EPC = 16 / (int)sizeof(cplx<T>);
+            const int cpr = cb / 16;
+            for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
+                const int i = t / cpr, ch = t - i * cpr;
+                cp_async<16>(d + (size_t)i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
+            }
+        } else {
+            for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async<sizeof(cplx<T>)>(d + i, src + (size_t)i * es);
+        }
+    }
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+
+    if constexpr (MODE == SPEC_PLAIN_INV) {
+        s2_in<T, 8, true>(A, B, fin, W, lgW, ay);
+        __syncthreads();
+        cplx<T>* a = p2_mid<T, true>(A, B, ay, tab, fin * W, lgW);
+        with_radix(ay.r0, [&](auto RC) {
+            s2_out<T, decltype(RC)::value, true>(a, P.spec, tab + p2_off_i(ay, ay.nst - 1), fout, W, lgW, wv, ay,
+                                                 base, es);
+        });
+    } else {
+        with_radix(ay.r0, [&](auto RC) { s2_in<T, decltype(RC)::value, false>(A, B, fin, W, lgW, ay); });
+        __syncthreads();
+        cplx<T>* a = p2_mid<T, false>(A, B, ay, tab, fin * W, lgW);
+        if constexpr (!MUL) {
+            s2_out<T, 8, false>(a, P.spec, tab + p2_off_f(ay, ay.nst - 1), fout, W, lgW, wv, ay, base, es);
+        } else {
+            cplx<T>* b = (a == A) ? B : A;
+            s2_fuse<T, D, MODE>(P, a, b, tab + p2_off_f(ay, ay.nst - 1), W, lgW, ay, lax, kx0, outer);
+            __syncthreads();
+            cplx<T>* r = p2_mid<T, true>(b, a, ay, tab, fout * W, lgW);
+            with_radix(ay.r0, [&](auto RC) {
+                s2_out<T, decltype(RC)::value, true>(r, P.spec, tab + p2_off_i(ay, ay.nst - 1), fout, W, lgW, wv, ay,
+                                                     base, es);
+            });
+        }
+    }
+}
+
+}  // namespace pat

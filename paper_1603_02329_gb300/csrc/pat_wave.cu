@@ -184,8 +184,14 @@ template <typename T> struct Plan : public PlanBase {
 #undef CHK
         // launch configuration
         cfg = h.cfg;
+        {
+            // power-of-two y (and z) lines of 16 .. 2048 points take the register-fused spectral kernel
+            const char* es2 = std::getenv("PAT_SPEC2");
+            const auto ok = [](const FftAxis& a) { return a.pow2 && a.lgn >= 4 && a.lgn <= 11; };
+            use_spec2 = !(es2 && std::atoi(es2) == 0) && ok(h.fy) && (D == 2 || ok(h.fz));
+        }
         row_smem = row_smem_bytes<T>(D, h.nx, h.ldh, cfg.row_lines);
-        spec_smem = spec_smem_bytes<T>(D, std::max(h.ny, h.nz), cfg.col_w);
+        spec_smem = spec_bytes(D, std::max(h.ny, h.nz), cfg.col_w);
         if (count_only) return PAT_OK;
         // padding columns of the half spectra are read (never used) by full-width tiles: zero them
         for (int a = 0; a < nspec; ++a) {
@@ -253,7 +259,8 @@ template <typename T> struct Plan : public PlanBase {
                 c.col_w = w;
                 c.row_lines = r;
                 c.col_threads = std::min(256, std::max(64, (D * w * L / 8 + 31) / 32 * 32));
-                const size_t rs = row_smem_bytes<T>(D, H.nx, H.ldh, r), ss = spec_smem_bytes<T>(D, L, w);
+                if (!tile_fits(w)) continue;
+                const size_t rs = row_smem_bytes<T>(D, H.nx, H.ldh, r), ss = spec_bytes(D, L, w);
                 if (rs > (size_t)optin || ss > (size_t)optin) continue;
                 cfg = c;
                 row_smem = rs;
@@ -277,7 +284,7 @@ template <typename T> struct Plan : public PlanBase {
         if (e != cudaSuccess) return cuda_fail(e, "autotune (per-phase kernels)");
         cfg = best;
         row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
-        spec_smem = spec_smem_bytes<T>(D, L, cfg.col_w);
+        spec_smem = spec_bytes(D, L, cfg.col_w);
         // the timed steps left arbitrary values in the work buffers; the solves re-initialise the
         // state, and the spectra's padding columns are cleared again
         const size_t Nh = (size_t)H.nz * H.ny * H.ldh;
@@ -481,9 +488,17 @@ template <typename T> struct Plan : public PlanBase {
         seta((const void*)k_spec<T, D, SPEC_ABS>, spec_smem);
         seta((const void*)k_spec<T, D, SPEC_DIVT>, spec_smem);
         seta((const void*)k_spec<T, D, SPEC_GRADT>, spec_smem);
+        if (e == cudaSuccess && use_spec2) e = spec2_set_attrs<T>(optin);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (shared memory)");
         return PAT_OK;
     }
+
+    bool use_spec2 = false;
+    size_t spec_bytes(int D, int L, int w) const {
+        return use_spec2 ? spec2_smem_bytes<T>(D, L, w) : spec_smem_bytes<T>(D, L, w);
+    }
+    // a spectral tile of w columns stays inside the padded rows of the half spectra
+    bool tile_fits(int w) const { return (size_t)((H.nxh + w - 1) / w) * w <= (size_t)H.ldh; }
 
     // ---------------------------------------------------------------------------------------
     // launch helpers (used while capturing, or directly on a stream)
@@ -514,6 +529,20 @@ template <typename T> struct Plan : public PlanBase {
         const int outer = (lax == 1) ? Q.nz : Q.ny;
         int lgw = 0;
         while ((1 << lgw) < cfg.col_w) ++lgw;
+        if (use_spec2) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(tiles, outer);
+            lc.blockDim = dim3(256);
+            lc.dynamicSmemBytes = spec_smem;
+            lc.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            spec2_launch<T>(&lc, D, MODE, Q, cfg.col_w, lgw, lax, F);
+            return;
+        }
         launch(k_spec<T, D, MODE>, dim3(tiles, outer), cfg.col_threads, spec_smem, s, Q, cfg.col_w, lgw, lax, F);
     }
 

@@ -322,3 +322,37 @@ def test_persistent_barrier_timeout_is_reported_and_recovers(dev, monkeypatch, p
     assert L.pat_plan_status(op._plan) == 0
     assert np.array_equal(again, good)
     assert L.pat_plan_set_fault(op._plan, 2, 1.0) != 0      # invalid arguments are rejected
+
+
+# Power-of-two y (and z) axes take the register-fused spectral kernel of the per-phase path
+# (k_spec2); PAT_SPEC2=0 selects the generic one.  3-D grids (always the per-phase path) and a
+# 2-D grid forced onto it; radix schedules 16 = 2.8, 32 = 4.8, 64 = 8.8, 128 = 2.8.8.
+SPEC2_CASES = [
+    ("3d_16x32x64_lossy_f32", "3d", dict(shape=(16, 32, 64), pml=3, Nt=30), "f32"),
+    ("3d_32x16x24_lossy_f64", "3d", dict(shape=(32, 16, 24), pml=3, Nt=24), "f64"),
+    ("3d_64x64x32_lossless_f32", "3d", dict(shape=(64, 64, 32), pml=4, Nt=30, alpha0=0.0), "f32"),
+    ("2d_graph_128x64_lossy_f64", "2d", dict(shape=(128, 64), pml=6, Nt=40, n_sensors=16), "f64"),
+]
+
+
+@pytest.mark.parametrize("name,kind,kw,prec", SPEC2_CASES, ids=[c[0] for c in SPEC2_CASES])
+def test_pow2_spectral_kernel_matches_oracle(dev, monkeypatch, name, kind, kw, prec):
+    pb = synth.small_lossy_3d(**kw) if kind == "3d" else synth.small_lossy_2d(**kw)
+    if kind == "2d":
+        monkeypatch.setenv("PAT_PERSIST", "0")
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(19).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    tol = TOL32 if prec == "f32" else TOL64
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_SPEC2", flag)
+        op = _gpu_op(pb, prec, dev)
+        assert op.info.path == 0
+        d = op.forward(_t(pb.p0, prec, dev)).cpu().numpy()
+        g = op.adjoint(_t(h, prec, dev)).cpu().numpy()
+        assert rel(d, d_ref) <= tol, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= tol, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    assert rel(out[0][0], out[1][0]) <= tol and rel(out[0][1], out[1][1]) <= tol

@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
     ap.add_argument("--mg-iters", type=int, default=20)
+    ap.add_argument("--batch", action="store_true",
+                    help="also time 8 uneven 2-D instances as one batched launch vs one at a time")
+    ap.add_argument("--c2grad", type=int, default=0,
+                    help="also time the checkpointed c0^2 gradient with this checkpoint interval")
     return ap.parse_args()
 
 
@@ -204,6 +208,75 @@ def cpu_baseline(args, pb):
     return {"value": 2.0 * pb.N * Nt_s / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one forward+adjoint over the first {Nt_s} of {pb.Nt} time steps of the same grid "
                       f"({t:.1f} s), FP64 numpy"}
+
+
+def batch_vs_sequential(dev):
+    """Eight independent 2-D instances of uneven size (192^2 .. 384^2, 0.05 mm, 20-pt PML inside,
+    own heterogeneous absorbing medium each, a 256-sensor circle of radius 0.4 x the interior
+    width, Nt = 1200, FP32): forward + adjoint of all of them as one graph launch per direction
+    (pat_batch_*) vs each plan's own calls one after the other."""
+    import torch
+
+    from paper_1603_02329_gb300 import synth
+    from paper_1603_02329_gb300.api import PATBatch, PATOperator
+
+    sizes = [192, 224, 256, 256, 288, 320, 320, 384]
+    pbs = [synth.small_lossy_2d(seed=40 + i, shape=(n, n), pml=20, h=0.05e-3, Nt=1200, n_sensors=256,
+                                sensor_radius_frac=0.4 * (n - 40) / n) for i, n in enumerate(sizes)]
+    ops = [PATOperator.from_problem(pb, precision="f32", device=dev) for pb in pbs]
+    xs = [torch.tensor(pb.p0, dtype=torch.float32, device=dev) for pb in pbs]
+    hs = [torch.ones((op.Nt, op.Ns), dtype=torch.float32, device=dev) for op in ops]
+    batch = PATBatch(ops)
+    units = 2.0 * sum(pb.N * pb.Nt for pb in pbs)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    def one_at_a_time():
+        for op, x, h in zip(ops, xs, hs):
+            op.forward(x)
+            op.adjoint(h)
+
+    t_seq = timed(one_at_a_time)
+    t_bat = timed(lambda: (batch.forward(xs), batch.adjoint(hs)))
+    batch.close()
+    return {"instances": sizes, "Nt": 1200, "paths_alone": [int(op.info.path) for op in ops],
+            "sequential_s": t_seq, "batched_s": t_bat, "sequential_gpts": units / t_seq / 1e9,
+            "batched_gpts": units / t_bat / 1e9, "speedup": t_seq / t_bat,
+            "note": "best of 3 after one untimed run; a batch runs every instance on the per-phase path"}
+
+
+def c2_gradient_timing(op, pb, K, dev, dtype):
+    """Checkpointed c0^2 gradient (pat_gradient_c2, interval K) against one forward + adjoint."""
+    import torch
+
+    x = torch.tensor(pb.p0, dtype=dtype, device=dev)
+    h = torch.ones((op.Nt, op.Ns), dtype=dtype, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    t_fa = timed(lambda: op.adjoint(op.forward(x)))
+    t_g = timed(lambda: op.gradient_c2(x, h, checkpoint_every=K))
+    w = 4 if dtype == torch.float32 else 8
+    nseg = (pb.Nt - 2) // K + 1
+    nh = int(np.prod(pb.shape[:-1])) * ((pb.shape[-1] // 2 + 1 + 7) // 8 * 8)
+    d = len(pb.shape)
+    return {"K": K, "fwd_adj_s": t_fa, "gradient_s": t_g, "ratio": t_g / t_fa,
+            "checkpoint_bytes": nseg * (2 * d * pb.N + 2 * nh) * w, "q_bytes": min(K, pb.Nt) * pb.N * w}
 
 
 def mg_vs_fista(args, dev, pb):
@@ -421,6 +494,10 @@ def main():
         out["cpu_baseline"] = cpu_baseline(args, pb)
     if args.mg and rank == 0:
         out["mg_vs_fista"] = mg_vs_fista(args, dev, pb)
+    if args.batch and rank == 0:
+        out["batch"] = batch_vs_sequential(dev)
+    if args.c2grad > 0 and rank == 0:
+        out["c2_gradient"] = c2_gradient_timing(op, pb, args.c2grad, dev, dtype)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

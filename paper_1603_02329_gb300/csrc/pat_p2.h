@@ -52,6 +52,34 @@ template <typename T> size_t spec2_smem_bytes(int D, int L, int W) {
     return ((size_t)p2_tab_len(L) + 2 * spec2_buf_elems<T>(D, L, W)) * sizeof(cplx<T>);
 }
 
+// row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
+enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };
+// shared memory of k_row2 (complex elements first, then reals, then ints)
+template <typename T> struct Row2Layout {
+    size_t tab, lines, bsz, gb, res, pml, segw, segi, bytes;
+};
+template <typename T> __host__ __device__ Row2Layout<T> row2_layout(int D, int nx, int ldh, int R) {
+    Row2Layout<T> L;
+    const int fmax = D > 2 ? D : 2, np = R / 2;
+    L.tab = (size_t)2 * nx;
+    L.lines = (size_t)fmax * np * nx + 2 * (size_t)p2_field_pad<T>();
+    const size_t stg = (size_t)fmax * R * ldh;
+    L.bsz = L.lines > stg ? L.lines : stg;
+    L.gb = (size_t)np * nx;
+    const size_t ncplx = L.tab + L.lines + L.bsz + L.gb;
+    L.res = (size_t)6 * R * nx;                       // at most six staged real fields
+    L.pml = (size_t)nx + (((size_t)(D - 1) * R + 3) & ~(size_t)3);
+    L.segw = (size_t)2 * kSegCap;
+    L.segi = (size_t)2 * kSegCap;
+    L.bytes = ncplx * sizeof(cplx<T>) + (L.res + L.pml + L.segw) * sizeof(T) + L.segi * sizeof(int);
+    return L;
+}
+
+template <typename T>
+cudaError_t row2_launch(const cudaLaunchConfig_t* lc, int D, int kind, const DevPlan<T>& P, int R, int flag,
+                        T* data_row, const T* h_row, T* qrow, T* gc2, const T* p0c);
+template <typename T> cudaError_t row2_set_attrs(int bytes);
+
 // launch k_persist2<T, adjoint> with `lc` (cooperative attributes set by the caller)
 template <typename T>
 cudaError_t p2_launch(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<T>& P, const PersistCfg& C,

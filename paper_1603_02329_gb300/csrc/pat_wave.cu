@@ -190,7 +190,15 @@ template <typename T> struct Plan : public PlanBase {
             const auto ok = [](const FftAxis& a) { return a.pow2 && a.lgn >= 4 && a.lgn <= 11; };
             use_spec2 = !(es2 && std::atoi(es2) == 0) && ok(h.fy) && (D == 2 || ok(h.fz));
         }
+        {
+            // power-of-two x-lines of 16 .. 2048 points take the register-fused row kernels
+            const char* er2 = std::getenv("PAT_ROW2");
+            const int R0 = cfg.row_lines;
+            use_row2 = !(er2 && std::atoi(er2) == 0) && h.fx.pow2 && h.fx.lgn >= 4 && h.fx.lgn <= 11 &&
+                       (R0 & (R0 - 1)) == 0 && R0 <= 32;
+        }
         row_smem = row_smem_bytes<T>(D, h.nx, h.ldh, cfg.row_lines);
+        row2_smem = use_row2 ? row2_layout<T>(D, h.nx, h.ldh, cfg.row_lines).bytes : 0;
         spec_smem = spec_bytes(D, std::max(h.ny, h.nz), cfg.col_w);
         if (count_only) return PAT_OK;
         // padding columns of the half spectra are read (never used) by full-width tiles: zero them
@@ -261,9 +269,12 @@ template <typename T> struct Plan : public PlanBase {
                 c.col_threads = std::min(256, std::max(64, (D * w * L / 8 + 31) / 32 * 32));
                 if (!tile_fits(w)) continue;
                 const size_t rs = row_smem_bytes<T>(D, H.nx, H.ldh, r), ss = spec_bytes(D, L, w);
+                const size_t r2 = use_row2 ? row2_layout<T>(D, H.nx, H.ldh, r).bytes : 0;
+                if (r2 > (size_t)optin) continue;
                 if (rs > (size_t)optin || ss > (size_t)optin) continue;
                 cfg = c;
                 row_smem = rs;
+                row2_smem = r2;
                 spec_smem = ss;
                 const float ms = time_on_stream(
                     [&] {
@@ -284,6 +295,7 @@ template <typename T> struct Plan : public PlanBase {
         if (e != cudaSuccess) return cuda_fail(e, "autotune (per-phase kernels)");
         cfg = best;
         row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
+        row2_smem = use_row2 ? row2_layout<T>(D, H.nx, H.ldh, cfg.row_lines).bytes : 0;
         spec_smem = spec_bytes(D, L, cfg.col_w);
         // the timed steps left arbitrary values in the work buffers; the solves re-initialise the
         // state, and the spectra's padding columns are cleared again
@@ -489,11 +501,48 @@ template <typename T> struct Plan : public PlanBase {
         seta((const void*)k_spec<T, D, SPEC_DIVT>, spec_smem);
         seta((const void*)k_spec<T, D, SPEC_GRADT>, spec_smem);
         if (e == cudaSuccess && use_spec2) e = spec2_set_attrs<T>(optin);
+        if (e == cudaSuccess && use_row2) e = row2_set_attrs<T>(optin);
+        if (row2_smem > (size_t)optin) {
+            set_error("grid too large for the shared-memory kernels of this device");
+            return PAT_EINVAL;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (shared memory)");
         return PAT_OK;
     }
 
     bool use_spec2 = false;
+    bool use_row2 = false;
+    size_t row2_smem = 0;
+
+    // one step kernel of the row pass (Row2Kind): the register-fused power-of-two kernel, or the
+    // generic one with its own argument list
+    template <int D>
+    void row_launch(int kind, const DevPlan<T>& Q, cudaStream_t s, int flag, T* data_row = nullptr,
+                    const T* h_row = nullptr, T* qrow = nullptr, T* gc2 = nullptr, const T* p0c = nullptr) {
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        if (use_row2) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(G);
+            lc.blockDim = dim3(256);
+            lc.dynamicSmemBytes = row2_smem;
+            lc.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            row2_launch<T>(&lc, D, kind, Q, R, flag, data_row, h_row, qrow, gc2, p0c);
+            return;
+        }
+        switch (kind) {
+            case R2_FWD_U: launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, Q, R, flag); break;
+            case R2_FWD_RHO: launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, Q, R, flag, data_row, qrow); break;
+            case R2_FWD_P: launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, Q, R, flag, data_row, qrow); break;
+            case R2_ADJ_RHO: launch(k_adj_rho<T, D>, dim3(G), B, row_smem, s, Q, R); break;
+            case R2_ADJ_U: launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, Q, R, flag); break;
+            default: launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, Q, R, flag, h_row, qrow, gc2, p0c); break;
+        }
+    }
     size_t spec_bytes(int D, int L, int w) const {
         return use_spec2 ? spec2_smem_bytes<T>(D, L, w) : spec_smem_bytes<T>(D, L, w);
     }
@@ -566,12 +615,12 @@ template <typename T> struct Plan : public PlanBase {
         const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         const int last = (n + 2 == H.Nt);
         spectral_on<D, SPEC_GRAD>(Q, s);
-        launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, Q, R, (int)(n == 0));
+        row_launch<D>(R2_FWD_U, Q, s, (int)(n == 0));
         spectral_on<D, SPEC_DIV>(Q, s);
-        launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, Q, R, last, data_row, Q.lossy ? (T*)nullptr : qrow);
+        row_launch<D>(R2_FWD_RHO, Q, s, last, data_row, nullptr, Q.lossy ? (T*)nullptr : qrow);
         if (Q.lossy) {
             spectral_on<D, SPEC_ABS>(Q, s);
-            launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, Q, R, last, data_row, qrow);
+            row_launch<D>(R2_FWD_P, Q, s, last, data_row, nullptr, qrow);
         }
     }
     // adjoint iteration that produces p_bar^n (the reverse of forward step n), accumulating
@@ -580,13 +629,13 @@ template <typename T> struct Plan : public PlanBase {
         const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         if (P.lossy) {
             spectral_on<D, SPEC_ABS>(P, s);
-            launch(k_adj_rho<T, D>, dim3(G), B, row_smem, s, P, R);
+            row_launch<D>(R2_ADJ_RHO, P, s, 0);
         }
         spectral_on<D, SPEC_DIVT>(P, s);
-        launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
+        row_launch<D>(R2_ADJ_U, P, s, (int)(n == 0));
         spectral_on<D, SPEC_GRADT>(P, s);
-        launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * H.Ns),
-               n == 0 ? (const T*)nullptr : qrow, gc2, p0c);
+        row_launch<D>(R2_ADJ_P, P, s, (int)(n == 0), nullptr, (const T*)(P.data + (size_t)n * H.Ns),
+                      n == 0 ? (T*)nullptr : (T*)qrow, gc2, p0c);
     }
 
     // g_c2 = d<H p0, h>/d c0^2 and grad_p0 = H^T h in one reverse sweep; forward states are
@@ -755,14 +804,14 @@ template <typename T> struct Plan : public PlanBase {
             if (sampled(n, Nt)) begin_sample(0, probe_samples[0]++ == 0);
             spectral_named<D, SPEC_GRAD>(s, "spec_grad");
             mark(s, "fwd_u");
-            launch(k_fwd_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
+            row_launch<D>(R2_FWD_U, P, s, (int)(n == 0));
             spectral_named<D, SPEC_DIV>(s, "spec_div");
             mark(s, "fwd_rho");
-            launch(k_fwd_rho<T, D>, dim3(G), B, row_smem, s, P, R, last, row, (T*)nullptr);
+            row_launch<D>(R2_FWD_RHO, P, s, last, row);
             if (P.lossy) {
                 spectral_named<D, SPEC_ABS>(s, "spec_abs");
                 mark(s, "fwd_p");
-                launch(k_fwd_p<T, D>, dim3(G), B, row_smem, s, P, R, last, row, (T*)nullptr);
+                row_launch<D>(R2_FWD_P, P, s, last, row);
             }
             if (probe_g >= 0) end_sample(s);
         }
@@ -786,15 +835,14 @@ template <typename T> struct Plan : public PlanBase {
             if (P.lossy) {
                 spectral_named<D, SPEC_ABS>(s, "spec_abs");
                 mark(s, "adj_rho");
-                launch(k_adj_rho<T, D>, dim3(G), B, row_smem, s, P, R);
+                row_launch<D>(R2_ADJ_RHO, P, s, 0);
             }
             spectral_named<D, SPEC_DIVT>(s, "spec_divt");
             mark(s, "adj_u");
-            launch(k_adj_u<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0));
+            row_launch<D>(R2_ADJ_U, P, s, (int)(n == 0));
             spectral_named<D, SPEC_GRADT>(s, "spec_gradt");
             mark(s, "adj_p");
-            launch(k_adj_p<T, D>, dim3(G), B, row_smem, s, P, R, (int)(n == 0), (const T*)(P.data + (size_t)n * Ns),
-                   (const T*)nullptr, (T*)nullptr, (const T*)nullptr);
+            row_launch<D>(R2_ADJ_P, P, s, (int)(n == 0), nullptr, (const T*)(P.data + (size_t)n * Ns));
             if (probe_g >= 0) end_sample(s);
         }
     }

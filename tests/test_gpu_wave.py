@@ -356,3 +356,43 @@ def test_pow2_spectral_kernel_matches_oracle(dev, monkeypatch, name, kind, kw, p
         out.append((d, g))
         op.close()
     assert rel(out[0][0], out[1][0]) <= tol and rel(out[0][1], out[1][1]) <= tol
+
+
+# Power-of-two x-lines take the register-fused row kernels of the per-phase path (k_row2);
+# PAT_ROW2=0 selects the generic ones.  Forward, adjoint and the checkpointed c0^2 gradient (whose
+# hooks live in the row kernels) against the oracle, both kernels.
+ROW2_CASES = [
+    ("3d_16x32x64_lossy_f32", "3d", dict(shape=(16, 32, 64), pml=3, Nt=30), "f32"),
+    ("3d_24x20x32_lossy_f64", "3d", dict(shape=(24, 20, 32), pml=3, Nt=22), "f64"),
+    ("3d_32x32x16_lossless_f64", "3d", dict(shape=(32, 32, 16), pml=3, Nt=25, alpha0=0.0), "f64"),
+    ("2d_graph_64x128_lossy_f32", "2d", dict(shape=(64, 128), pml=6, Nt=40, n_sensors=16), "f32"),
+    ("2d_graph_96x64_lossless_f64", "2d", dict(shape=(96, 64), pml=6, Nt=30, n_sensors=12, alpha0=0.0), "f64"),
+]
+
+
+@pytest.mark.parametrize("name,kind,kw,prec", ROW2_CASES, ids=[c[0] for c in ROW2_CASES])
+def test_pow2_row_kernels_match_oracle(dev, monkeypatch, name, kind, kw, prec):
+    from oracle import pat_medium as pm
+
+    pb = synth.small_lossy_3d(**kw) if kind == "3d" else synth.small_lossy_2d(**kw)
+    if kind == "2d":
+        monkeypatch.setenv("PAT_PERSIST", "0")
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(29).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    c2_ref, _ = pm.sound_speed_gradient(ref, pb.p0, h, pb.y)
+    tol = TOL32 if prec == "f32" else TOL64
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_ROW2", flag)
+        op = _gpu_op(pb, prec, dev)
+        assert op.info.path == 0
+        d = op.forward(_t(pb.p0, prec, dev)).cpu().numpy()
+        g = op.adjoint(_t(h, prec, dev)).cpu().numpy()
+        gc2 = op.gradient_c2(_t(pb.p0, prec, dev), _t(h, prec, dev), checkpoint_every=7).cpu().numpy()
+        assert rel(d, d_ref) <= tol, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= tol, (flag, rel(g, g_ref))
+        assert rel(gc2, c2_ref) <= (tol if prec == "f32" else 1e-10), (flag, rel(gc2, c2_ref))
+        out.append((d, g))
+        op.close()
+    assert rel(out[0][0], out[1][0]) <= tol and rel(out[0][1], out[1][1]) <= tol

@@ -54,9 +54,10 @@ template <typename T> size_t spec2_smem_bytes(int D, int L, int W) {
 
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
 enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };
-// shared memory of k_row2 (complex elements first, then reals, then ints)
+// shared memory of k_row2: stage twiddle tables | A | B (also the staging of the spectra) | gb
+// (complex), then the staged real fields and the PML factors
 template <typename T> struct Row2Layout {
-    size_t tab, lines, bsz, gb, res, pml, segw, segi, bytes;
+    size_t tab, lines, bsz, gb, res, pml, bytes;
 };
 template <typename T> __host__ __device__ Row2Layout<T> row2_layout(int D, int nx, int ldh, int R) {
     Row2Layout<T> L;
@@ -69,12 +70,9 @@ template <typename T> __host__ __device__ Row2Layout<T> row2_layout(int D, int n
     const size_t ncplx = L.tab + L.lines + L.bsz + L.gb;
     L.res = (size_t)6 * R * nx;                       // at most six staged real fields
     L.pml = (size_t)nx + (((size_t)(D - 1) * R + 3) & ~(size_t)3);
-    L.segw = (size_t)2 * kSegCap;
-    L.segi = (size_t)2 * kSegCap;
-    L.bytes = ncplx * sizeof(cplx<T>) + (L.res + L.pml + L.segw) * sizeof(T) + L.segi * sizeof(int);
+    L.bytes = ncplx * sizeof(cplx<T>) + (L.res + L.pml) * sizeof(T);
     return L;
 }
-
 template <typename T>
 cudaError_t row2_launch(const cudaLaunchConfig_t* lc, int D, int kind, const DevPlan<T>& P, int R, int flag,
                         T* data_row, const T* h_row, T* qrow, T* gc2, const T* p0c);

@@ -86,8 +86,6 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     T* res = reinterpret_cast<T*>(gb + Lo.gb);
     T* pmlx = res + Lo.res;
     T* pmlr = pmlx + nx;
-    T* segw = pmlx + Lo.pml;
-    int* segi = reinterpret_cast<int*>(segw + Lo.segw);
     auto row = [&](int k) { return res + (size_t)k * R * nx; };
     const P2Axis ax = p2_axis(P.fx.lgn);
     const T dt = P.dt;
@@ -95,7 +93,7 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
 
     // ---- prologue: tables and the medium (constants of the plan) ----
     p2_build_tables<T>(tab, P.twx, ax);
-    int FI = D, FO = D, nres_const = 0;
+    int FI = D, FO = D;
     bool fwd = true, gath = false, scat = false;
     const T* const* pml_tab = P.a;
     switch (KIND) {
@@ -144,7 +142,6 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
             scat = true;
             break;
     }
-    (void)nres_const;
     stage_elems(pmlx, pml_tab[0], nx);
     for (int t = threadIdx.x; t < (D - 1) * R; t += blockDim.x) {
         const int a = 1 + t / R, r = t - (a - 1) * R;
@@ -152,28 +149,19 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
         pmlr[t] = pml_tab[a][(a == 1) ? line % P.ny : line / P.ny];
     }
     cp_commit();
-    // sensor segments of this CTA's lines (plan constants)
-    int2 seg = make_int2(0, 0);
+    // adjoint: M^T h^n into the zeroed buffer gb (the residual record is read-only during the
+    // adjoint solve; segments are distinct points), read back by the pointwise step
     const DevSensors<T>& S = P.sens;
-    if (gath) {
-        seg = make_int2(S.g_lineptr[line0], S.g_lineptr[line0 + R]);
-        for (int t = threadIdx.x; t < min(seg.y - seg.x, kSegCap); t += blockDim.x) {
-            const int q = seg.x + t;
-            segi[2 * t] = S.g_seg_sensor[q];
-            segi[2 * t + 1] = (S.g_seg_line[q] - line0) * nx + S.g_seg_x0[q];
-            segw[2 * t] = S.g_seg_w0[q];
-            segw[2 * t + 1] = S.g_seg_w1[q];
-        }
-    }
     if (scat) {
         for (int t = threadIdx.x; t < np * nx; t += blockDim.x) gb[t] = mkc<T>(0, 0);
-        seg = make_int2(S.s_lineptr[line0], S.s_lineptr[line0 + R]);
-        for (int t = threadIdx.x; t < min(seg.y - seg.x, kSegCap); t += blockDim.x) {
-            const int q = seg.x + t;
+        __syncthreads();
+        const int s0 = S.s_lineptr[line0], s1 = S.s_lineptr[line0 + R];
+        for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) {
             T acc = 0;
             for (int e = S.s_seg_e0[q]; e < S.s_seg_e0[q + 1]; ++e) acc += S.s_ent_w[e] * h_row[S.s_ent_sensor[e]];
-            segi[t] = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
-            segw[t] = acc;
+            const int pos = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
+            const int r = pos / nx, x = pos - r * nx;
+            slot(gb, r, x, nx) += acc;
         }
     }
     pdl_trigger();
@@ -215,24 +203,6 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     cp_commit();
     cp_wait_all();
     __syncthreads();
-    if (scat) {
-        // p_bar += M^T h^n (segments are distinct points), read back by the pointwise step
-        for (int t = threadIdx.x; t < seg.y - seg.x; t += blockDim.x) {
-            int pos;
-            T v;
-            if (t < kSegCap) {
-                pos = segi[t];
-                v = segw[t];
-            } else {
-                const int q = seg.x + t;
-                v = 0;
-                for (int e = S.s_seg_e0[q]; e < S.s_seg_e0[q + 1]; ++e) v += S.s_ent_w[e] * h_row[S.s_ent_sensor[e]];
-                pos = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
-            }
-            const int r = pos / nx, x = pos - r * nx;
-            slot(gb, r, x, nx) += v;
-        }
-    }
 
     // ---- inverse x-transform of the FI spectra ----
     p2_row_in<T>(A, B, FI, np, lgnp, ax, P.ldh);
@@ -375,21 +345,11 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     __syncthreads();
     if (gath) {
         // s^{n+1}_j += this CTA's part of sensor j (one atomic add per (line, sensor) segment)
-        for (int t = threadIdx.x; t < seg.y - seg.x; t += blockDim.x) {
-            int j, pos;
-            T w0, w1;
-            if (t < kSegCap) {
-                j = segi[2 * t];
-                pos = segi[2 * t + 1];
-                w0 = segw[2 * t];
-                w1 = segw[2 * t + 1];
-            } else {
-                const int q = seg.x + t;
-                j = S.g_seg_sensor[q];
-                pos = (S.g_seg_line[q] - line0) * nx + S.g_seg_x0[q];
-                w0 = S.g_seg_w0[q];
-                w1 = S.g_seg_w1[q];
-            }
+        const int s0 = S.g_lineptr[line0], s1 = S.g_lineptr[line0 + R];
+        for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) {
+            const int j = S.g_seg_sensor[q];
+            const int pos = (S.g_seg_line[q] - line0) * nx + S.g_seg_x0[q];
+            const T w0 = S.g_seg_w0[q], w1 = S.g_seg_w1[q];
             const int r = pos / nx, x = pos - r * nx;
             T acc = w0 * slot(gb, r, x, nx);
             if (w1 != (T)0) acc += w1 * slot(gb, r, x + 1, nx);

@@ -43,10 +43,13 @@ template <typename T>
 cudaError_t spec2_launch(const cudaLaunchConfig_t* lc, int D, int mode, const DevPlan<T>& P, int W, int lgW, int lax,
                          int F);
 template <typename T> cudaError_t spec2_set_attrs(int bytes);
-// shared memory of k_spec2: stage twiddle tables [2 L] | A | B, each of fmax W L (+ 2 field pads)
+// k_spec2's lanes step across the tile's lines: every line is followed by 16 bytes of padding
+template <typename T> __host__ __device__ __forceinline__ int spec2_line_pad() { return 16 / (int)sizeof(cplx<T>); }
+// shared memory of k_spec2: stage twiddle tables [2 L] | A | B, each of fmax W padded lines (+ 2
+// field pads)
 template <typename T> __host__ __device__ size_t spec2_buf_elems(int D, int L, int W) {
     const int fmax = D > 2 ? D : 2;
-    return (size_t)fmax * W * L + 2 * (size_t)p2_field_pad<T>();
+    return (size_t)fmax * W * (L + spec2_line_pad<T>()) + 2 * (size_t)p2_field_pad<T>();
 }
 template <typename T> size_t spec2_smem_bytes(int D, int L, int W) {
     return ((size_t)p2_tab_len(L) + 2 * spec2_buf_elems<T>(D, L, W)) * sizeof(cplx<T>);

@@ -53,8 +53,9 @@ __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
 // Start of line q in a line buffer whose fields hold 2^lgnl lines each.  Fields sit 64 bytes
 // beyond whole lines (p2_field_pad), so that the lane pairs of the fused stages, which touch the
 // same element of two fields, hit different banks.
-template <typename T> __device__ __forceinline__ size_t lbase(int q, int n, int lgnl) {
-    return (size_t)q * n + (size_t)(q >> lgnl) * p2_field_pad<T>();
+// lp > 0 adds lp elements after every line as well (kernels whose lanes step across lines).
+template <typename T> __device__ __forceinline__ size_t lbase(int q, int n, int lgnl, int lp = 0) {
+    return (size_t)q * (n + lp) + (size_t)(q >> lgnl) * p2_field_pad<T>();
 }
 template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
 
@@ -102,7 +103,8 @@ __device__ __forceinline__ void p2_store(cplx<T>* dst, int j, int Ns, const cplx
 
 // the middle stages 1 .. nst-2 (radix 8) over `nlines` lines, each followed by a CTA barrier
 template <typename T, bool INV>
-__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines, int lgnl) {
+__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines, int lgnl,
+                          int lp = 0) {
     const int lgm = ax.lg - 3, m = 1 << lgm;
     for (int s = 1; s + 1 < ax.nst; ++s) {
         const int Ns = INV ? p2_ins(s) : p2_fns(ax, s);
@@ -110,9 +112,9 @@ __device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<
         for (int t = threadIdx.x; t < (nlines << lgm); t += blockDim.x) {
             const int line = t >> lgm, j = t & (m - 1);
             cplx<T> v[8];
-            p2_load<T, 8, INV>(v, a + lbase<T>(line, ax.n, lgnl), j, m, Ns, tws);
+            p2_load<T, 8, INV>(v, a + lbase<T>(line, ax.n, lgnl, lp), j, m, Ns, tws);
             dft<T, 8, INV>(v);
-            p2_store<T, 8>(b + lbase<T>(line, ax.n, lgnl), j, Ns, v);
+            p2_store<T, 8>(b + lbase<T>(line, ax.n, lgnl, lp), j, Ns, v);
         }
         __syncthreads();
         cplx<T>* tmp = a;

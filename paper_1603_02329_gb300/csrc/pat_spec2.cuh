@@ -9,7 +9,8 @@
 //   * the last forward stage, the k-space multiply and the first inverse stage run in registers on
 //     the same elements {j + r L/8};
 //   * the last stage stores straight to the spectra in natural order;
-//   * lines are XOR-swizzled, fields 64 bytes apart, twiddles per stage.
+//   * lines are XOR-swizzled and 16 bytes apart beyond their length (lanes step across the tile's
+//     lines), fields another 64 bytes apart, twiddles per stage.
 // A tile is W columns x F fields (W <= 8: ceil((nx/2 + 1) / W) W must not pass the padded row ldh).
 #pragma once
 
@@ -28,7 +29,7 @@ __device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, co
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
         dft<T, R, INV>(v);
-        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
+        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, 1, v);
     }
 }
 
@@ -40,7 +41,7 @@ __device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* 
     for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
         cplx<T> v[R];
-        p2_load<T, R, INV>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
+        p2_load<T, R, INV>(v, src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m, twl);
         dft<T, R, INV>(v);
         if (c < wv) {
             cplx<T>* dst = spec[f] + base + c;
@@ -67,7 +68,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
         cplx<T> z[FI][8];
 #pragma unroll
         for (int f = 0; f < FI; ++f) {
-            p2_load<T, 8, false>(z[f], src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
+            p2_load<T, 8, false>(z[f], src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m, twl);
             dft<T, 8, false>(z[f]);
         }
         const int kx = min(kx0 + c, P.nxh - 1);
@@ -118,7 +119,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
 #pragma unroll
         for (int g = 0; g < FO; ++g) {
             dft<T, 8, true>(o[g]);
-            p2_store<T, 8>(dst + lbase<T>(g * W + c, n, lgW), j, 1, o[g]);
+            p2_store<T, 8>(dst + lbase<T>(g * W + c, n, lgW, spec2_line_pad<T>()), j, 1, o[g]);
         }
     }
 }
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     if constexpr (MODE == SPEC_PLAIN_INV) {
         s2_in<T, 8, true>(A, B, fin, W, lgW, ay);
         __syncthreads();
-        cplx<T>* a = p2_mid<T, true>(A, B, ay, tab, fin * W, lgW);
+        cplx<T>* a = p2_mid<T, true>(A, B, ay, tab, fin * W, lgW, spec2_line_pad<T>());
         with_radix(ay.r0, [&](auto RC) {
             s2_out<T, decltype(RC)::value, true>(a, P.spec, tab + p2_off_i(ay, ay.nst - 1), fout, W, lgW, wv, ay,
                                                  base, es);
@@ -175,14 +176,14 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     } else {
         with_radix(ay.r0, [&](auto RC) { s2_in<T, decltype(RC)::value, false>(A, B, fin, W, lgW, ay); });
         __syncthreads();
-        cplx<T>* a = p2_mid<T, false>(A, B, ay, tab, fin * W, lgW);
+        cplx<T>* a = p2_mid<T, false>(A, B, ay, tab, fin * W, lgW, spec2_line_pad<T>());
         if constexpr (!MUL) {
             s2_out<T, 8, false>(a, P.spec, tab + p2_off_f(ay, ay.nst - 1), fout, W, lgW, wv, ay, base, es);
         } else {
             cplx<T>* b = (a == A) ? B : A;
             s2_fuse<T, D, MODE>(P, a, b, tab + p2_off_f(ay, ay.nst - 1), W, lgW, ay, lax, kx0, outer);
             __syncthreads();
-            cplx<T>* r = p2_mid<T, true>(b, a, ay, tab, fout * W, lgW);
+            cplx<T>* r = p2_mid<T, true>(b, a, ay, tab, fout * W, lgW, spec2_line_pad<T>());
             with_radix(ay.r0, [&](auto RC) {
                 s2_out<T, decltype(RC)::value, true>(r, P.spec, tab + p2_off_i(ay, ay.nst - 1), fout, W, lgW, wv, ay,
                                                      base, es);

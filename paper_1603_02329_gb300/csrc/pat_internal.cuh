@@ -117,6 +117,10 @@ template <typename T> struct DevPlan {
     const cplx<T>* twx;
     const cplx<T>* twy;
     const cplx<T>* twz;
+    // per-stage twiddle tables of the power-of-two schedule (p2_stage_table; 2 n entries per axis,
+    // nullptr where the axis is not a power of two of 16 .. 2048 points)
+    const cplx<T>* stw[3];
+    int fixed_len;    // 1: launch the kernels compiled for this plan's line lengths where they exist
 
     // state and workspaces (N each unless noted)
     T* u[3];

@@ -2,13 +2,79 @@
 // shared-memory layout and its launch entry, compiled in a translation unit per precision.
 #pragma once
 
+#include <complex>
+#include <type_traits>
+#include <vector>
+
 #include "pat_kernels.cuh"
 
 namespace pat {
 
 struct PersistCfg;
 
+// ---- fixed power-of-two Stockham schedule ----
+// nst = ceil(lg / 3) stages (lg >= 4); forward stage s: radix r0 (s = 0) or 8, Ns = 1 (s = 0) or
+// r0 8^(s - 1); inverse stage s: radix 8 (s < nst - 1) or r0, Ns = 8^s.
+struct P2Axis {
+    int n, lg, nst, r0;
+};
+__host__ __device__ __forceinline__ P2Axis p2_axis(int lg) {
+    P2Axis a;
+    a.lg = lg;
+    a.n = 1 << lg;
+    a.nst = (lg + 2) / 3;
+    a.r0 = 1 << (lg - 3 * (a.nst - 1));
+    return a;
+}
+// The same schedule with the line length fixed when the kernel is compiled: every span, stride and
+// table offset of a stage is then a constant, and the swizzled addresses of a butterfly are one
+// per-thread base plus constant offsets.  Kernels take either type as their axis.
+template <int LG> struct P2AxisC {
+    static constexpr int lg = LG, n = 1 << LG, nst = (LG + 2) / 3, r0 = 1 << (LG - 3 * ((LG + 2) / 3 - 1));
+};
+template <class AX> struct P2IsC : std::false_type {};
+template <int LG> struct P2IsC<P2AxisC<LG>> : std::true_type {};
+// axis of a kernel compiled for line length 2^LG (LG = 0: any length, from the plan)
+template <int LG> struct P2Sel {
+    using type = P2AxisC<LG>;
+    static __host__ __device__ __forceinline__ type make(int) { return type{}; }
+};
+template <> struct P2Sel<0> {
+    using type = P2Axis;
+    static __host__ __device__ __forceinline__ type make(int lg) { return p2_axis(lg); }
+};
+
+template <class AX> __host__ __device__ __forceinline__ int p2_fns(const AX& a, int s) {
+    return s == 0 ? 1 : a.r0 << (3 * (s - 1));
+}
+__host__ __device__ __forceinline__ int p2_ins(int s) { return 1 << (3 * s); }
+template <class AX> __host__ __device__ __forceinline__ int p2_ir(const AX& a, int s) {
+    return s == a.nst - 1 ? a.r0 : 8;
+}
+// twiddle tables of one axis: forward stages 1..nst-1, then inverse stages 1..nst-1 (< 2 n entries)
+template <class AX> __host__ __device__ __forceinline__ int p2_off_f(const AX& a, int s) { return p2_fns(a, s) - a.r0; }
+template <class AX> __host__ __device__ __forceinline__ int p2_off_i(const AX& a, int s) {
+    return a.n - a.r0 + p2_ins(s) - 8;
+}
+
 __host__ __device__ __forceinline__ int p2_tab_len(int n) { return 2 * n; }
+
+// Stage twiddle tables of a power-of-two axis (n = 2^lg, lg >= 4) from its full table
+// tw[m] = exp(-2 pi i m / n): entry (r, k) of a stage of radix R and span Ns is tw[r k n / (Ns R)].
+// A gather of the same values, so the rounded tables the kernels use are those of the full table.
+inline std::vector<std::complex<double>> p2_stage_table(const std::vector<std::complex<double>>& tw, int lg) {
+    const P2Axis a = p2_axis(lg);
+    std::vector<std::complex<double>> t((size_t)p2_tab_len(a.n), std::complex<double>(0.0, 0.0));
+    for (int s = 1; s < a.nst; ++s) {
+        const int NsF = p2_fns(a, s), NsI = p2_ins(s), RI = p2_ir(a, s);
+        const int stepF = a.n / (NsF * 8), stepI = a.n / (NsI * RI);
+        for (int r = 1; r < 8; ++r)
+            for (int k = 0; k < NsF; ++k) t[(size_t)p2_off_f(a, s) + (r - 1) * NsF + k] = tw[(size_t)r * k * stepF];
+        for (int r = 1; r < RI; ++r)
+            for (int k = 0; k < NsI; ++k) t[(size_t)p2_off_i(a, s) + (r - 1) * NsI + k] = tw[(size_t)r * k * stepI];
+    }
+    return t;
+}
 
 // ---- shared-memory layout (pow2 kernel) ----
 // twx[2 nx] | twy[2 ny] | dpl[ny] | dml[ny] | cdp[8] | cdm[8] | work | gb[rmax / 2 nx] (complex)
@@ -81,10 +147,32 @@ cudaError_t row2_launch(const cudaLaunchConfig_t* lc, int D, int kind, const Dev
                         T* data_row, const T* h_row, T* qrow, T* gc2, const T* p0c);
 template <typename T> cudaError_t row2_set_attrs(int bytes);
 
-// launch k_persist2<T, adjoint> with `lc` (cooperative attributes set by the caller)
+// launch k_persist2<T, adjoint> with `lc` (cooperative attributes set by the caller); p2_kernel is
+// the kernel that p2_launch runs for a grid of 2^lgx x 2^lgy points and P.fixed_len = fixed_len
 template <typename T>
 cudaError_t p2_launch(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<T>& P, const PersistCfg& C,
                       unsigned* gbar);
-template <typename T> const void* p2_kernel(bool adjoint);
+template <typename T> const void* p2_kernel(bool adjoint, int lgx, int lgy, int fixed_len);
+
+// ---- kernels compiled for fixed lengths (float fields) ----
+// The 2-D persistent kernel for 256^2 and 512^2 grids, and the 3-D spectral and row kernels for
+// lines of 64, 128 and 256 points; a plan takes them unless it was created with PAT_P2SPEC=0
+// (DevPlan::fixed_len = 0), which runs the kernels for any length instead (for comparison).
+// lg of the fixed-size 2-D persistent kernel for a 2^lgx x 2^lgy grid, 0 if there is none
+inline int p2_sq_lg(int lgx, int lgy, int on) { return (on && lgx == lgy && (lgx == 8 || lgx == 9)) ? lgx : 0; }
+// lg of the fixed-length 3-D spectral or row kernel for lines of 2^lg points, 0 if there is none
+inline int p2_3d_lg(int lg, int on) { return (on && lg >= 6 && lg <= 8) ? lg : 0; }
+template <int LG>
+cudaError_t p2_launch_f32_sq(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<float>& P, const PersistCfg& C,
+                             unsigned* gbar);
+template <int LG> const void* p2_kernel_f32_sq(bool adjoint);
+template <int LG>
+cudaError_t spec2_launch_f32_3d(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P, int W, int lgW, int lax,
+                                int F);
+template <int LG> cudaError_t spec2_set_attrs_f32_3d(int bytes);
+template <int LG>
+cudaError_t row2_launch_f32_3d(const cudaLaunchConfig_t* lc, int kind, const DevPlan<float>& P, int R, int flag,
+                               float* data_row, const float* h_row, float* qrow, float* gc2, const float* p0c);
+template <int LG> cudaError_t row2_set_attrs_f32_3d(int bytes);
 
 }  // namespace pat

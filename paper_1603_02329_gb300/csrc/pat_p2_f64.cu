@@ -10,7 +10,7 @@ cudaError_t p2_launch<double>(bool adjoint, const cudaLaunchConfig_t* lc, const 
     return cudaLaunchKernelEx(lc, k_persist2<double, false>, P, C, gbar);
 }
 
-template <> const void* p2_kernel<double>(bool adjoint) {
+template <> const void* p2_kernel<double>(bool adjoint, int, int, int) {
     return adjoint ? (const void*)k_persist2<double, true> : (const void*)k_persist2<double, false>;
 }
 

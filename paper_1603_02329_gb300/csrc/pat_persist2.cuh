@@ -28,27 +28,6 @@
 
 namespace pat {
 
-// ---- fixed power-of-two Stockham schedule ----
-// nst = ceil(lg / 3) stages (lg >= 4); forward stage s: radix r0 (s = 0) or 8, Ns = 1 (s = 0) or
-// r0 8^(s - 1); inverse stage s: radix 8 (s < nst - 1) or r0, Ns = 8^s.
-struct P2Axis {
-    int n, lg, nst, r0;
-};
-__host__ __device__ __forceinline__ P2Axis p2_axis(int lg) {
-    P2Axis a;
-    a.lg = lg;
-    a.n = 1 << lg;
-    a.nst = (lg + 2) / 3;
-    a.r0 = 1 << (lg - 3 * (a.nst - 1));
-    return a;
-}
-__device__ __forceinline__ int p2_fns(const P2Axis& a, int s) { return s == 0 ? 1 : a.r0 << (3 * (s - 1)); }
-__device__ __forceinline__ int p2_ins(int s) { return 1 << (3 * s); }
-__device__ __forceinline__ int p2_ir(const P2Axis& a, int s) { return s == a.nst - 1 ? a.r0 : 8; }
-// twiddle tables of one axis: forward stages 1..nst-1, then inverse stages 1..nst-1 (< 2 n entries)
-__device__ __forceinline__ int p2_off_f(const P2Axis& a, int s) { return p2_fns(a, s) - a.r0; }
-__device__ __forceinline__ int p2_off_i(const P2Axis& a, int s) { return a.n - a.r0 + p2_ins(s) - 8; }
-
 __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
 // Start of line q in a line buffer whose fields hold 2^lgnl lines each.  Fields sit 64 bytes
 // beyond whole lines (p2_field_pad), so that the lane pairs of the fused stages, which touch the
@@ -59,31 +38,28 @@ template <typename T> __device__ __forceinline__ size_t lbase(int q, int n, int 
 }
 template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
 
-// stage tables from the full table tw[m] = exp(-2 pi i m / n): entry (r, k) of a stage of radix R
-// and span Ns is tw[r k n / (Ns R)] (a copy, no new rounding)
-template <typename T> __device__ void p2_build_tables(cplx<T>* tab, const cplx<T>* tw, const P2Axis& a) {
-    for (int s = 1; s < a.nst; ++s) {
-        const int NsF = p2_fns(a, s), NsI = p2_ins(s), RI = p2_ir(a, s);
-        const int stepF = a.n / (NsF * 8), stepI = a.n / (NsI * RI);
-        cplx<T>* tf = tab + p2_off_f(a, s);
-        cplx<T>* ti = tab + p2_off_i(a, s);
-        for (int t = threadIdx.x; t < 7 * NsF; t += blockDim.x) {
-            const int r = t / NsF + 1, k = t - (r - 1) * NsF;
-            tf[t] = tw[r * k * stepF];
-        }
-        for (int t = threadIdx.x; t < (RI - 1) * NsI; t += blockDim.x) {
-            const int r = t / NsI + 1, k = t - (r - 1) * NsI;
-            ti[t] = tw[r * k * stepI];
-        }
-    }
+// The swizzle is linear over XOR: swz(a ^ b) = swz(a) ^ swz(b).  Element j + r m of a butterfly
+// (j < m, m a power of two) is j ^ (r m), and an output b + r Ns of a Stockham store is b ^ (r Ns)
+// (disjoint bits), so their swizzled indices are the thread's swz(j) or swz(b) XOR a per-r term.
+// With the line length fixed at compile time (CM) that term is a constant; when r m is a multiple
+// of 16 it splits into a XOR of the low four bits and an added offset (swz(j) has no bit of r m),
+// which the loads take as an immediate.
+__device__ __forceinline__ int swz_xor(int sj, int rm) {
+    return (rm % 16 == 0) ? (sj ^ ((rm >> 3) & 15)) + rm : sj ^ swz(rm);
 }
 
 // butterfly j of a stage (span Ns, stride m = n / R): load elements j + r m of `src`, twiddle
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool CM = false>
 __device__ __forceinline__ void p2_load(cplx<T> (&v)[R], const cplx<T>* src, int j, int m, int Ns,
                                         const cplx<T>* tws) {
+    if constexpr (CM) {
+        const int sj = swz(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[swz(j + r * m)];
+        for (int r = 0; r < R; ++r) v[r] = src[swz_xor(sj, r * m)];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[swz(j + r * m)];
+    }
     if (Ns > 1) {
         const int k = j & (Ns - 1);
 #pragma unroll
@@ -93,28 +69,38 @@ __device__ __forceinline__ void p2_load(cplx<T> (&v)[R], const cplx<T>* src, int
         }
     }
 }
-template <typename T, int R>
+template <typename T, int R, bool CM = false>
 __device__ __forceinline__ void p2_store(cplx<T>* dst, int j, int Ns, const cplx<T> (&v)[R]) {
     const int k = j & (Ns - 1);
     const int b = (j - k) * R + k;
+    if constexpr (CM) {
+        // Ns >= 16: bits 0..3 of b are those of k, so swz(b) leaves the bits of r Ns clear
+        const int sb = swz(b);
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[swz(b + r * Ns)] = v[r];
+        for (int r = 0; r < R; ++r)
+            dst[Ns % 16 == 0 ? (sb ^ ((r * Ns >> 3) & 15)) + r * Ns : sb ^ swz(r * Ns)] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[swz(b + r * Ns)] = v[r];
+    }
 }
 
 // the middle stages 1 .. nst-2 (radix 8) over `nlines` lines, each followed by a CTA barrier
-template <typename T, bool INV>
-__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const P2Axis& ax, const cplx<T>* tab, int nlines, int lgnl,
+template <typename T, bool INV, class AX>
+__device__ cplx<T>* p2_mid(cplx<T>* a, cplx<T>* b, const AX& ax, const cplx<T>* tab, int nlines, int lgnl,
                           int lp = 0) {
+    constexpr bool CM = P2IsC<AX>::value;
     const int lgm = ax.lg - 3, m = 1 << lgm;
+#pragma unroll
     for (int s = 1; s + 1 < ax.nst; ++s) {
         const int Ns = INV ? p2_ins(s) : p2_fns(ax, s);
         const cplx<T>* tws = tab + (INV ? p2_off_i(ax, s) : p2_off_f(ax, s));
         for (int t = threadIdx.x; t < (nlines << lgm); t += blockDim.x) {
             const int line = t >> lgm, j = t & (m - 1);
             cplx<T> v[8];
-            p2_load<T, 8, INV>(v, a + lbase<T>(line, ax.n, lgnl, lp), j, m, Ns, tws);
+            p2_load<T, 8, INV, CM>(v, a + lbase<T>(line, ax.n, lgnl, lp), j, m, Ns, tws);
             dft<T, 8, INV>(v);
-            p2_store<T, 8>(b + lbase<T>(line, ax.n, lgnl, lp), j, Ns, v);
+            p2_store<T, 8, CM>(b + lbase<T>(line, ax.n, lgnl, lp), j, Ns, v);
         }
         __syncthreads();
         cplx<T>* tmp = a;
@@ -144,8 +130,8 @@ __device__ __forceinline__ void p2_row_stage(cplx<T>* S, cplx<T>* const* spec, i
 }
 
 // inverse x-stage 0 (radix 8, no twiddles) on the C2R packing of the staged half spectra
-template <typename T>
-__device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, int lgnp, const P2Axis& ax, int ldh) {
+template <typename T, class AX>
+__device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, int lgnp, const AX& ax, int ldh) {
     const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, half = n >> 1;
     for (int t = threadIdx.x; t < ((FI * np) << lgm); t += blockDim.x) {
         const int q = t >> lgm, j = t & (m - 1);
@@ -172,7 +158,7 @@ __device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, int lg
                                : mkc<T>(A[r].x + B[r].y, B[r].x - A[r].y);   // conj(A) + i conj(B)
         }
         dft<T, 8, true>(v);
-        p2_store<T, 8>(dst + lbase<T>(q, n, lgnp), j, 1, v);
+        p2_store<T, 8, P2IsC<AX>::value>(dst + lbase<T>(q, n, lgnp), j, 1, v);
     }
 }
 
@@ -211,10 +197,11 @@ __device__ __forceinline__ void p2_each(int p, int j, int m, int h, const cplx<T
 // of the positions (r = h H + k), where it runs pw(p, j, m, h, zi, oo); a second exchange gives
 // lane h every position of output field h, which it transforms and stores (FO = 1: both lanes
 // transform field 0 and each stores its half).  FI = 0: pw reads its inputs itself.
-template <typename T, int R, class PW>
-__device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax,
+template <typename T, int R, class AX, class PW>
+__device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const AX& ax,
                                             int np, int lgnp, int FI, int FO, bool fwd, PW&& pw) {
     constexpr int H = R / 2;
+    constexpr bool CM = P2IsC<AX>::value;
     const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
     const int total = (np << lgm) * 2;
@@ -225,7 +212,7 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
         const int p = u >> lgm, j = u & (m - 1);
         cplx<T> z[R];
         if (valid && FI > 0) {
-            p2_load<T, R, true>(z, src + lbase<T>((FI == 2 ? h : 0) * np + p, n, lgnp), j, m, m, twl);
+            p2_load<T, R, true, CM>(z, src + lbase<T>((FI == 2 ? h : 0) * np + p, n, lgnp), j, m, m, twl);
             dft<T, R, true>(z);
         }
         cplx<T> zi[2][H], oo[2][H];
@@ -253,7 +240,7 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
         dft<T, R, false>(w);
         cplx<T>* d = dst + lbase<T>((FO == 2 ? h : 0) * np + p, n, lgnp);
         if (FO == 2) {
-            p2_store<T, R>(d, j, 1, w);
+            p2_store<T, R, CM>(d, j, 1, w);
         } else {
 #pragma unroll
             for (int k = 0; k < H; ++k) d[swz(j * R + h * H + k)] = h ? w[H + k] : w[k];
@@ -263,9 +250,10 @@ __device__ __forceinline__ void p2_row_fuse(const cplx<T>* src, cplx<T>* dst, co
 
 // last forward x-stage (radix 8, Ns = n / 8) and R2C unpacking into the half spectra: unit u of a
 // line runs butterflies u and m - u (u = 0: 0 and m / 2), which hold every X[k] with its X[n - k]
-template <typename T>
-__device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, const P2Axis& ax,
+template <typename T, class AX>
+__device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, const AX& ax,
                            int FO, int np, int lgnp, int line0, int ldh) {
+    constexpr bool CM = P2IsC<AX>::value;
     const int n = ax.n, lgm = ax.lg - 3, m = 1 << lgm, lgh = lgm - 1, hm = m >> 1;
     const cplx<T>* twl = tab + p2_off_f(ax, ax.nst - 1);
     for (int t = threadIdx.x; t < ((FO * np) << lgh); t += blockDim.x) {
@@ -274,8 +262,8 @@ __device__ void p2_row_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
         const int j1 = u, j2 = (u == 0) ? hm : m - u;
         const cplx<T>* line = src + lbase<T>(q, n, lgnp);
         cplx<T> X1[8], X2[8];
-        p2_load<T, 8, false>(X1, line, j1, m, m, twl);
-        p2_load<T, 8, false>(X2, line, j2, m, m, twl);
+        p2_load<T, 8, false, CM>(X1, line, j1, m, m, twl);
+        p2_load<T, 8, false, CM>(X2, line, j2, m, m, twl);
         dft<T, 8, false>(X1);
         dft<T, 8, false>(X2);
         cplx<T>* a = spec[f] + (size_t)(line0 + 2 * p) * ldh;
@@ -344,8 +332,8 @@ __device__ __forceinline__ void p2_col_stage(cplx<T>* S, cplx<T>* const* spec, i
 }
 
 // forward y-stage 0 (radix R, no twiddles) on the staged columns
-template <typename T, int R>
-__device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const P2Axis& ay) {
+template <typename T, int R, class AX>
+__device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const AX& ay) {
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
@@ -354,7 +342,7 @@ __device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
         dft<T, R, false>(v);
-        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
+        p2_store<T, R, P2IsC<AX>::value>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
     }
 }
 
@@ -364,9 +352,10 @@ __device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW
 // each storing half).  The multipliers of the CTA's tile are resident: kapt = kappa / N, s0t /
 // s1t = |k|^(y-2) / N and |k|^(y-1) / N (Eq. Twelve's fractional Laplacians), [ky][c]; the shift
 // operators per column (cdp / cdm) and per row (dpl / dml).
-template <typename T>
+template <typename T, class AX>
 __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>* src, cplx<T>* dst,
-                                            const P2Axis& ay, int W, int lgW, int mode) {
+                                            const AX& ay, int W, int lgW, int mode) {
+    constexpr bool CM = P2IsC<AX>::value;
     const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
     const cplx<T>* twl = s.twy + p2_off_f(ay, ay.nst - 1);
@@ -378,7 +367,7 @@ __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>
         const int c = u & (W - 1), j = u >> lgW;
         cplx<T> z[8], o[8];
         if (valid) {
-            p2_load<T, 8, false>(z, src + lbase<T>((fi == 2 ? h : 0) * W + c, n, lgW), j, m, m, twl);
+            p2_load<T, 8, false, CM>(z, src + lbase<T>((fi == 2 ? h : 0) * W + c, n, lgW), j, m, m, twl);
             dft<T, 8, false>(z);
         }
         switch (mode) {
@@ -427,7 +416,7 @@ __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>
         dft<T, 8, true>(o);
         cplx<T>* d = dst + lbase<T>((fo == 2 ? h : 0) * W + c, n, lgW);
         if (fo == 2) {
-            p2_store<T, 8>(d, j, 1, o);
+            p2_store<T, 8, CM>(d, j, 1, o);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) d[swz(j * 8 + h * 4 + k)] = h ? o[4 + k] : o[k];
@@ -436,15 +425,15 @@ __device__ __forceinline__ void p2_col_fuse(const PersistSm<T>& s, const cplx<T>
 }
 
 // last inverse y-stage (radix R, Ns = n / R), stored to the spectra (valid columns only)
-template <typename T, int R>
+template <typename T, int R, class AX>
 __device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* tab, int FO, int W, int lgW,
-                           int kx0, int wv, const P2Axis& ay, int ldh) {
+                           int kx0, int wv, const AX& ay, int ldh) {
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ay, ay.nst - 1);
     for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
         cplx<T> v[R];
-        p2_load<T, R, true>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
+        p2_load<T, R, true, P2IsC<AX>::value>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
         dft<T, R, true>(v);
         if (c < wv) {
             cplx<T>* dst = spec[f] + kx0 + c;
@@ -455,8 +444,8 @@ __device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
 }
 
 // whole column phase of `mode` for columns [kx0, kx0 + W)
-template <typename T>
-__device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& P, const P2Axis& ay, int kx0, int W,
+template <typename T, class AX>
+__device__ __forceinline__ void p2_col(const PersistSm<T>& s, const DevPlan<T>& P, const AX& ay, int kx0, int W,
                                        int lgW, int mode) {
     const int fi = (mode == SPEC_GRAD) ? 1 : 2, fo = (mode == SPEC_GRADT) ? 1 : 2;
     cplx<T>* A = s.work;
@@ -556,10 +545,11 @@ template <bool ADJ> __device__ __forceinline__ P2Phase p2_phase(int k, int Nt, b
     return d;
 }
 
-template <typename T, bool ADJ>
+// LGX, LGY > 0: compiled for nx = 2^LGX, ny = 2^LGY (the launcher checks the plan); 0: any size
+template <typename T, bool ADJ, int LGX = 0, int LGY = 0>
 __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, unsigned* gbar) {
     PersistSm<T> s = p2_carve<T>(P, C);
-    const int nx = P.nx, ny = P.ny, b = blockIdx.x;
+    const int nx = LGX ? (1 << LGX) : P.nx, ny = LGY ? (1 << LGY) : P.ny, b = blockIdx.x;
     const unsigned G = gridDim.x;
     const int pair0 = b * C.ppc;
     const int npair = max(0, min(ny / 2 - pair0, C.ppc));
@@ -568,7 +558,8 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
     const int kx0 = b * C.W;
     const T dt = P.dt;
     const int Nt = P.Nt, Ns = P.sens.Ns;
-    const P2Axis axx = p2_axis(P.fx.lgn), axy = p2_axis(P.fy.lgn);
+    const auto axx = P2Sel<LGX>::make(P.fx.lgn);
+    const auto axy = P2Sel<LGY>::make(P.fy.lgn);
     unsigned kbar = 0;
     const TraceRef TR{P.trace, P.trace_k0, P.trace_nk};
     s.tr = TR;
@@ -578,8 +569,8 @@ __global__ void __launch_bounds__(256) k_persist2(DevPlan<T> P, PersistCfg C, un
     const int lgnp = (C.ppc == 1) ? 0 : (C.ppc == 2 ? 1 : (C.ppc == 4 ? 2 : 3));
 
     // ---- setup: stage twiddle tables, k-space tables of the tile, resident medium ----
-    p2_build_tables<T>(s.twx, P.twx, axx);
-    p2_build_tables<T>(s.twy, P.twy, axy);
+    stage16(s.twx, P.stw[0], (size_t)p2_tab_len(nx) * sizeof(cplx<T>));
+    stage16(s.twy, P.stw[1], (size_t)p2_tab_len(ny) * sizeof(cplx<T>));
     stage16(s.dpl, P.dp[1], (size_t)ny * sizeof(cplx<T>));
     stage16(s.dml, P.dm[1], (size_t)ny * sizeof(cplx<T>));
     stage_elems(s.ax, P.a[0], nx);

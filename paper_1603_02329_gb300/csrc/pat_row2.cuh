@@ -22,9 +22,10 @@ namespace pat {
 
 // Last inverse x-stage (radix R) of FI <= FIM fields, the pointwise step pw(p, j, m, z, o) with every
 // field of butterfly (p, j) in one thread, and -- when `fwd` -- forward x-stage 0 of FO <= FOM outputs.
-template <typename T, int R, int FIM, int FOM, class PW>
-__device__ __forceinline__ void r2_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const P2Axis& ax,
+template <typename T, int R, int FIM, int FOM, class AX, class PW>
+__device__ __forceinline__ void r2_fuse(const cplx<T>* src, cplx<T>* dst, const cplx<T>* tab, const AX& ax,
                                         int np, int lgnp, int FI, int FO, bool fwd, PW&& pw) {
+    constexpr bool CM = P2IsC<AX>::value;
     const int n = ax.n, lgm = ax.lg - Lg2<R>::v, m = 1 << lgm;
     const cplx<T>* twl = tab + p2_off_i(ax, ax.nst - 1);
     for (int t = threadIdx.x; t < (np << lgm); t += blockDim.x) {
@@ -33,7 +34,7 @@ __device__ __forceinline__ void r2_fuse(const cplx<T>* src, cplx<T>* dst, const 
 #pragma unroll
         for (int f = 0; f < FIM; ++f) {
             if (f < FI) {
-                p2_load<T, R, true>(z[f], src + lbase<T>(f * np + p, n, lgnp), j, m, m, twl);
+                p2_load<T, R, true, CM>(z[f], src + lbase<T>(f * np + p, n, lgnp), j, m, m, twl);
                 dft<T, R, true>(z[f]);
             }
         }
@@ -43,7 +44,7 @@ __device__ __forceinline__ void r2_fuse(const cplx<T>* src, cplx<T>* dst, const 
             for (int g = 0; g < FOM; ++g) {
                 if (g < FO) {
                     dft<T, R, false>(o[g]);
-                    p2_store<T, R>(dst + lbase<T>(g * np + p, n, lgnp), j, 1, o[g]);
+                    p2_store<T, R, CM>(dst + lbase<T>(g * np + p, n, lgnp), j, 1, o[g]);
                 }
             }
         }
@@ -72,11 +73,12 @@ __device__ __forceinline__ void r2_each(int p, int j, int m, const cplx<T> (&z)[
     }
 }
 
-template <typename T, int D, int KIND>
+// LG > 0: compiled for x-lines of 2^LG points (the launcher checks the plan); 0: any power of two
+template <typename T, int D, int KIND, int LG = 0>
 __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* data_row, const T* h_row, T* qrow,
                                               T* gc2, const T* p0c) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nx = P.nx, np = R >> 1, line0 = blockIdx.x * R;
+    const int nx = LG ? (1 << LG) : P.nx, np = R >> 1, line0 = blockIdx.x * R;
     const int lgnp = (np == 1) ? 0 : (np == 2 ? 1 : (np == 4 ? 2 : (np == 8 ? 3 : 4)));
     const Row2Layout<T> Lo = row2_layout<T>(D, nx, P.ldh, R);
     cplx<T>* tab = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -87,12 +89,12 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     T* pmlx = res + Lo.res;
     T* pmlr = pmlx + nx;
     auto row = [&](int k) { return res + (size_t)k * R * nx; };
-    const P2Axis ax = p2_axis(P.fx.lgn);
+    const auto ax = P2Sel<LG>::make(P.fx.lgn);
     const T dt = P.dt;
     const bool lossy = P.lossy != 0;
 
     // ---- prologue: tables and the medium (constants of the plan) ----
-    p2_build_tables<T>(tab, P.twx, ax);
+    stage16(tab, P.stw[0], (size_t)p2_tab_len(nx) * sizeof(cplx<T>));
     int FI = D, FO = D;
     bool fwd = true, gath = false, scat = false;
     const T* const* pml_tab = P.a;

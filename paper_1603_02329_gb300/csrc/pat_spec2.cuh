@@ -19,8 +19,8 @@
 namespace pat {
 
 // stage 0 (radix R, no twiddles; forward or inverse) from the staged tile S[f][i][c]
-template <typename T, int R, bool INV>
-__device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const P2Axis& ay) {
+template <typename T, int R, bool INV, class AX>
+__device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const AX& ay) {
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
@@ -29,19 +29,20 @@ __device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, co
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
         dft<T, R, INV>(v);
-        p2_store<T, R>(dst + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, 1, v);
+        p2_store<T, R, P2IsC<AX>::value>(dst + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, 1, v);
     }
 }
 
 // last stage (radix R, span n / R; forward or inverse) and the store of valid columns
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, class AX>
 __device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* twl, int FO, int W, int lgW,
-                       int wv, const P2Axis& ay, size_t base, size_t es) {
+                       int wv, const AX& ay, size_t base, size_t es) {
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FO * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
         cplx<T> v[R];
-        p2_load<T, R, INV>(v, src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m, twl);
+        p2_load<T, R, INV, P2IsC<AX>::value>(v, src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m,
+                                             twl);
         dft<T, R, INV>(v);
         if (c < wv) {
             cplx<T>* dst = spec[f] + base + c;
@@ -55,9 +56,10 @@ __device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* 
 // Symbols (Sec. II.A, Eq. (state)): kappa = sinc(c_ref |k| dt / 2), D+-_xi = i k_xi e^{+-i k_xi h/2},
 // |k|^(y-2), |k|^(y-1); all scaled by 1/N.  Field f's shift factor: f = 0 -> x (column kx),
 // f = 1 -> y (the CTA's outer index in a z pass, the line index in a y pass), f = 2 -> z (line).
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, class AX>
 __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, const cplx<T>* twl, int W, int lgW,
-                        const P2Axis& ay, int lax, int kx0, int outer) {
+                        const AX& ay, int lax, int kx0, int outer) {
+    constexpr bool CM = P2IsC<AX>::value;
     constexpr int FI = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
     constexpr int FO = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
     constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
@@ -68,7 +70,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
         cplx<T> z[FI][8];
 #pragma unroll
         for (int f = 0; f < FI; ++f) {
-            p2_load<T, 8, false>(z[f], src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m, twl);
+            p2_load<T, 8, false, CM>(z[f], src + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, m, m, twl);
             dft<T, 8, false>(z[f]);
         }
         const int kx = min(kx0 + c, P.nxh - 1);
@@ -119,18 +121,19 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
 #pragma unroll
         for (int g = 0; g < FO; ++g) {
             dft<T, 8, true>(o[g]);
-            p2_store<T, 8>(dst + lbase<T>(g * W + c, n, lgW, spec2_line_pad<T>()), j, 1, o[g]);
+            p2_store<T, 8, CM>(dst + lbase<T>(g * W + c, n, lgW, spec2_line_pad<T>()), j, 1, o[g]);
         }
     }
 }
 
-template <typename T, int D, int MODE>
+// LG > 0: compiled for lines of 2^LG points (the launcher checks the plan); 0: any power of two
+template <typename T, int D, int MODE, int LG = 0>
 __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int lax, int F) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool MUL = (MODE != SPEC_PLAIN_FWD && MODE != SPEC_PLAIN_INV);
     const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
     const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
-    const P2Axis ay = p2_axis((lax == 1) ? P.fy.lgn : P.fz.lgn);
+    const auto ay = P2Sel<LG>::make((lax == 1) ? P.fy.lgn : P.fz.lgn);
     const int L = ay.n;
     cplx<T>* tab = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* A = tab + p2_tab_len(L);
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     const size_t base = (lax == 1) ? (size_t)outer * P.ny * P.ldh + kx0 : (size_t)outer * P.ldh + kx0;
 
     // prologue: stage twiddle tables (plan constants, never written by the preceding kernel)
-    p2_build_tables<T>(tab, (lax == 1) ? P.twy : P.twz, ay);
+    stage16(tab, P.stw[lax], (size_t)p2_tab_len(L) * sizeof(cplx<T>));
     pdl_trigger();
     pdl_wait();
     // stage the tile's columns of every input field: B[f][i][c]; tiles reach into the zeroed
@@ -152,9 +155,9 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
         cplx<T>* d = B + (size_t)f * L * W;
         if (cb >= 16) {
             constexpr int EPC = 16 / (int)sizeof(cplx<T>);
-            const int cpr = cb / 16;
+            const int cpr = cb / 16, lgc = lgW - (EPC == 2 ? 1 : 0);   // 16-byte pieces per row: 2^lgc
             for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
-                const int i = t / cpr, ch = t - i * cpr;
+                const int i = t >> lgc, ch = t & (cpr - 1);
                 cp_async<16>(d + (size_t)i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
             }
         } else {

@@ -108,6 +108,10 @@ template <typename T> struct Plan : public PlanBase {
         P.Nt = h.Nt;
         P.bar_extra = 0;
         P.bar_limit_ns = 2000000000ull;
+        {
+            const char* ef = std::getenv("PAT_P2SPEC");
+            P.fixed_len = (ef && std::atoi(ef) == 0) ? 0 : 1;
+        }
         const size_t N = (size_t)h.N;
         const size_t Nh = (size_t)h.nz * h.ny * h.ldh;
 #define CHK(x) \
@@ -144,6 +148,14 @@ template <typename T> struct Plan : public PlanBase {
         CHK(P.twx = upload_c(h.tw[0], &st));
         CHK(P.twy = upload_c(h.tw[1], &st));
         CHK(P.twz = upload_c(h.tw[2], &st));
+        {
+            const FftAxis* fa[3] = {&h.fx, &h.fy, &h.fz};
+            for (int a = 0; a < 3; ++a) {
+                P.stw[a] = nullptr;
+                if (a < D && fa[a]->pow2 && fa[a]->lgn >= 4 && fa[a]->lgn <= 11)
+                    CHK(P.stw[a] = upload_c(p2_stage_table(h.tw[a], fa[a]->lgn), &st));
+            }
+        }
         for (int a = 0; a < 3; ++a) {
             if (a < D) {
                 CHK(P.u[a] = dalloc<T>(N, &st));
@@ -332,8 +344,8 @@ template <typename T> struct Plan : public PlanBase {
         const char* ep2 = std::getenv("PAT_P2");
         const bool p2 = !(ep2 && std::atoi(ep2) == 0) && h.fx.pow2 && h.fy.pow2 && h.fx.lgn >= 4 &&
                         h.fy.lgn >= 4 && h.fx.lgn <= 11 && h.fy.lgn <= 11;
-        const void* kf = p2 ? p2_kernel<T>(false) : (const void*)k_persist<T, false>;
-        const void* ka = p2 ? p2_kernel<T>(true) : (const void*)k_persist<T, true>;
+        const void* kf = p2 ? p2_kernel<T>(false, h.fx.lgn, h.fy.lgn, P.fixed_len) : (const void*)k_persist<T, false>;
+        const void* ka = p2 ? p2_kernel<T>(true, h.fx.lgn, h.fy.lgn, P.fixed_len) : (const void*)k_persist<T, true>;
         cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) {

@@ -324,6 +324,40 @@ def test_persistent_barrier_timeout_is_reported_and_recovers(dev, monkeypatch, p
     assert L.pat_plan_set_fault(op._plan, 2, 1.0) != 0      # invalid arguments are rejected
 
 
+# Kernels compiled for fixed line lengths (float fields): the 2-D persistent kernel for 256^2 and
+# 512^2 grids, the 3-D spectral kernels for y / z lines and the 3-D row kernels for x-lines of 64,
+# 128 and 256 points.  Their arithmetic is that of the kernels for any length (only the index
+# arithmetic is resolved at compile time), which PAT_P2SPEC=0 selects: both must match the
+# oracle, and each other.
+FIXED_CASES = [
+    ("2d_256x256_lossy", "2d", dict(shape=(256, 256), pml=12, Nt=80, n_sensors=32)),
+    ("2d_512x512_lossless", "2d", dict(shape=(512, 512), pml=20, Nt=40, n_sensors=32, alpha0=0.0)),
+    ("3d_16x128x64_lossy", "3d", dict(shape=(16, 128, 64), pml=3, Nt=24)),        # y 128, x 64
+    ("3d_16x256x128_lossy", "3d", dict(shape=(16, 256, 128), pml=3, Nt=20)),      # y 256, x 128
+    ("3d_256x16x256_lossless", "3d", dict(shape=(256, 16, 256), pml=3, Nt=16, alpha0=0.0)),   # z 256, x 256
+]
+
+
+@pytest.mark.parametrize("name,kind,kw", FIXED_CASES, ids=[c[0] for c in FIXED_CASES])
+def test_fixed_length_kernels_match_generic_and_oracle(dev, monkeypatch, name, kind, kw):
+    pb = synth.small_lossy_3d(**kw) if kind == "3d" else synth.small_lossy_2d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(31).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_P2SPEC", flag)
+        op = _gpu_op(pb, "f32", dev)
+        assert op.info.path == (2 if kind == "2d" else 0)
+        d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+        g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+        assert rel(d, d_ref) <= TOL32, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= TOL32, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
+
+
 # Power-of-two y (and z) axes take the register-fused spectral kernel of the per-phase path
 # (k_spec2); PAT_SPEC2=0 selects the generic one.  3-D grids (always the per-phase path) and a
 # 2-D grid forced onto it; radix schedules 16 = 2.8, 32 = 4.8, 64 = 8.8, 128 = 2.8.8.

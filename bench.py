@@ -501,6 +501,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
+                          layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
                           parallelism=f"replicas x{world}",
                           path={0: "CUDA graph of per-phase kernels", 1: "persistent kernel per solve",
                                 2: "persistent kernel per solve, register-fused power-of-two transforms"}[int(op.info.path)]),

@@ -111,14 +111,21 @@ cudaError_t spec2_launch(const cudaLaunchConfig_t* lc, int D, int mode, const De
 template <typename T> cudaError_t spec2_set_attrs(int bytes);
 // k_spec2's lanes step across the tile's lines: every line is followed by 16 bytes of padding
 template <typename T> __host__ __device__ __forceinline__ int spec2_line_pad() { return 16 / (int)sizeof(cplx<T>); }
-// shared memory of k_spec2: stage twiddle tables [2 L] | A | B, each of fmax W padded lines (+ 2
-// field pads)
-template <typename T> __host__ __device__ size_t spec2_buf_elems(int D, int L, int W) {
-    const int fmax = D > 2 ? D : 2;
-    return (size_t)fmax * W * (L + spec2_line_pad<T>()) + 2 * (size_t)p2_field_pad<T>();
+// fields a k_spec2 launch holds at once: max(fields in, fields out)
+__host__ __device__ __forceinline__ int spec2_nf(int D, int mode, int F) {
+    if (mode == SPEC_PLAIN_FWD || mode == SPEC_PLAIN_INV) return F > 1 ? F : 1;
+    return mode == SPEC_ABS ? 2 : D;
 }
-template <typename T> size_t spec2_smem_bytes(int D, int L, int W) {
-    return ((size_t)p2_tab_len(L) + 2 * spec2_buf_elems<T>(D, L, W)) * sizeof(cplx<T>);
+// shared memory of k_spec2: stage twiddle tables [2 L] | the line axis' k [L] (real) and shift
+// operator [L] (complex) | A | B, each of nf W padded lines (+ 2 field pads)
+template <typename T> __host__ __device__ size_t spec2_buf_elems(int nf, int L, int W) {
+    return (size_t)nf * W * (L + spec2_line_pad<T>()) + 2 * (size_t)p2_field_pad<T>();
+}
+template <typename T> __host__ __device__ size_t spec2_pre_elems(int L) {
+    return (size_t)p2_tab_len(L) + (size_t)L + ((size_t)L * sizeof(T) + sizeof(cplx<T>) - 1) / sizeof(cplx<T>);
+}
+template <typename T> size_t spec2_smem_bytes(int nf, int L, int W) {
+    return (spec2_pre_elems<T>(L) + 2 * spec2_buf_elems<T>(nf, L, W)) * sizeof(cplx<T>);
 }
 
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)

@@ -11,7 +11,8 @@
 //   * the last stage stores straight to the spectra in natural order;
 //   * lines are XOR-swizzled and 16 bytes apart beyond their length (lanes step across the tile's
 //     lines), fields another 64 bytes apart, twiddles per stage.
-// A tile is W columns x F fields (W <= 8: ceil((nx/2 + 1) / W) W must not pass the padded row ldh).
+// A tile is W columns x F fields (W <= 8: ceil((nx/2 + 1) / W) W must not pass the padded row ldh);
+// shared memory holds max(fields in, fields out) of them (spec2_nf), sized per launch.
 #pragma once
 
 #include "pat_persist2.cuh"
@@ -57,14 +58,13 @@ __device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* 
 // |k|^(y-2), |k|^(y-1); all scaled by 1/N.  Field f's shift factor: f = 0 -> x (column kx),
 // f = 1 -> y (the CTA's outer index in a z pass, the line index in a y pass), f = 2 -> z (line).
 template <typename T, int D, int MODE, class AX>
-__device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, const cplx<T>* twl, int W, int lgW,
-                        const AX& ay, int lax, int kx0, int outer) {
+__device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, const cplx<T>* twl, const T* kl_s,
+                        const cplx<T>* ml_s, int W, int lgW, const AX& ay, int lax, int kx0, int outer) {
     constexpr bool CM = P2IsC<AX>::value;
     constexpr int FI = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
     constexpr int FO = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
     constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
     const int n = ay.n, lgm = ay.lg - 3, m = 1 << lgm;
-    const int la = lax;   // axis index of the line
     for (int t = threadIdx.x; t < (W << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = t >> lgW;
         cplx<T> z[FI][8];
@@ -88,7 +88,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int i = j + r * m;
-            const T kl = P.kv[la][i];
+            const T kl = kl_s[i];
             const T k2 = ckx2 + kl * kl + ko2;
             if constexpr (MODE == SPEC_ABS) {
                 const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
@@ -98,7 +98,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
             } else {
                 const T kap = sinc_sq(P.kap_a * P.kap_a * k2) * P.invN;
                 const T sg = (MODE == SPEC_DIVT || MODE == SPEC_GRADT) ? -kap : kap;
-                const cplx<T> ml = plus ? P.dp[la][i] : P.dm[la][i];
+                const cplx<T> ml = ml_s[i];
                 cplx<T> mf[3];
                 mf[0] = mx;
                 mf[1] = (lax == 2) ? mo : ml;
@@ -136,8 +136,10 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     const auto ay = P2Sel<LG>::make((lax == 1) ? P.fy.lgn : P.fz.lgn);
     const int L = ay.n;
     cplx<T>* tab = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* A = tab + p2_tab_len(L);
-    cplx<T>* B = A + spec2_buf_elems<T>(D, L, W);
+    cplx<T>* ml_s = tab + p2_tab_len(L);
+    T* kl_s = reinterpret_cast<T*>(ml_s + L);
+    cplx<T>* A = tab + spec2_pre_elems<T>(L);
+    cplx<T>* B = A + spec2_buf_elems<T>(spec2_nf(D, MODE, F), L, W);
     const int kx0 = blockIdx.x * W, outer = blockIdx.y;
     const int wv = min(W, P.nxh - kx0);
     const size_t es = (lax == 1) ? (size_t)P.ldh : (size_t)P.ny * P.ldh;
@@ -145,6 +147,12 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
 
     // prologue: stage twiddle tables (plan constants, never written by the preceding kernel)
     stage16(tab, P.stw[lax], (size_t)p2_tab_len(L) * sizeof(cplx<T>));
+    if constexpr (MUL) {
+        // the line axis' wavenumbers and its shift operator (D+ for GRAD / DIVT, D- otherwise)
+        constexpr bool plus = (MODE == SPEC_GRAD || MODE == SPEC_DIVT);
+        stage_elems(kl_s, P.kv[lax], L);
+        if constexpr (MODE != SPEC_ABS) stage16(ml_s, plus ? P.dp[lax] : P.dm[lax], (size_t)L * sizeof(cplx<T>));
+    }
     pdl_trigger();
     pdl_wait();
     // stage the tile's columns of every input field: B[f][i][c]; tiles reach into the zeroed
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
             s2_out<T, 8, false>(a, P.spec, tab + p2_off_f(ay, ay.nst - 1), fout, W, lgW, wv, ay, base, es);
         } else {
             cplx<T>* b = (a == A) ? B : A;
-            s2_fuse<T, D, MODE>(P, a, b, tab + p2_off_f(ay, ay.nst - 1), W, lgW, ay, lax, kx0, outer);
+            s2_fuse<T, D, MODE>(P, a, b, tab + p2_off_f(ay, ay.nst - 1), kl_s, ml_s, W, lgW, ay, lax, kx0, outer);
             __syncthreads();
             cplx<T>* r = p2_mid<T, true>(b, a, ay, tab, fout * W, lgW, spec2_line_pad<T>());
             with_radix(ay.r0, [&](auto RC) {

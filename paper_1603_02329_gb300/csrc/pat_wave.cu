@@ -556,7 +556,7 @@ template <typename T> struct Plan : public PlanBase {
         }
     }
     size_t spec_bytes(int D, int L, int w) const {
-        return use_spec2 ? spec2_smem_bytes<T>(D, L, w) : spec_smem_bytes<T>(D, L, w);
+        return use_spec2 ? spec2_smem_bytes<T>(std::max(D, 2), L, w) : spec_smem_bytes<T>(D, L, w);
     }
     // a spectral tile of w columns stays inside the padded rows of the half spectra
     bool tile_fits(int w) const { return (size_t)((H.nxh + w - 1) / w) * w <= (size_t)H.ldh; }
@@ -594,7 +594,8 @@ template <typename T> struct Plan : public PlanBase {
             cudaLaunchConfig_t lc = {};
             lc.gridDim = dim3(tiles, outer);
             lc.blockDim = dim3(256);
-            lc.dynamicSmemBytes = spec_smem;
+            // shared memory for the fields this launch holds (at most spec_smem)
+            lc.dynamicSmemBytes = spec2_smem_bytes<T>(spec2_nf(D, MODE, F), lax == 1 ? H.ny : H.nz, cfg.col_w);
             lc.stream = s;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

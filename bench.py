@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--mg-iters", type=int, default=20)
     ap.add_argument("--batch", action="store_true",
                     help="also time 8 uneven 2-D instances as one batched launch vs one at a time")
+    ap.add_argument("--trace", type=int, default=0,
+                    help="persistent path: after the timed steps, record the phase timeline of N grid barriers "
+                         "in the middle of one forward solve (pat_plan_set_trace) and report its medians")
     ap.add_argument("--c2grad", type=int, default=0,
                     help="also time the checkpointed c0^2 gradient with this checkpoint interval")
     return ap.parse_args()
@@ -109,12 +112,12 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from
 # ncu captures of the same command with the time axis cut to Nt = 20 and Nt = 40: the two agree
-# (forward 8.27 MB, adjoint 6.66 MB; the state stays in shared memory, so the traffic is the
-# set-up loads of the medium and tables), so the figure is taken as the full-length launch's.
-# Valid for the kernel version the captures were taken of.
+# (forward 8.26 / 8.20 MB, adjoint 6.64 / 6.64 MB; the state stays in shared memory, so the traffic
+# is the set-up loads of the medium and tables), so the figure is taken as the full-length launch's.
+# Valid for the kernel version the captures were taken of (the 512^2 fixed-size k_persist2).
 MEASURED_TRAFFIC = {
-    ("vessel2d_512", "k_persist2_adj"): 6.66e6,
-    ("vessel2d_512", "k_persist2_fwd"): 8.27e6,
+    ("vessel2d_512", "k_persist2_adj"): 6.64e6,
+    ("vessel2d_512", "k_persist2_fwd"): 8.23e6,
 }
 
 
@@ -267,6 +270,39 @@ def batch_vs_sequential(dev):
             "sequential_s": t_seq, "batched_s": t_bat, "sequential_gpts": units / t_seq / 1e9,
             "batched_gpts": units / t_bat / 1e9, "speedup": t_seq / t_bat,
             "note": "best of 3 after one untimed run; a batch runs every instance on the per-phase path"}
+
+
+def phase_trace(op, x, data, stream, nk):
+    """Timeline of nk grid barriers in the middle of one forward solve of the persistent kernel:
+    per barrier, the median over CTAs of the wait (entry to exit) and of the next phase's time to
+    each of its sub-phase marks and to the next barrier, in microseconds."""
+    import torch
+
+    nph = op.Nt * (6 if op.lossy else 4)
+    k0 = max(0, nph // 2 - nk // 2)
+    op.set_trace(k0, nk)
+    op.forward(x, out=data, stream=stream)
+    torch.cuda.synchronize()
+    tr = op.read_trace()
+    op.set_trace(0, 0)
+    if tr is None:
+        return None
+    tr = tr.astype(np.int64)
+    ent, ext = tr[:, :, 0], tr[:, :, 1]
+    rows = []
+    for k in range(nk - 1):
+        nxt = ent[:, k + 1]
+        marks = []
+        for j in range(6):
+            m = tr[:, k, 2 + j]
+            ok = (m > 0) & (m >= ext[:, k]) & (m <= nxt)
+            marks.append(round(float(np.median(m[ok] - ext[ok, k])) / 1e3, 3) if ok.any() else None)
+        rows.append({"barrier": int(k0 + k), "wait_us": round(float(np.median(ext[:, k] - ent[:, k])) / 1e3, 3),
+                     "phase_us": round(float(np.median(nxt - ext[:, k])) / 1e3, 3), "marks_us": marks})
+    return {"first_barrier": int(k0), "ctas": int(tr.shape[0]), "barriers": rows,
+            "note": "marks: time from the barrier exit to sub-phase marks 0..5 of the next phase "
+                    "(row phase: staged, inverse stage 0, inverse middle, fused, forward middle, stored; "
+                    "column phase: staged, stage 0, middle, fused, inverse middle, stored)"}
 
 
 def c2_gradient_timing(op, pb, K, dev, dtype):
@@ -488,7 +524,10 @@ def main():
                 "traffic": measured_traffic(args.workload, name) if not args.nt else None,
                 "kernel": dom, "kernel_ms": ms, "algorithmic_bytes": b,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                "note": "working set is L2-resident (about 15 MB < 129 MB L2); the fraction is effective bandwidth"}
+                "note": ("one persistent launch per solve keeps the state in shared memory (DRAM traffic: "
+                         "the set-up loads); the fraction is effective bandwidth of the algorithmic bytes"
+                         if name.startswith("k_persist") else
+                         "algorithmic bytes of this kernel's operands (read and written once) per launch")}
     # whole-step roofline by the per-point-step algorithmic bytes (state once + medium once)
     B_pt = (2 * (2 * len(pb.shape) + 1) + (4 if op.lossy else 2)) * w
     step_roof = {"bytes_per_pt_step": B_pt, "achieved_gbs": value * 1e9 * B_pt / 1e9 / world,
@@ -515,6 +554,8 @@ def main():
         out["batch"] = batch_vs_sequential(dev)
     if args.c2grad > 0 and rank == 0:
         out["c2_gradient"] = c2_gradient_timing(op, pb, args.c2grad, dev, dtype)
+    if args.trace > 0 and rank == 0 and persistent:
+        out["phase_trace"] = phase_trace(op, x, data, stream, args.trace)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

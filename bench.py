@@ -294,7 +294,7 @@ def phase_trace(op, x, data, stream, nk):
         nxt = ent[:, k + 1]
         marks = []
         for j in range(6):
-            m = tr[:, k, 2 + j]
+            m = tr[:, k + 1, 2 + j]    # a phase's marks share the slot of the barrier that ends it
             ok = (m > 0) & (m >= ext[:, k]) & (m <= nxt)
             marks.append(round(float(np.median(m[ok] - ext[ok, k])) / 1e3, 3) if ok.any() else None)
         rows.append({"barrier": int(k0 + k), "wait_us": round(float(np.median(ext[:, k] - ent[:, k])) / 1e3, 3),

@@ -337,10 +337,11 @@ __device__ void p2_col_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
-        const cplx<T>* src = S + (size_t)f * n * W + c;
+        const cplx<T>* src = S + (f * n + j) * W + c;   // staged columns [f][ky][c], ky = j + r m
+        const int step = m * W;
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
+        for (int r = 0; r < R; ++r) v[r] = src[r * step];
         dft<T, R, false>(v);
         p2_store<T, R, P2IsC<AX>::value>(dst + lbase<T>(f * W + c, n, lgW), j, 1, v);
     }
@@ -436,9 +437,13 @@ __device__ void p2_col_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<
         p2_load<T, R, true, P2IsC<AX>::value>(v, src + lbase<T>(f * W + c, n, lgW), j, m, m, twl);
         dft<T, R, true>(v);
         if (c < wv) {
-            cplx<T>* dst = spec[f] + kx0 + c;
+            cplx<T>* dst = spec[f] + kx0 + c + (size_t)j * ldh;
+            const size_t mld = (size_t)m * ldh;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(size_t)(j + r * m) * ldh] = v[r];
+            for (int r = 0; r < R; ++r) {
+                *dst = v[r];
+                dst += mld;
+            }
         }
     }
 }

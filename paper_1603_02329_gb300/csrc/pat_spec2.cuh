@@ -25,10 +25,11 @@ __device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, co
     const int n = ay.n, lgm = ay.lg - Lg2<R>::v, m = 1 << lgm;
     for (int t = threadIdx.x; t < ((FI * W) << lgm); t += blockDim.x) {
         const int c = t & (W - 1), j = (t >> lgW) & (m - 1), f = t >> (lgW + lgm);
-        const cplx<T>* src = S + (size_t)f * n * W + c;
+        const cplx<T>* src = S + (f * n + j) * W + c;   // staged tile [f][i][c], i = j + r m
+        const int step = m * W;
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(size_t)(j + r * m) * W];
+        for (int r = 0; r < R; ++r) v[r] = src[r * step];
         dft<T, R, INV>(v);
         p2_store<T, R, P2IsC<AX>::value>(dst + lbase<T>(f * W + c, n, lgW, spec2_line_pad<T>()), j, 1, v);
     }
@@ -46,9 +47,13 @@ __device__ void s2_out(const cplx<T>* src, cplx<T>* const* spec, const cplx<T>* 
                                              twl);
         dft<T, R, INV>(v);
         if (c < wv) {
-            cplx<T>* dst = spec[f] + base + c;
+            cplx<T>* dst = spec[f] + base + c + (size_t)j * es;
+            const size_t mes = (size_t)m * es;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(size_t)(j + r * m) * es] = v[r];
+            for (int r = 0; r < R; ++r) {
+                *dst = v[r];
+                dst += mes;
+            }
         }
     }
 }

@@ -207,6 +207,63 @@ def test_vessel_512_full_size_prefix_and_dot(dev):
     assert np.isfinite(d).all() and np.abs(d).max() > 0
 
 
+def test_tube_128_full_size_prefix_and_dot(dev):
+    # 128^3 heterogeneous absorbing medium, Nt = 1000, 64 x 64 sensors: the launch configuration the
+    # benchmark times (per-phase graph, tuned layout, the kernels compiled for 128-point lines).
+    # Prefix of K samples vs the oracle (causality), adjoint of a residual supported on that prefix
+    # vs the oracle, and the dot identity over all 1000 samples.  The tubes start 6 px beyond the
+    # sensor plane (about 3.3 steps per px at CFL 0.3), so K = 40 holds arrived signal.
+    pb = synth.tube_phantom_3d(seed=3, n=128, pml=10, Nt=1000, sensors=64)
+    K = 40
+    ref = Operator.from_problem(pb, Nt=K)
+    op = _gpu_op(pb, "f32", dev)
+    assert op.info.path == 0
+    d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+    assert d.shape == (1000, 64 * 64)
+    d_ref = ref.forward(pb.p0)
+    assert np.abs(d_ref[K - 10:]).max() > 1e-2 * np.abs(pb.p0).max()
+    assert rel(d[:K], d_ref) <= TOL32
+    rng = np.random.default_rng(13)
+    h = np.zeros((pb.Nt, op.Ns))
+    h[:K] = rng.standard_normal((K, op.Ns))
+    g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+    assert rel(g, ref.adjoint(h[:K])) <= TOL32
+    x = _t(rng.standard_normal(pb.shape), "f32", dev)
+    hh = _t(rng.standard_normal((pb.Nt, op.Ns)), "f32", dev)
+    Hx = op.forward(x).double()
+    HTh = op.adjoint(hh).double()
+    lhs = torch.sum(Hx * hh.double()).item()
+    rhs = torch.sum(x.double() * HTh).item()
+    assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * hh.double().norm().item()
+
+
+def test_tube_256_full_size_adjoint_prefix_and_dot(dev):
+    # 256^3, Nt = 1500, 128 x 128 sensors: the largest benchmark configuration (about 2.5 GB of
+    # device state, the kernels compiled for 256-point lines).  The oracle at this size manages a
+    # few steps: the adjoint of a residual supported on the first K = 3 samples (the adjoint wave
+    # spreads from the sensor plane for 3 steps) vs the oracle, and the dot identity over all 1500
+    # samples.
+    pb = synth.tube_phantom_3d(seed=3, n=256, pml=20, Nt=1500, sensors=128)
+    K = 3
+    ref = Operator.from_problem(pb, Nt=K)
+    op = _gpu_op(pb, "f32", dev)
+    assert op.info.path == 0
+    rng = np.random.default_rng(14)
+    h = np.zeros((pb.Nt, op.Ns))
+    h[:K] = rng.standard_normal((K, op.Ns))
+    g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+    g_ref = ref.adjoint(h[:K])
+    assert np.abs(g_ref).max() > 0
+    assert rel(g, g_ref) <= TOL32
+    x = _t(rng.standard_normal(pb.shape), "f32", dev)
+    hh = _t(rng.standard_normal((pb.Nt, op.Ns)), "f32", dev)
+    Hx = op.forward(x).double()
+    HTh = op.adjoint(hh).double()
+    lhs = torch.sum(Hx * hh.double()).item()
+    rhs = torch.sum(x.double() * HTh).item()
+    assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * hh.double().norm().item()
+
+
 def test_both_2d_paths_agree_with_oracle(dev, monkeypatch):
     # 2-D plans use the persistent single-kernel path when the per-CTA state fits in shared
     # memory; PAT_PERSIST=0 forces the per-phase CUDA-graph path.  Both must match the oracle.

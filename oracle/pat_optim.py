@@ -46,6 +46,17 @@ O11 Weight of the coarse data term (Eq. (Fourteen) writes the coarse objective w
     coherence) and L_c use the same w.  On a 128^2 line-array case (40 dB noise), MG-FISTA with
     w = 1 gains a few iterations at the start only; with w = 1/2 it reaches in 3 iterations the RE
     that FISTA reaches in 10.
+O12 More than two levels (the paper states Alg. 3 for two grids; Sec. V.E).  A coarse level l >= 1
+    minimises phi_l = w_l/2 ||H_l x - p_l||^2 + lambda J_rho(x) + <v_l, x> on {x >= b_l} by the
+    projected FISTA of O7, and when a level l + 1 exists, an iteration k > 1 of it takes a
+    recursive direction under the test of Sec. V.D applied to phi_l (its own y~, K_r, K_d):
+    x_{l+1,0} = R y, v_{l+1} = R grad phi_l(y) - grad(w_{l+1}/2 ||H_{l+1} x - p_{l+1}||^2 +
+    lambda J_rho)(x_{l+1,0}) (first-order coherence with phi_l), the bound restricted from b_l as
+    b_{l+1} = R y - min_{j in the fine neighbourhood} (y - b_l)_j (Eq. (constraint) for a bound
+    b_l in place of 0, so that y + P(x_{l+1} - x_{l+1,0}) >= b_l whenever x_{l+1} >= b_{l+1}),
+    and x = y + P(x_{l+1,*} - x_{l+1,0}).  Data decimate by 2 in time per level (O6); the data
+    weight compounds, w_l = (2^(1-d))^l (O11 per level step); L_l = w_l L(H_l^T H_l) +
+    lambda 4 d / rho.  With one coarse level this is O7 exactly.
 """
 from __future__ import annotations
 
@@ -223,24 +234,30 @@ def neighbourhood_min(yf):
     return m
 
 
-def coarse_lower_bound(y_fine):
-    """phi_{h-1} = R y - min over the fine neighbourhood (Sec. V.C Eq. (constraint); O5)."""
-    return restrict(y_fine) - neighbourhood_min(y_fine)
+def coarse_lower_bound(y_fine, lower_fine=None):
+    """phi_{h-1} = R y - min over the fine neighbourhood of y (Sec. V.C Eq. (constraint); O5), or of
+    y - b for a fine bound b (O12)."""
+    if lower_fine is None:
+        return restrict(y_fine) - neighbourhood_min(y_fine)
+    return restrict(y_fine) - neighbourhood_min(np.asarray(y_fine, dtype=float) - lower_fine)
 
 
 # ---------------------------------------------------------------------------------------------
 # Levels (O6) and the power method (O10)
 # ---------------------------------------------------------------------------------------------
 
-def coarse_operator(pb):
-    """Coarse-level operator for a Problem (O6).  Returns (Operator, Nt_c)."""
-    d = pb.ndim
+def coarse_problem(pb):
+    """The coarse level's problem description (O6), in the fields Operator.from_problem reads; a
+    coarse problem can itself be coarsened (O12)."""
+    import types
+
+    d = pb.ndim if hasattr(pb, "ndim") else len(pb.shape)
     shape_c = tuple(n // 2 for n in pb.shape)
     spacing_c = tuple(2.0 * h for h in pb.spacing)
     pml_c = tuple(p // 2 for p in pb.pml)
     sl = tuple(slice(0, None, 2) for _ in range(d))
-    c_c = np.asarray(pb.c)[sl]
-    rho_c = np.asarray(pb.rho)[sl]
+    c_c = np.broadcast_to(np.asarray(pb.c, dtype=float), pb.shape)[sl]
+    rho_c = np.broadcast_to(np.asarray(pb.rho, dtype=float), pb.shape)[sl]
     a_c = np.broadcast_to(np.asarray(pb.alpha0, dtype=float), pb.shape)[sl]
     Nt_c = (pb.Nt + 1) // 2
     if pb.sensor_index is not None:
@@ -254,9 +271,15 @@ def coarse_operator(pb):
         lo = (0 - shape_c[a] // 2) * spacing_c[a]
         hi = (shape_c[a] - 1 - shape_c[a] // 2) * spacing_c[a]
         pos[:, d - 1 - a] = np.clip(pos[:, d - 1 - a], lo, hi)
-    op = Operator(shape_c, spacing_c, pml_c, pb.pml_alpha, c_c, rho_c, a_c, pb.y, 2.0 * pb.dt, Nt_c,
-                  sensor_pos=pos)
-    return op, Nt_c
+    return types.SimpleNamespace(ndim=d, shape=shape_c, spacing=spacing_c, pml=pml_c, pml_alpha=pb.pml_alpha,
+                                 c=c_c, rho=rho_c, alpha0=a_c, y=pb.y, dt=2.0 * pb.dt, Nt=Nt_c,
+                                 sensor_pos=pos, sensor_index=None)
+
+
+def coarse_operator(pb):
+    """Coarse-level operator for a Problem (O6).  Returns (Operator, Nt_c)."""
+    pc = coarse_problem(pb)
+    return Operator.from_problem(pc), pc.Nt
 
 
 def power_iteration(apply_HtH: Callable[[np.ndarray], np.ndarray], shape, n_iter=30, seed=0):
@@ -305,10 +328,15 @@ class IterRecord:
     adj: int
 
 
-def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts, w=1.0):
+def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts, w=1.0, deeper=(), w_step=None):
     """Coarse-level FISTA/ISTA on phi = w/2||H_c x - p_c||^2 + lam J_rho(x) + <v, x> with the
-    projection on {x >= lower} (Sec. V.E; O7, O11).  Returns (x_*, number of iterations, fwd, adj)."""
+    projection on {x >= lower} (Sec. V.E; O7, O11).  ``deeper`` = [(op, phat, L_data), ...] are the
+    next coarser levels: with one or more, an iteration k > 1 may take a recursive direction (O12);
+    ``w_step`` is the weight factor per level step (2^(1-d) by default).  Returns (x_*, number of
+    iterations, fwd, adj, recursive iterations at this level and below)."""
     alpha = 1.0 / L_c
+    d = x0.ndim
+    ws = w_step if w_step is not None else 2.0 ** (1 - d)
 
     def phi(x, Hx):
         r = Hx - phat_c
@@ -316,16 +344,44 @@ def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts, w=1
 
     x_prev = x0.copy()
     Hx_prev = op_c.forward(x_prev)
-    fwd, adj = 1, 0
+    fwd, adj, nrec = 1, 0, 0
     y, Hy = x_prev.copy(), Hx_prev.copy()
     phi_prev = phi(x_prev, Hx_prev)
     t = 1.0
+    K_d, K_r = 0, 0
+    y_tilde = None
     k = 0
     while True:
         k += 1
         grad = w * op_c.adjoint(Hy - phat_c) + lam * tv_smooth_grad(y, rho) + v
         adj += 1
-        x = np.maximum(y - alpha * grad, lower)
+        recursive = False
+        if deeper and opts.recursion and k > 1:
+            Rg = restrict(grad)
+            c1 = np.linalg.norm(Rg) > opts.kappa * np.linalg.norm(grad)
+            far = (y_tilde is not None) and (np.linalg.norm(y - y_tilde) > opts.vartheta * np.linalg.norm(y_tilde))
+            recursive = bool(c1 and (far or K_r == 0 or K_d > opts.q_d))
+        if recursive:
+            K_d, K_r = 0, K_r + 1
+            y_tilde = y.copy()
+            op_n, phat_n, Ld_n = deeper[0]
+            w_n = w * ws
+            x_n0 = restrict(y)
+            g_n = w_n * op_n.adjoint(op_n.forward(x_n0) - phat_n) + lam * tv_smooth_grad(x_n0, rho)
+            fwd += 1
+            adj += 1
+            v_n = Rg - g_n                                       # coherence with phi (O12)
+            lower_n = coarse_lower_bound(y, lower)               # restricted bound (O12)
+            L_n = w_n * Ld_n + lam * 4.0 * d / rho
+            x_ns, _, cf, ca, cr = fista_coarse(op_n, phat_n, x_n0, v_n, lower_n, lam, rho, L_n, opts, w=w_n,
+                                               deeper=deeper[1:], w_step=ws)
+            fwd += cf
+            adj += ca
+            nrec += 1 + cr
+            x = y + prolong(x_ns - x_n0)
+        else:
+            K_d += 1
+            x = np.maximum(y - alpha * grad, lower)
         Hx = op_c.forward(x)
         fwd += 1
         phi_x = phi(x, Hx)
@@ -340,15 +396,17 @@ def fista_coarse(op_c, phat_c, x0, v, lower, lam, rho, L_c, opts: FistaOpts, w=1
         dec = (phi_prev - phi_x) / max(abs(phi_prev), abs(phi_x), 1e-300)
         x_prev, Hx_prev, phi_prev = x, Hx, phi_x
         if dec < opts.eps_c or k >= opts.q_c:
-            return x, k, fwd, adj
+            return x, k, fwd, adj, nrec
 
 
 def mg_fista(op, phat, x0, L, opts: FistaOpts, coarse=None, p_exact=None,
              callback: Optional[Callable[[IterRecord], None]] = None):
-    """Alg. 3 (Sec. V.E) on two levels; with ``coarse`` None or ``opts.recursion`` False it is
-    Alg. 2 (FISTA) or Alg. 1 (ISTA, variant 0).
+    """Alg. 3 (Sec. V.E) on two levels, or on more (O12); with ``coarse`` None or
+    ``opts.recursion`` False it is Alg. 2 (FISTA) or Alg. 1 (ISTA, variant 0).
 
-    ``coarse`` = (op_c, phat_c, L_c_data).  Returns (x, list of IterRecord)."""
+    ``coarse`` = (op_c, phat_c, L_c_data) for two levels, or a list of such tuples from the first
+    coarse level down.  Returns (x, list of IterRecord)."""
+    levels = [] if coarse is None else ([coarse] if isinstance(coarse, tuple) else list(coarse))
     lam, rho = opts.lam, opts.tv_rho
     d = x0.ndim
     alpha = opts.step_scale / L
@@ -371,7 +429,7 @@ def mg_fista(op, phat, x0, L, opts: FistaOpts, coarse=None, p_exact=None,
         gf = op.adjoint(Hy - phat)   # grad f(y_k) = H^T (H y_k - p_hat), Eq. (Six)
         adj += 1
         recursive = False
-        if coarse is not None and opts.recursion and k > 1:
+        if levels and opts.recursion and k > 1:
             gF = gf + lam * tv_smooth_grad(y, rho)   # Eq. (Twentyone)
             Rg = restrict(gF)
             c1 = np.linalg.norm(Rg) > opts.kappa * np.linalg.norm(gF)
@@ -381,7 +439,7 @@ def mg_fista(op, phat, x0, L, opts: FistaOpts, coarse=None, p_exact=None,
         if recursive:
             K_d, K_r = 0, K_r + 1
             y_tilde = y.copy()
-            op_c, phat_c, L_c_data = coarse
+            op_c, phat_c, L_c_data = levels[0]
             x_c0 = restrict(y)
             w_c = opts.coarse_weight if opts.coarse_weight > 0 else 2.0 ** (1 - d)   # O11
             gc = w_c * op_c.adjoint(op_c.forward(x_c0) - phat_c) + lam * tv_smooth_grad(x_c0, rho)
@@ -390,7 +448,8 @@ def mg_fista(op, phat, x0, L, opts: FistaOpts, coarse=None, p_exact=None,
             v = Rg - gc                                   # Eq. (Fourteen)
             lower = coarse_lower_bound(y)                 # Eq. (constraint) at y (O5)
             L_c = w_c * L_c_data + lam * 4.0 * d / rho
-            x_cs, _, cf, ca = fista_coarse(op_c, phat_c, x_c0, v, lower, lam, rho, L_c, opts, w=w_c)
+            x_cs, _, cf, ca, _ = fista_coarse(op_c, phat_c, x_c0, v, lower, lam, rho, L_c, opts, w=w_c,
+                                              deeper=levels[1:], w_step=w_c)
             fwd += cf
             adj += ca
             x = y + prolong(x_cs - x_c0)

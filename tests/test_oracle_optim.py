@@ -220,6 +220,81 @@ def test_mg_fista_runs_recursive_branch_and_stays_feasible():
     assert recs[-1].F < 0.5 * F0
 
 
+def _mg3_setup():
+    # three levels: 32^2 -> 16^2 -> 8^2 (O12)
+    pb, op, phat, L, lev1 = _mg_setup()
+    p1 = po.coarse_problem(pb)
+    op2, Nt2 = po.coarse_operator(p1)
+    L2 = po.power_iteration(lambda v: op2.adjoint(op2.forward(v)), op2.shape, n_iter=15, seed=3)
+    lev2 = (op2, lev1[1][::2][:Nt2], L2)
+    return pb, op, phat, L, lev1, lev2
+
+
+def test_restricted_bound_keeps_a_nonzero_fine_bound():
+    # O12: with b_c = R y - min_{neighbourhood}(y - b), every x_c >= b_c gives y + P(x_c - R y) >= b
+    rng = np.random.default_rng(21)
+    for shape in [(16, 12), (8, 6, 10)]:
+        y = rng.standard_normal(shape)
+        b = y - np.abs(rng.standard_normal(shape))          # y is feasible for b
+        bc = po.coarse_lower_bound(y, b)
+        xc = bc + np.abs(rng.standard_normal(bc.shape)) * rng.integers(0, 2, bc.shape)   # some active
+        x = y + po.prolong(xc - po.restrict(y))
+        assert (x - b).min() >= -1e-12
+    # b = 0 is Eq. (constraint) as before
+    y = np.abs(rng.standard_normal((12, 10)))
+    assert np.array_equal(po.coarse_lower_bound(y, np.zeros_like(y)), po.coarse_lower_bound(y))
+
+
+def test_second_level_first_order_coherence():
+    # O12: grad phi_2(x_{2,0}) = R grad phi_1(y) for the coarse model phi_1 of a fine iterate
+    pb, op, phat, L, (op1, p1, L1), (op2, p2, L2) = _mg3_setup()
+    rng = np.random.default_rng(8)
+    lam, rho, w1 = 1e-2, 1e-2, 0.5
+    y = np.abs(rng.standard_normal(op1.shape))
+    v1 = rng.standard_normal(op1.shape)
+    g1 = w1 * op1.adjoint(op1.forward(y) - p1) + lam * po.tv_smooth_grad(y, rho) + v1
+    x20 = po.restrict(y)
+    w2 = w1 * 0.5
+    v2 = po.restrict(g1) - (w2 * op2.adjoint(op2.forward(x20) - p2) + lam * po.tv_smooth_grad(x20, rho))
+    g2 = w2 * op2.adjoint(op2.forward(x20) - p2) + lam * po.tv_smooth_grad(x20, rho) + v2
+    assert np.max(np.abs(g2 - po.restrict(g1))) < 1e-12 * np.abs(g1).max()
+
+
+def test_three_levels_reduce_to_two_with_one_coarse_iteration():
+    # the level-1 solve recurses only from its second iteration on (O12), so with q_c = 1 the
+    # three-level run is the two-level run, operation for operation
+    pb, op, phat, L, lev1, lev2 = _mg3_setup()
+    opts = po.FistaOpts(variant=1, max_iter=5, eps_d=-1.0, q_c=1)
+    x2, r2 = po.mg_fista(op, phat, np.zeros(pb.shape), L, opts, coarse=lev1)
+    x3, r3 = po.mg_fista(op, phat, np.zeros(pb.shape), L, opts, coarse=[lev1, lev2])
+    assert any(r.branch == "recursive" for r in r2)
+    assert np.array_equal(x2, x3)
+    assert [r.F for r in r2] == [r.F for r in r3]
+
+
+def test_three_levels_recurse_at_the_middle_level_and_stay_feasible():
+    pb, op, phat, L, (op1, p1, L1), lev2 = _mg3_setup()
+    rng = np.random.default_rng(9)
+    lam, rho, w1 = 1e-2, 1e-2, 0.5
+    y = np.abs(rng.standard_normal(pb.shape))
+    x10 = po.restrict(y)
+    g = op.adjoint(op.forward(y) - phat) + lam * po.tv_smooth_grad(y, rho)
+    v1 = po.restrict(g) - (w1 * op1.adjoint(op1.forward(x10) - p1) + lam * po.tv_smooth_grad(x10, rho))
+    b1 = po.coarse_lower_bound(y)
+    L1c = w1 * L1 + lam * 8.0 / rho
+    opts = po.FistaOpts(variant=1, q_c=8, eps_c=-1.0, kappa=0.25)
+    xa, ka, _, _, nra = po.fista_coarse(op1, p1, x10, v1, b1, lam, rho, L1c, opts, w=w1)
+    xb, kb, _, _, nrb = po.fista_coarse(op1, p1, x10, v1, b1, lam, rho, L1c, opts, w=w1, deeper=[lev2])
+    assert nra == 0 and nrb >= 1 and ka == kb == 8
+    assert (xb - b1).min() >= -1e-12
+
+    def phi(x):
+        r = op1.forward(x) - p1
+        return 0.5 * w1 * np.sum(r * r) + lam * po.tv_smooth(x, rho) + np.sum(v1 * x)
+
+    assert phi(xb) < phi(x10) and phi(xa) < phi(x10)
+
+
 def test_paper_parameters_golden():
     # The algorithm parameters printed in Sec. VI.A / VI.B are the FistaOpts defaults (2-D).
     with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:

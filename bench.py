@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
     ap.add_argument("--mg-iters", type=int, default=20)
+    ap.add_argument("--mg-levels", type=int, default=2, help="levels of MG-FISTA (2 or 3)")
     ap.add_argument("--batch", action="store_true",
                     help="also time 8 uneven 2-D instances as one batched launch vs one at a time")
     ap.add_argument("--trace", type=int, default=0,
@@ -343,6 +344,7 @@ def mg_vs_fista(args, dev, pb):
 
     op = PATOperator.from_problem(pb, precision="f32", device=dev)
     opc = op.coarse()
+    opc2 = opc.coarse() if args.mg_levels >= 3 else None
     x_true = torch.tensor(pb.p0, dtype=torch.float32, device=dev)
     clean = op.forward(x_true).cpu().numpy()
     noisy = synth.awgn(np.random.default_rng(2), clean, 40.0)
@@ -350,6 +352,8 @@ def mg_vs_fista(args, dev, pb):
     t0 = time.perf_counter()
     L = op.power_iteration(torch.tensor(synth.random_image(11, pb.shape), dtype=torch.float32, device=dev), 30)
     Lc = opc.power_iteration(torch.tensor(synth.random_image(12, opc.shape), dtype=torch.float32, device=dev), 30)
+    Lc2 = (opc2.power_iteration(torch.tensor(synth.random_image(13, opc2.shape), dtype=torch.float32, device=dev), 30)
+           if opc2 is not None else None)
     setup_s = time.perf_counter() - t0
     x0 = torch.zeros_like(x_true)
     d = len(pb.shape)
@@ -359,7 +363,10 @@ def mg_vs_fista(args, dev, pb):
     def timed(coarse, recursion, max_iter, target):
         stamps = []
         t_start = time.perf_counter()
-        _, rep, recs = mg_fista(op, coarse, data, x0, L, L_coarse=Lc, p_exact=x_true, recursion=recursion,
+        Lco = Lc
+        if coarse is not None and opc2 is not None:
+            coarse, Lco = [opc, opc2], [Lc, Lc2]
+        _, rep, recs = mg_fista(op, coarse, data, x0, L, L_coarse=Lco, p_exact=x_true, recursion=recursion,
                                 max_iter=max_iter, target_re=target,
                                 callback=lambda r: stamps.append(time.perf_counter() - t_start), **common)
         for r, ts in zip(recs, stamps):
@@ -385,15 +392,18 @@ def mg_vs_fista(args, dev, pb):
         return time.perf_counter() - t0
 
     fine_pair, coarse_pair = pair_s(op), pair_s(opc)
+    coarse2_pair = pair_s(opc2) if opc2 is not None else None
     curve = lambda recs: [(r["k"], r["branch"][0], round(r["RE"], 4), round(r["t"], 3)) for r in recs]
     return {"workload": pb.name, "target_re": target, "fista_best_re": best, "fista_s": t_f, "fista_iters": it_f,
-            "fwd_adj_pair_s": {"fine": fine_pair, "coarse": coarse_pair, "ratio": coarse_pair / fine_pair},
+            "levels": args.mg_levels,
+            "fwd_adj_pair_s": {"fine": fine_pair, "coarse": coarse_pair, "ratio": coarse_pair / fine_pair,
+                               "coarse2": coarse2_pair},
             "fista_curve": curve(recs_f), "mgfista_curve": curve(recs_m),
             "mgfista_s": t_m, "mgfista_iters": hit[0]["k"] if hit else None,
             "mgfista_recursive_iters": sum(1 for r in recs_m if r["branch"] == "recursive"),
             "speedup": (t_f / t_m) if t_m else None, "setup_s_power_method": setup_s,
             "data": "forward of the phantom on the same grid + 40 dB AWGN (inverse crime, stated)",
-            "params": dict(common, lam=1e-2, L=L, L_coarse=Lc)}
+            "params": dict(common, lam=1e-2, L=L, L_coarse=Lc, L_coarse2=Lc2)}
 
 
 def main():

@@ -282,6 +282,25 @@ pat_status pat_mg_fista(pat_plan* fine, pat_plan* coarse, const void* data, cons
                         const pat_fista_opts* opts, void* x_out, pat_fista_report* report, pat_iter_callback cb,
                         void* cb_ctx, void* stream);
 
+/* pat_mg_fista_levels -- the same method on nlevels >= 1 levels (at most 8): levels[0] is the fine
+ * plan and levels[l] the coarse plan of levels[l - 1] (pat_plan_create_coarse); L_levels[l] is
+ * sigma_max(H_l^T H_l) (pat_power_iteration; L_levels[0] takes the place of opts->L and
+ * L_levels[1] of opts->L_coarse, which are not read here).  The paper states Alg. 3 for two
+ * grids (Sec. V.E).  With more, the projected FISTA of a coarse level l may itself take recursive
+ * directions to level l + 1 under the same test, applied to its model phi_l (reading O12 of the
+ * optimisation oracle):
+ *   - the coherence term is formed from grad phi_l;
+ *   - the bound is restricted from level l's own bound, R y - min over the fine neighbourhood of
+ *     (y - b_l);
+ *   - the data term's weight compounds per level step (w_l = w^l, w as in opts->coarse_weight).
+ * With two levels it is pat_mg_fista exactly.  Errors: PAT_EINVAL for NULL arguments, nlevels
+ * outside 1 .. 8, a level that is not the coarse level of the one above, or L_levels <= 0 on a
+ * level the recursion uses.  report->recursive_iters counts the fine level's recursive
+ * iterations; fwd_solves / adj_solves count the solves of every level. */
+pat_status pat_mg_fista_levels(pat_plan* const* levels, int nlevels, const double* L_levels, const void* data,
+                               const void* x0, const pat_fista_opts* opts, void* x_out, pat_fista_report* report,
+                               pat_iter_callback cb, void* cb_ctx, void* stream);
+
 /* pat_plan_status -- synchronise the device and return the status word of the plan's last solve:
  * PAT_OK, or PAT_ETIMEOUT if a bounded device-side wait (the grid barrier of the persistent
  * kernel) ran out; the kernel then stopped early and its outputs are not valid. */

@@ -134,6 +134,10 @@ def lib() -> ctypes.CDLL:
     L.pat_mg_fista.argtypes = [vp, vp, vp, vp, ctypes.POINTER(pat_fista_opts), vp, ctypes.POINTER(pat_fista_report),
                                ITER_CB, vp, vp]
     L.pat_mg_fista.restype = i32
+    L.pat_mg_fista_levels.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_double), vp, vp,
+                                      ctypes.POINTER(pat_fista_opts), vp, ctypes.POINTER(pat_fista_report), ITER_CB,
+                                      vp, vp]
+    L.pat_mg_fista_levels.restype = i32
     L.pat_last_error.argtypes = []
     L.pat_last_error.restype = ctypes.c_char_p
     _lib = L

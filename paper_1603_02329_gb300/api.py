@@ -343,7 +343,11 @@ FISTA_DEFAULTS = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25, vartheta=
 
 def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.Tensor, x0: torch.Tensor, L: float,
              L_coarse: float = 0.0, p_exact: Optional[torch.Tensor] = None, callback=None, stream=None, **opts):
-    """pat_mg_fista: Alg. 3 (two levels) or Alg. 2 / Alg. 1.  Returns (x, report dict, records)."""
+    """pat_mg_fista: Alg. 3 (two levels) or Alg. 2 / Alg. 1.  Returns (x, report dict, records).
+
+    ``coarse`` may also be a list of operators, each the coarse level of the one before
+    (``PATOperator.coarse()``), with ``L_coarse`` the list of their sigma_max(H^T H): the call is
+    then pat_mg_fista_levels on 1 + len(coarse) levels."""
     o = dict(FISTA_DEFAULTS)
     o.update(opts)
     po = _lib.pat_fista_opts()
@@ -361,7 +365,7 @@ def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.T
     po.max_iter = int(o["max_iter"])
     po.recursion = int(bool(o["recursion"]))
     po.L = float(L)
-    po.L_coarse = float(L_coarse)
+    po.L_coarse = float(L_coarse[0] if isinstance(L_coarse, (list, tuple)) else L_coarse)
     po.target_re = float(o["target_re"])
     po.p_exact = ctypes.c_void_p(p_exact.data_ptr()) if p_exact is not None else None
     po.coarse_weight = float(o.get("coarse_weight", 0.0))
@@ -375,11 +379,25 @@ def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.T
     cb = _lib.ITER_CB(_cb)
     rep = _lib.pat_fista_report()
     x = torch.empty_like(x0)
-    cplan = coarse._plan if coarse is not None else None
-    with torch.cuda.device(fine.device):
-        check(lib().pat_mg_fista(fine._plan, cplan, ctypes.c_void_p(data.data_ptr()), ctypes.c_void_p(x0.data_ptr()),
-                                 ctypes.byref(po), ctypes.c_void_p(x.data_ptr()), ctypes.byref(rep), cb, None,
-                                 _stream_ptr(stream, fine.device)))
+    if isinstance(coarse, (list, tuple)):
+        ops = [fine] + list(coarse)
+        Ls = [float(L)] + [float(v) for v in (L_coarse if isinstance(L_coarse, (list, tuple)) else [L_coarse])]
+        if len(Ls) != len(ops):
+            raise ValueError("L_coarse needs one value per coarse level")
+        plans = (ctypes.c_void_p * len(ops))(*[op._plan.value for op in ops])
+        larr = (ctypes.c_double * len(Ls))(*Ls)
+        po.L_coarse = Ls[1] if len(Ls) > 1 else 0.0
+        with torch.cuda.device(fine.device):
+            check(lib().pat_mg_fista_levels(plans, len(ops), larr, ctypes.c_void_p(data.data_ptr()),
+                                            ctypes.c_void_p(x0.data_ptr()), ctypes.byref(po),
+                                            ctypes.c_void_p(x.data_ptr()), ctypes.byref(rep), cb, None,
+                                            _stream_ptr(stream, fine.device)))
+    else:
+        cplan = coarse._plan if coarse is not None else None
+        with torch.cuda.device(fine.device):
+            check(lib().pat_mg_fista(fine._plan, cplan, ctypes.c_void_p(data.data_ptr()),
+                                     ctypes.c_void_p(x0.data_ptr()), ctypes.byref(po), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.byref(rep), cb, None, _stream_ptr(stream, fine.device)))
     report = dict(iters=rep.iters, recursive_iters=rep.recursive_iters, fwd_solves=rep.fwd_solves,
                   adj_solves=rep.adj_solves, F=rep.F, RES=rep.RES, RE=rep.RE)
     return x, report, records

@@ -8,6 +8,7 @@
 // synchronising once per reduction.
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "pat_host.h"
@@ -51,48 +52,107 @@ template <typename T> struct Driver {
         return st;
     }
 
-    // Coarse-level FISTA / ISTA on phi = 1/2 ||H_c x - p_c||^2 + lam J_rho(x) + <v, x> with the
-    // projection on {x >= lower} (Alg. 3 line 9; Sec. V.E).  x0 is x_{h-1,0}; result in xout.
-    static pat_status coarse_solve(pat_plan* cp, const pat_grid* gc, const T* phat_c, const T* x0, const T* v,
-                                   const T* lower, double L_c, double wc, const pat_fista_opts* o, T* xout,
-                                   T* const* ws, T* const* wd, int* nfwd, int* nadj, cudaStream_t s) {
-        const long long N = cp->impl->info.N, M = (long long)cp->impl->info.Nt * cp->impl->info.Ns;
-        const double alpha = 1.0 / L_c, lam = o->lambda, rho = o->tv_rho;
-        T* xp = ws[0];
-        T* y = ws[1];
-        T* g = ws[2];
-        T* x = ws[3];
-        T* Hxp = wd[0];
-        T* Hy = wd[1];
-        T* Hx = wd[2];
-        T* r = wd[3];
+    // One coarse level of the hierarchy (levels 1 .. nl - 1 below the fine level 0): its plan, grid
+    // and sizes, L(H^T H), the weight w of its data term (O11 per level step) and its work arrays.
+    struct Lev {
+        pat_plan* plan = nullptr;
+        pat_grid grid{};
+        long long N = 0, M = 0;
+        int Nt = 0, Ns = 0;
+        double Ld = 0.0, w = 1.0;
+        // images: start x_{l,0}, coherence term v_l, bound b_l, gradient of the level's own data and
+        // TV terms at x_{l,0}, result x_{l,*}, the FISTA iterates, y~, the restricted gradient of
+        // the level above, scratch of the restricted bound
+        T *x0, *v, *lower, *gcb, *xs, *xp, *y, *gr, *x, *ytil, *rg, *tmp;
+        // data: p_hat_l (decimated in time), H x_prev, H y, H x, residual
+        T *phat, *Hxp, *Hy, *Hx, *r;
+    };
+    struct Count {
+        int nfwd = 0, nadj = 0;
+    };
+
+    // Level-l FISTA / ISTA on phi_l = w_l/2 ||H_l x - p_l||^2 + lam J_rho(x) + <v_l, x> with the
+    // projection on {x >= b_l} (Alg. 3 line 9; Sec. V.E), from x_{l,0} into x_{l,*}.  When a level
+    // l + 1 exists, an iteration k > 1 takes a recursive direction under the test of Sec. V.D
+    // applied to phi_l, with the bound restricted from b_l (the multi-level reading of the oracle,
+    // O12); with two levels this is the coarse solve of Alg. 3 exactly.
+    static pat_status level_solve(Lev* lv, int nl, int l, const pat_fista_opts* o, Count* cnt, cudaStream_t s) {
+        Lev& L = lv[l];
+        const long long N = L.N, M = L.M;
+        const int d = L.grid.ndim;
+        const double lam = o->lambda, rho = o->tv_rho;
+        const double L_c = L.w * L.Ld + lam * 4.0 * d / rho;
+        const double alpha = 1.0 / L_c;
+        T* xp = L.xp;
+        T* x = L.x;
+        T* Hxp = L.Hxp;
+        T* Hx = L.Hx;
+        T* y = L.y;
+        T* g = L.gr;
+        T* Hy = L.Hy;
+        T* r = L.r;
         auto phi = [&](const T* xx, const T* Hxx, double* out) -> pat_status {
             double sq = 0.0, js = 0.0, vx = 0.0;
-            TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, M, Hxx, phat_c, 0.0, &sq, s));
-            TRY(Ops<T>::reduce(HRED_TVS, gc, N, xx, nullptr, rho, &js, s));
-            TRY(Ops<T>::reduce(HRED_DOT, nullptr, N, v, xx, 0.0, &vx, s));
-            *out = 0.5 * wc * sq + lam * js + vx;
+            TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, M, Hxx, L.phat, 0.0, &sq, s));
+            TRY(Ops<T>::reduce(HRED_TVS, &L.grid, N, xx, nullptr, rho, &js, s));
+            TRY(Ops<T>::reduce(HRED_DOT, nullptr, N, L.v, xx, 0.0, &vx, s));
+            *out = 0.5 * L.w * sq + lam * js + vx;
             return PAT_OK;
         };
-        TRY(Ops<T>::lincomb(N, xp, 1.0, x0, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
-        TRY(fwd(cp, xp, Hxp, s));
-        ++*nfwd;
+        auto norm = [&](const T* a, long long n, double* out) -> pat_status {
+            double q = 0.0;
+            TRY(Ops<T>::reduce(HRED_DOT, nullptr, n, a, a, 0.0, &q, s));
+            *out = std::sqrt(q);
+            return PAT_OK;
+        };
+        TRY(Ops<T>::lincomb(N, xp, 1.0, L.x0, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
+        TRY(fwd(L.plan, xp, Hxp, s));
+        ++cnt->nfwd;
         TRY(Ops<T>::lincomb(N, y, 1.0, xp, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
         TRY(Ops<T>::lincomb(M, Hy, 1.0, Hxp, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
         double phi_prev = 0.0;
         TRY(phi(xp, Hxp, &phi_prev));
         double t = 1.0;
+        int K_d = 0, K_r = 0;
+        bool have_ytil = false;
         for (int k = 1;; ++k) {
-            // grad = w H_c^T (H_c y - p_c) + lam grad J_rho(y) + v
-            TRY(Ops<T>::lincomb(M, r, 1.0, Hy, -1.0, phat_c, 0.0, nullptr, nullptr, 0, s));
-            TRY(adj(cp, r, g, s));
-            ++*nadj;
-            TRY(Ops<T>::tv_smooth_grad(gc, y, rho, g, lam, wc, s));
-            TRY(Ops<T>::lincomb(N, g, 1.0, g, 1.0, v, 0.0, nullptr, nullptr, 0, s));
-            // x = max(y - alpha grad, lower)
-            TRY(Ops<T>::lincomb(N, x, 1.0, y, -alpha, g, 0.0, nullptr, lower, 0, s));
-            TRY(fwd(cp, x, Hx, s));
-            ++*nfwd;
+            // grad phi_l(y) = w H^T (H y - p) + lam grad J_rho(y) + v
+            TRY(Ops<T>::lincomb(M, r, 1.0, Hy, -1.0, L.phat, 0.0, nullptr, nullptr, 0, s));
+            TRY(adj(L.plan, r, g, s));
+            ++cnt->nadj;
+            TRY(Ops<T>::tv_smooth_grad(&L.grid, y, rho, g, lam, L.w, s));
+            TRY(Ops<T>::lincomb(N, g, 1.0, g, 1.0, L.v, 0.0, nullptr, nullptr, 0, s));
+            bool recursive = false;
+            if (l + 1 < nl && o->recursion && k > 1) {
+                Lev& C = lv[l + 1];
+                TRY(Ops<T>::restrict_(&L.grid, g, C.rg, s));
+                double nRg = 0.0, ng = 0.0;
+                TRY(norm(C.rg, C.N, &nRg));
+                TRY(norm(g, N, &ng));
+                bool far = false;
+                if (have_ytil) {
+                    double ndiff = 0.0, nyt = 0.0;
+                    TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, N, y, L.ytil, 0.0, &ndiff, s));
+                    TRY(norm(L.ytil, N, &nyt));
+                    far = std::sqrt(ndiff) > o->vartheta * nyt;
+                }
+                recursive = (nRg > o->kappa * ng) && (far || K_r == 0 || K_d > o->q_d);
+            }
+            if (recursive) {
+                K_d = 0;
+                ++K_r;
+                have_ytil = true;
+                TRY(Ops<T>::lincomb(N, L.ytil, 1.0, y, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
+                TRY(coarse_step(lv, nl, l + 1, &L.grid, y, L.lower, o, cnt, s));
+                TRY(Ops<T>::lincomb(N, x, 1.0, y, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
+                TRY(Ops<T>::prolong(&L.grid, lv[l + 1].xs, x, 1.0, 1.0, s));
+            } else {
+                ++K_d;
+                // x = max(y - alpha grad, lower)
+                TRY(Ops<T>::lincomb(N, x, 1.0, y, -alpha, g, 0.0, nullptr, L.lower, 0, s));
+            }
+            TRY(fwd(L.plan, x, Hx, s));
+            ++cnt->nfwd;
             double phi_x = 0.0;
             TRY(phi(x, Hx, &phi_x));
             double theta = 0.0;
@@ -110,26 +170,56 @@ template <typename T> struct Driver {
             phi_prev = phi_x;
             if (dec < o->eps_c || k >= o->q_c) break;
         }
-        return Ops<T>::lincomb(N, xout, 1.0, xp, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s);
+        return Ops<T>::lincomb(N, L.xs, 1.0, xp, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s);
     }
 
-    static pat_status run(pat_plan* fp, pat_plan* cp, const T* phat, const T* x0, const pat_fista_opts* o, T* xout,
-                          pat_fista_report* rep, pat_iter_callback cb, void* ctx, cudaStream_t s) {
-        const PlanBase* fb = fp->impl;
+    // Recursive search direction from the level above level c (Alg. 3 lines 4-10): with C.rg =
+    // R grad of the level above at y, set x_{c,0} = R y, v_c = R grad - grad(w_c/2 ||H_c x - p_c||^2
+    // + lam J_rho)(x_{c,0}) (Eq. (Fourteen)), the bound restricted at y (Eq. (constraint); from
+    // b_above when the level above has a bound, O12), solve level c, and leave x_{c,*} - x_{c,0} in
+    // C.xs for the caller to prolong.
+    static pat_status coarse_step(Lev* lv, int nl, int c, const pat_grid* gabove, const T* y, const T* b_above,
+                                  const pat_fista_opts* o, Count* cnt, cudaStream_t s) {
+        Lev& C = lv[c];
+        const double lam = o->lambda, rho = o->tv_rho;
+        TRY(Ops<T>::restrict_(gabove, y, C.x0, s));
+        TRY(fwd(C.plan, C.x0, C.Hxp, s));
+        ++cnt->nfwd;
+        TRY(Ops<T>::lincomb(C.M, C.r, 1.0, C.Hxp, -1.0, C.phat, 0.0, nullptr, nullptr, 0, s));
+        TRY(adj(C.plan, C.r, C.gcb, s));
+        ++cnt->nadj;
+        TRY(Ops<T>::tv_smooth_grad(&C.grid, C.x0, rho, C.gcb, lam, C.w, s));
+        TRY(Ops<T>::lincomb(C.N, C.v, 1.0, C.rg, -1.0, C.gcb, 0.0, nullptr, nullptr, 0, s));
+        TRY(Ops<T>::coarse_bound(gabove, y, C.lower, C.tmp, s, b_above));
+        TRY(level_solve(lv, nl, c, o, cnt, s));
+        return Ops<T>::lincomb(C.N, C.xs, 1.0, C.xs, -1.0, C.x0, 0.0, nullptr, nullptr, 0, s);
+    }
+
+    // plans[0] is the fine level, plans[l] the level below plans[l - 1] (pat_plan_create_coarse);
+    // Ls[l] = L(H_l^T H_l) from the power method
+    static pat_status run(pat_plan* const* plans, int nl, const double* Ls, const T* phat, const T* x0,
+                          const pat_fista_opts* o, T* xout, pat_fista_report* rep, pat_iter_callback cb, void* ctx,
+                          cudaStream_t s) {
+        const PlanBase* fb = plans[0]->impl;
         const pat_grid gf = fb->in.grid;
         const long long N = fb->info.N, M = (long long)fb->info.Nt * fb->info.Ns;
-        const int d = gf.ndim;
-        pat_grid gc = gf;
-        long long Nc = 0, Mc = 0;
-        int Ntc = 0;
-        if (cp) {
-            for (int a = 0; a < d; ++a) gc.n[a] = gf.n[a] / 2;
-            Nc = cp->impl->info.N;
-            Ntc = cp->impl->info.Nt;
-            Mc = (long long)Ntc * cp->impl->info.Ns;
+        // weight of the coarse data term per level step (O11): 2^(1-d) unless given
+        const double wc = (o->coarse_weight > 0.0) ? o->coarse_weight : std::ldexp(1.0, 1 - gf.ndim);
+        std::vector<Lev> lv((size_t)nl);
+        // workspaces: fine image x 6, fine data x 4; per coarse level image x 12, data x 5
+        size_t elems = (size_t)(6 * N + 4 * M);
+        for (int l = 1; l < nl; ++l) {
+            Lev& L = lv[l];
+            L.plan = plans[l];
+            L.grid = plans[l]->impl->in.grid;
+            L.N = plans[l]->impl->info.N;
+            L.Nt = plans[l]->impl->info.Nt;
+            L.Ns = plans[l]->impl->info.Ns;
+            L.M = (long long)L.Nt * L.Ns;
+            L.Ld = Ls[l];
+            L.w = (l == 1) ? wc : lv[l - 1].w * wc;
+            elems += (size_t)(12 * L.N + 5 * L.M);
         }
-        // workspaces: fine image x 6, fine data x 4, coarse image x 10, coarse data x 5
-        const size_t elems = (size_t)(6 * N + 4 * M + 10 * Nc + 5 * Mc);
         T* buf = nullptr;
         cudaError_t e = cudaMallocAsync(&buf, elems * sizeof(T), s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (MG-FISTA)");
@@ -149,25 +239,29 @@ template <typename T> struct Driver {
         T* Hx = take(M);
         T* Hy = take(M);
         T* r = take(M);
-        T* cimg[10];
-        T* cdat[5];
-        for (int k = 0; k < 10; ++k) cimg[k] = take(Nc);
-        for (int k = 0; k < 5; ++k) cdat[k] = take(Mc);
-        pat_status st = run_inner(fp, cp, gf, gc, N, M, Nc, Mc, Ntc, phat, x0, o, xout, rep, cb, ctx, s, xp, x, y, g,
-                                  z, ytil, Hxp, Hx, Hy, r, cimg, cdat);
+        for (int l = 1; l < nl; ++l) {
+            Lev& L = lv[l];
+            T** im[12] = {&L.x0, &L.v, &L.lower, &L.gcb, &L.xs, &L.xp, &L.y, &L.gr, &L.x, &L.ytil, &L.rg, &L.tmp};
+            for (T** q : im) *q = take(L.N);
+            T** da[5] = {&L.phat, &L.Hxp, &L.Hy, &L.Hx, &L.r};
+            for (T** q : da) *q = take(L.M);
+        }
+        pat_status st = PAT_OK;
+        // data of each coarse level: the record of the level above decimated in time (p_c^m = p^{2m})
+        for (int l = 1; l < nl && st == PAT_OK; ++l)
+            st = Ops<T>::decimate_rows(l == 1 ? phat : lv[l - 1].phat, lv[l].phat, lv[l].Nt, lv[l].Ns, s);
+        if (st == PAT_OK)
+            st = run_inner(plans[0], gf, N, M, lv.data(), nl, phat, x0, o, xout, rep, cb, ctx, s, xp, x, y, g, z,
+                           ytil, Hxp, Hx, Hy, r);
         cudaFreeAsync(buf, s);
         return st;
     }
 
-    static pat_status run_inner(pat_plan* fp, pat_plan* cp, const pat_grid& gf, const pat_grid& gc, long long N,
-                                long long M, long long Nc, long long Mc, int Ntc, const T* phat, const T* x0,
-                                const pat_fista_opts* o, T* xout, pat_fista_report* rep, pat_iter_callback cb,
-                                void* ctx, cudaStream_t s, T* xp, T* x, T* y, T* g, T* z, T* ytil, T* Hxp, T* Hx,
-                                T* Hy, T* r, T* const* cimg, T* const* cdat) {
-        const int d = gf.ndim;
+    static pat_status run_inner(pat_plan* fp, const pat_grid& gf, long long N, long long M, Lev* lv, int nl,
+                                const T* phat, const T* x0, const pat_fista_opts* o, T* xout, pat_fista_report* rep,
+                                pat_iter_callback cb, void* ctx, cudaStream_t s, T* xp, T* x, T* y, T* g, T* z,
+                                T* ytil, T* Hxp, T* Hx, T* Hy, T* r) {
         const double lam = o->lambda, rho = o->tv_rho;
-        // weight of the coarse data term (O11): 2^(1-d) unless given
-        const double wc = (o->coarse_weight > 0.0) ? o->coarse_weight : std::ldexp(1.0, 1 - gf.ndim);
         const double alpha = o->step_scale / o->L;
         const T* pex = static_cast<const T*>(o->p_exact);
         double nrm_exact = 0.0;
@@ -175,7 +269,8 @@ template <typename T> struct Driver {
             TRY(Ops<T>::reduce(HRED_DOT, nullptr, N, pex, pex, 0.0, &nrm_exact, s));
             nrm_exact = std::sqrt(nrm_exact);
         }
-        int nfwd = 0, nadj = 0, nrec = 0;
+        Count cnt;
+        int nrec = 0;
         auto F_of = [&](const T* xx, const T* Hxx, double* F, double* RES) -> pat_status {
             double sq = 0.0, tv = 0.0;
             TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, M, Hxx, phat, 0.0, &sq, s));
@@ -190,13 +285,9 @@ template <typename T> struct Driver {
             *out = std::sqrt(q);
             return PAT_OK;
         };
-        // coarse data: the fine record decimated in time (p_c^m = p^{2m})
-        T* phat_c = cp ? cdat[4] : nullptr;
-        if (cp) TRY(Ops<T>::decimate_rows(phat, phat_c, Ntc, cp->impl->info.Ns, s));
-
         TRY(Ops<T>::lincomb(N, xp, 1.0, x0, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
         TRY(fwd(fp, xp, Hxp, s));
-        ++nfwd;
+        ++cnt.nfwd;
         double F_prev = 0.0, RES0 = 0.0;
         TRY(F_of(xp, Hxp, &F_prev, &RES0));
         TRY(Ops<T>::lincomb(N, y, 1.0, xp, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
@@ -210,15 +301,15 @@ template <typename T> struct Driver {
             // grad f(y_k) = H^T (H y_k - p_hat)   (Eq. (Six))
             TRY(Ops<T>::lincomb(M, r, 1.0, Hy, -1.0, phat, 0.0, nullptr, nullptr, 0, s));
             TRY(adj(fp, r, g, s));
-            ++nadj;
+            ++cnt.nadj;
             bool recursive = false;
-            if (cp && o->recursion && k > 1) {
-                // grad F_rho(y) (Eq. (Twentyone)) into z; R grad F_rho into cimg[8]
+            if (nl > 1 && o->recursion && k > 1) {
+                // grad F_rho(y) (Eq. (Twentyone)) into z; R grad F_rho into the first coarse level
                 TRY(Ops<T>::lincomb(N, z, 1.0, g, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
                 TRY(Ops<T>::tv_smooth_grad(&gf, y, rho, z, lam, 1.0, s));
-                TRY(Ops<T>::restrict_(&gf, z, cimg[8], s));
+                TRY(Ops<T>::restrict_(&gf, z, lv[1].rg, s));
                 double nRg = 0.0, ngF = 0.0;
-                TRY(norm(cimg[8], Nc, &nRg));
+                TRY(norm(lv[1].rg, lv[1].N, &nRg));
                 TRY(norm(z, N, &ngF));
                 const bool c1 = nRg > o->kappa * ngF;
                 bool far = false;
@@ -237,30 +328,10 @@ template <typename T> struct Driver {
                 ++nrec;
                 have_ytil = true;
                 TRY(Ops<T>::lincomb(N, ytil, 1.0, y, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
-                T* xc0 = cimg[0];
-                T* v = cimg[1];
-                T* lower = cimg[2];
-                T* gcb = cimg[3];
-                T* xcs = cimg[9];
-                // x_{h-1,0} = R y; v = R grad F_rho,h(y) - grad F_rho,h-1(x_{h-1,0})  (Eq. (Fourteen))
-                TRY(Ops<T>::restrict_(&gf, y, xc0, s));
-                TRY(fwd(cp, xc0, cdat[0], s));
-                ++nfwd;
-                TRY(Ops<T>::lincomb(Mc, cdat[1], 1.0, cdat[0], -1.0, phat_c, 0.0, nullptr, nullptr, 0, s));
-                TRY(adj(cp, cdat[1], gcb, s));
-                ++nadj;
-                TRY(Ops<T>::tv_smooth_grad(&gc, xc0, rho, gcb, lam, wc, s));
-                TRY(Ops<T>::lincomb(Nc, v, 1.0, cimg[8], -1.0, gcb, 0.0, nullptr, nullptr, 0, s));
-                // restricted bound at y (Eq. (constraint))
-                TRY(Ops<T>::coarse_bound(&gf, y, lower, cimg[4], s));
-                const double L_c = wc * o->L_coarse + lam * 4.0 * d / rho;
-                T* const ws[4] = {cimg[4], cimg[5], cimg[6], cimg[7]};
-                T* const wd[4] = {cdat[0], cdat[1], cdat[2], cdat[3]};
-                TRY(coarse_solve(cp, &gc, phat_c, xc0, v, lower, L_c, wc, o, xcs, ws, wd, &nfwd, &nadj, s));
-                // x = y + P (x_{h-1,*} - x_{h-1,0})
-                TRY(Ops<T>::lincomb(Nc, xcs, 1.0, xcs, -1.0, xc0, 0.0, nullptr, nullptr, 0, s));
+                // x = y + P (x_{h-1,*} - x_{h-1,0}), the coarse levels below solved recursively
+                TRY(coarse_step(lv, nl, 1, &gf, y, nullptr, o, &cnt, s));
                 TRY(Ops<T>::lincomb(N, x, 1.0, y, 0.0, nullptr, 0.0, nullptr, nullptr, 0, s));
-                TRY(Ops<T>::prolong(&gf, xcs, x, 1.0, 1.0, s));
+                TRY(Ops<T>::prolong(&gf, lv[1].xs, x, 1.0, 1.0, s));
             } else {
                 ++K_d;
                 // x = prox_{alpha g}(y - alpha grad f(y))   (Alg. 1 lines 3-4)
@@ -268,7 +339,7 @@ template <typename T> struct Driver {
                 TRY(Ops<T>::tv_prox(&gf, z, x, alpha * lam, o->n_tv, 1, s));
             }
             TRY(fwd(fp, x, Hx, s));
-            ++nfwd;
+            ++cnt.nfwd;
             double F_x = 0.0, RES = 0.0;
             TRY(F_of(x, Hx, &F_x, &RES));
             double RE = NAN;
@@ -277,7 +348,7 @@ template <typename T> struct Driver {
                 TRY(Ops<T>::reduce(HRED_SQDIFF, nullptr, N, x, pex, 0.0, &sq, s));
                 RE = std::sqrt(sq) / nrm_exact;
             }
-            if (cb) cb(ctx, k, recursive ? 1 : 0, F_x, RES, RE, nfwd, nadj);
+            if (cb) cb(ctx, k, recursive ? 1 : 0, F_x, RES, RE, cnt.nfwd, cnt.nadj);
             double theta = 0.0;
             if (o->variant == 1) {
                 const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
@@ -302,8 +373,8 @@ template <typename T> struct Driver {
         if (rep) {
             rep->iters = std::min(k, o->max_iter);
             rep->recursive_iters = nrec;
-            rep->fwd_solves = nfwd;
-            rep->adj_solves = nadj;
+            rep->fwd_solves = cnt.nfwd;
+            rep->adj_solves = cnt.nadj;
             rep->F = F_last;
             rep->RES = RES_last;
             rep->RE = RE_last;
@@ -394,31 +465,65 @@ pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** out) {
                            in.prec, out);
 }
 
+pat_status pat_mg_fista_levels(pat_plan* const* levels, int nlevels, const double* L_levels, const void* data,
+                               const void* x0, const pat_fista_opts* opts, void* x_out, pat_fista_report* report,
+                               pat_iter_callback cb, void* cb_ctx, void* stream) {
+    set_error("");
+    if (!levels || nlevels < 1 || nlevels > 8 || !L_levels || !levels[0] || !data || !x0 || !opts || !x_out) {
+        set_error("NULL argument or nlevels outside 1 .. 8");
+        return PAT_EINVAL;
+    }
+    const bool rec = opts->recursion != 0 && nlevels > 1;
+    if (!(L_levels[0] > 0.0) || opts->max_iter < 0 || !(opts->tv_rho > 0.0)) {
+        set_error("bad options (L, tv_rho must be > 0)");
+        return PAT_EINVAL;
+    }
+    for (int l = 1; l < nlevels; ++l) {
+        const pat_plan* up = levels[l - 1];
+        const pat_plan* lo = levels[l];
+        if (!lo) {
+            set_error("NULL level plan");
+            return PAT_EINVAL;
+        }
+        bool ok = lo->impl->info.precision == up->impl->info.precision && lo->impl->info.Ns == up->impl->info.Ns &&
+                  lo->impl->info.Nt == (up->impl->info.Nt + 1) / 2 &&
+                  lo->impl->in.grid.ndim == up->impl->in.grid.ndim;
+        for (int a = 0; ok && a < up->impl->in.grid.ndim; ++a)
+            ok = lo->impl->in.grid.n[a] == up->impl->in.grid.n[a] / 2;
+        if (!ok) {
+            set_error("level " + std::to_string(l) + " is not the coarse level of level " + std::to_string(l - 1) +
+                      " (use pat_plan_create_coarse)");
+            return PAT_EINVAL;
+        }
+        if (rec && !(L_levels[l] > 0.0)) {
+            set_error("L_levels must be > 0 on every level");
+            return PAT_EINVAL;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nl = rec ? nlevels : 1;
+    if (levels[0]->impl->info.precision == PAT_F32)
+        return Driver<float>::run(levels, nl, L_levels, (const float*)data, (const float*)x0, opts, (float*)x_out,
+                                  report, cb, cb_ctx, s);
+    return Driver<double>::run(levels, nl, L_levels, (const double*)data, (const double*)x0, opts, (double*)x_out,
+                               report, cb, cb_ctx, s);
+}
+
 pat_status pat_mg_fista(pat_plan* fine, pat_plan* coarse, const void* data, const void* x0,
                         const pat_fista_opts* opts, void* x_out, pat_fista_report* report, pat_iter_callback cb,
                         void* cb_ctx, void* stream) {
     set_error("");
-    if (!fine || !data || !x0 || !opts || !x_out) {
+    if (!fine || !opts) {
         set_error("NULL argument");
         return PAT_EINVAL;
     }
-    if (!(opts->L > 0.0) || (coarse && opts->recursion && !(opts->L_coarse > 0.0)) || opts->max_iter < 0 ||
-        !(opts->tv_rho > 0.0)) {
-        set_error("bad options (L, L_coarse, tv_rho must be > 0)");
+    if (coarse && opts->recursion && !(opts->L_coarse > 0.0)) {
+        set_error("bad options (L_coarse must be > 0)");
         return PAT_EINVAL;
     }
-    if (coarse && (coarse->impl->info.precision != fine->impl->info.precision ||
-                   coarse->impl->info.Ns != fine->impl->info.Ns ||
-                   coarse->impl->info.Nt != (fine->impl->info.Nt + 1) / 2)) {
-        set_error("coarse plan does not match the fine plan (use pat_plan_create_coarse)");
-        return PAT_EINVAL;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    if (fine->impl->info.precision == PAT_F32)
-        return Driver<float>::run(fine, coarse, (const float*)data, (const float*)x0, opts, (float*)x_out, report, cb,
-                                  cb_ctx, s);
-    return Driver<double>::run(fine, coarse, (const double*)data, (const double*)x0, opts, (double*)x_out, report, cb,
-                               cb_ctx, s);
+    pat_plan* lv[2] = {fine, coarse};
+    const double Ls[2] = {opts->L, opts->L_coarse};
+    return pat_mg_fista_levels(lv, coarse ? 2 : 1, Ls, data, x0, opts, x_out, report, cb, cb_ctx, stream);
 }
 
 }  // extern "C"

@@ -274,7 +274,7 @@ __global__ void k_prolong(ImgDims F, ImgDims C, const T* xc, T* xf, T alpha, T b
 
 // phi_i = (R y)_i - min over fine {2i-1, 2i, 2i+1}^d (clamped) of y  (Sec. V.C)
 template <typename T>
-__global__ void k_coarse_bound(ImgDims F, ImgDims C, const T* y, const T* Ry, T* phi) {
+__global__ void k_coarse_bound(ImgDims F, ImgDims C, const T* y, const T* Ry, const T* b, T* phi) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < C.N; i += (long long)gridDim.x * blockDim.x) {
         int c[3];
         unflat(i, C, c);
@@ -286,7 +286,8 @@ __global__ void k_coarse_bound(ImgDims F, ImgDims C, const T* y, const T* Ry, T*
                     const int fx = min(max(2 * c[0] + dx, 0), F.n[0] - 1);
                     const int fy = min(max(2 * c[1] + dy, 0), F.n[1] - 1);
                     const int fz = (C.d == 3) ? min(max(2 * c[2] + dz, 0), F.n[2] - 1) : 0;
-                    m = fmin(m, y[fx + F.s[1] * fy + F.s[2] * fz]);
+                    const long long f = fx + F.s[1] * fy + F.s[2] * fz;
+                    m = fmin(m, b ? y[f] - b[f] : y[f]);
                 }
         phi[i] = Ry[i] - m;
     }
@@ -425,10 +426,10 @@ pat_status Ops<T>::prolong(const pat_grid* fine, const T* xc, T* xf, double alph
 }
 
 template <typename T>
-pat_status Ops<T>::coarse_bound(const pat_grid* fine, const T* y, T* phi, T* tmp, cudaStream_t s) {
+pat_status Ops<T>::coarse_bound(const pat_grid* fine, const T* y, T* phi, T* tmp, cudaStream_t s, const T* b) {
     const ImgDims F = img_dims(*fine), C = img_dims(coarse_of(*fine));
     k_restrict<T><<<grid_for(C.N), 256, 0, s>>>(F, C, y, tmp);
-    k_coarse_bound<T><<<grid_for(C.N), 256, 0, s>>>(F, C, y, tmp, phi);
+    k_coarse_bound<T><<<grid_for(C.N), 256, 0, s>>>(F, C, y, tmp, b, phi);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PAT_OK : cuda_fail(e, "coarse bound");
 }

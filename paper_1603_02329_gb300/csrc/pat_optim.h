@@ -20,7 +20,9 @@ template <typename T> struct Ops {
     static pat_status restrict_(const pat_grid* fine, const T* xf, T* xc, cudaStream_t s);
     // xf = beta xf + alpha P xc
     static pat_status prolong(const pat_grid* fine, const T* xc, T* xf, double alpha, double beta, cudaStream_t s);
-    static pat_status coarse_bound(const pat_grid* fine, const T* y, T* phi, T* tmp, cudaStream_t s);
+    // phi = R y - min over the fine neighbourhood of y (of y - b when a fine bound b is given)
+    static pat_status coarse_bound(const pat_grid* fine, const T* y, T* phi, T* tmp, cudaStream_t s,
+                                   const T* b = nullptr);
     // out = a x + b y + c w, then max(lower, .) or max(0, .) if nonneg
     static pat_status lincomb(long long n, T* out, double a, const T* x, double b, const T* y, double c, const T* w,
                               const T* lower, int nonneg, cudaStream_t s);

@@ -137,6 +137,50 @@ def test_mg_fista_f32_close_to_oracle(dev):
     assert rep["iters"] == 5 and rep["fwd_solves"] >= 6
 
 
+@pytest.mark.parametrize("q_c", [8, 1])
+def test_mg_fista_three_levels_match_oracle_f64(dev, q_c):
+    # pat_mg_fista_levels on three levels (reading O12) against the oracle, iterate by iterate; with
+    # q_c = 1 the middle level never recurses and the run equals the two-level one
+    from paper_1603_02329_gb300.api import mg_fista
+
+    pb, ref, phat, L, lev1, op, opc = _mg_setup(dev, "f64")
+    p1 = po.coarse_problem(pb)
+    ref2, Nt2 = po.coarse_operator(p1)
+    L2 = po.power_iteration(lambda v: ref2.adjoint(ref2.forward(v)), ref2.shape, n_iter=15, seed=3)
+    lev2 = (ref2, lev1[1][::2][:Nt2], L2)
+    opc2 = opc.coarse()
+    assert opc2.shape == ref2.shape and opc2.Nt == Nt2
+    oo = po.FistaOpts(variant=1, max_iter=6, eps_d=-1.0, q_c=q_c, kappa=0.25)
+    x_ref, recs = po.mg_fista(ref, phat, np.zeros(pb.shape), L, oo, coarse=[lev1, lev2], p_exact=pb.p0)
+    x, rep, grecs = mg_fista(op, [opc, opc2], T(phat, dev), T(np.zeros(pb.shape), dev), L,
+                             L_coarse=[lev1[2], L2], p_exact=T(pb.p0, dev), max_iter=6, eps_d=-1.0, q_c=q_c,
+                             kappa=0.25)
+    assert [r["branch"] for r in grecs] == [r.branch for r in recs]
+    assert any(r.branch == "recursive" for r in recs)
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
+    for a, b in zip(grecs, recs):
+        assert abs(a["F"] - b.F) <= 1e-9 * abs(b.F)
+    assert x.cpu().numpy().min() >= -1e-12
+    if q_c == 1:
+        x2, _, _ = mg_fista(op, opc, T(phat, dev), T(np.zeros(pb.shape), dev), L, L_coarse=lev1[2],
+                            p_exact=T(pb.p0, dev), max_iter=6, eps_d=-1.0, q_c=1, kappa=0.25)
+        assert torch.equal(x, x2)
+
+
+def test_mg_fista_levels_argument_checks(dev):
+    from paper_1603_02329_gb300 import _lib
+    from paper_1603_02329_gb300.api import mg_fista
+
+    pb, ref, phat, L, lev1, op, opc = _mg_setup(dev, "f64")
+    with pytest.raises(Exception):   # a level that is not the coarse level of the one above
+        mg_fista(op, [opc, opc], T(phat, dev), T(np.zeros(pb.shape), dev), L, L_coarse=[1.0, 1.0], max_iter=2)
+    with pytest.raises(Exception):   # L of a level the recursion uses
+        mg_fista(op, [opc, opc.coarse()], T(phat, dev), T(np.zeros(pb.shape), dev), L, L_coarse=[1.0, 0.0],
+                 max_iter=2)
+    assert _lib.lib().pat_mg_fista_levels(None, 0, None, None, None, None, None, None, _lib.ITER_CB(0), None,
+                                          None) != 0
+
+
 def test_coarse_plan_with_edge_line_sensors(dev):
     from paper_1603_02329_gb300.api import PATOperator
 

@@ -111,7 +111,7 @@ template <typename T> struct PersistSm {
     int nx, rmax;
     TraceRef tr;
     const unsigned* kb;   // barriers passed so far
-    __device__ T* row(int j) const { return res + (size_t)j * rmax * nx; }
+    __device__ T* row(int j) const { return res + j * rmax * nx; }
     // sub-phase mark j (call after a __syncthreads): time of the CTA reaching this point
     __device__ void mark(int j) const {
         if (!tr.buf || threadIdx.x != 0) return;

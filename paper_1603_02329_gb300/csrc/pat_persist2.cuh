@@ -33,8 +33,9 @@ __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
 // beyond whole lines (p2_field_pad), so that the lane pairs of the fused stages, which touch the
 // same element of two fields, hit different banks.
 // lp > 0 adds lp elements after every line as well (kernels whose lanes step across lines).
-template <typename T> __device__ __forceinline__ size_t lbase(int q, int n, int lgnl, int lp = 0) {
-    return (size_t)q * (n + lp) + (size_t)(q >> lgnl) * p2_field_pad<T>();
+// (shared-memory offsets: 32-bit)
+template <typename T> __device__ __forceinline__ int lbase(int q, int n, int lgnl, int lp = 0) {
+    return q * (n + lp) + (q >> lgnl) * p2_field_pad<T>();
 }
 template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
 
@@ -136,7 +137,7 @@ __device__ void p2_row_in(cplx<T>* dst, const cplx<T>* S, int FI, int np, int lg
     for (int t = threadIdx.x; t < ((FI * np) << lgm); t += blockDim.x) {
         const int q = t >> lgm, j = t & (m - 1);
         const int f = q / np, p = q - f * np;
-        const cplx<T>* a = S + (size_t)(f * 2 * np + 2 * p) * ldh;
+        const cplx<T>* a = S + (f * 2 * np + 2 * p) * ldh;
         const cplx<T>* b = a + ldh;
         cplx<T> A[8], B[8];
 #pragma unroll
@@ -303,10 +304,10 @@ __device__ __forceinline__ void p2_col_stage(cplx<T>* S, cplx<T>* const* spec, i
         constexpr int EPC = 16 / (int)sizeof(cplx<T>);
         for (int f = 0; f < FI; ++f) {
             const cplx<T>* src = spec[f] + kx0;
-            cplx<T>* d = S + (size_t)f * ny * W;
+            cplx<T>* d = S + f * ny * W;
             for (int t = threadIdx.x; t < ny * cpr; t += blockDim.x) {
                 const int i = t / cpr, ch = t - i * cpr;
-                cp_async<16>(d + (size_t)i * W + ch * EPC, src + (size_t)i * ldh + ch * EPC);
+                cp_async<16>(d + i * W + ch * EPC, src + (size_t)i * ldh + ch * EPC);
             }
         }
         cp_commit();

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     T* res = reinterpret_cast<T*>(gb + Lo.gb);
     T* pmlx = res + Lo.res;
     T* pmlr = pmlx + nx;
-    auto row = [&](int k) { return res + (size_t)k * R * nx; };
+    auto row = [&](int k) { return res + k * R * nx; };
     const auto ax = P2Sel<LG>::make(P.fx.lgn);
     const T dt = P.dt;
     const bool lossy = P.lossy != 0;

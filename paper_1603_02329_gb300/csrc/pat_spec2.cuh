@@ -165,13 +165,13 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     const int cb = W * (int)sizeof(cplx<T>);
     for (int f = 0; f < fin; ++f) {
         const cplx<T>* src = P.spec[f] + base;
-        cplx<T>* d = B + (size_t)f * L * W;
+        cplx<T>* d = B + f * L * W;
         if (cb >= 16) {
             constexpr int EPC = 16 / (int)sizeof(cplx<T>);
             const int cpr = cb / 16, lgc = lgW - (EPC == 2 ? 1 : 0);   // 16-byte pieces per row: 2^lgc
             for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
                 const int i = t >> lgc, ch = t & (cpr - 1);
-                cp_async<16>(d + (size_t)i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
+                cp_async<16>(d + i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
             }
         } else {
             for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async<sizeof(cplx<T>)>(d + i, src + (size_t)i * es);

@@ -113,12 +113,12 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from
 # ncu captures of the same command with the time axis cut to Nt = 20 and Nt = 40: the two agree
-# (forward 8.26 / 8.20 MB, adjoint 6.64 / 6.64 MB; the state stays in shared memory, so the traffic
+# (forward 8.25 / 8.26 MB, adjoint 6.60 / 6.72 MB; the state stays in shared memory, so the traffic
 # is the set-up loads of the medium and tables), so the figure is taken as the full-length launch's.
 # Valid for the kernel version the captures were taken of (the 512^2 fixed-size k_persist2).
 MEASURED_TRAFFIC = {
-    ("vessel2d_512", "k_persist2_adj"): 6.64e6,
-    ("vessel2d_512", "k_persist2_fwd"): 8.23e6,
+    ("vessel2d_512", "k_persist2_adj"): 6.66e6,
+    ("vessel2d_512", "k_persist2_fwd"): 8.26e6,
 }
 
 

@@ -105,3 +105,9 @@ def test_host_side_argument_validation(L):
     assert L.pat_forward_plan(None, None, None, None) == PAT_EINVAL
     assert L.pat_adjoint(None, None, None, None) == PAT_EINVAL
     assert L.pat_plan_destroy(None) == 0
+    # multi-level MG-FISTA: NULL levels, nlevels outside 1 .. 8 (checked before any device work)
+    from paper_1603_02329_gb300._lib import ITER_CB
+
+    assert L.pat_mg_fista_levels(None, 2, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL
+    assert "nlevels" in L.pat_last_error().decode()
+    assert L.pat_mg_fista(None, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL

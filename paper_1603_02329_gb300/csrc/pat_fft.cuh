@@ -97,6 +97,35 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cplx<T>* v)
     v[7] = csub(e3, w3o3);
 }
 
+// 16 points: even / odd split into two 8-point DFTs, X[k] = E[k] + W16^k O[k], X[k+8] = E[k] -
+// W16^k O[k]; W16^k = exp(-+2 pi i k / 16) from cos(pi/8), sin(pi/8) and sqrt(1/2)
+template <typename T, bool INV> __device__ __forceinline__ void dft16(cplx<T>* v) {
+    cplx<T> e[8], o[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        e[r] = v[2 * r];
+        o[r] = v[2 * r + 1];
+    }
+    dft8<T, INV>(e);
+    dft8<T, INV>(o);
+    const T c1 = (T)0.9238795325112867561282, s1 = (T)0.3826834323650897717285, h = (T)0.7071067811865475244008;
+    // forward twiddles (cos, -sin) of 2 pi k / 16, k = 0..7; the inverse takes the conjugates
+    const T wc[8] = {(T)1, c1, h, s1, (T)0, -s1, -h, -c1};
+    const T ws[8] = {(T)0, s1, h, c1, (T)1, c1, h, s1};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cplx<T> t;
+        if (k == 0) t = o[0];
+        else if (k == 4) t = rot90<T, INV>(o[4]);
+        else {
+            const T sn = INV ? ws[k] : -ws[k];
+            t = mkc<T>(o[k].x * wc[k] - o[k].y * sn, o[k].x * sn + o[k].y * wc[k]);
+        }
+        v[k] = cadd(e[k], t);
+        v[k + 8] = csub(e[k], t);
+    }
+}
+
 // odd radix R = 3, 5, 7 by the symmetric pairing X_k = A_k -+ i B_k, X_{R-k} = A_k +- i B_k
 template <typename T, int R, bool INV> __device__ __forceinline__ void dft_odd(cplx<T>* v) {
     constexpr int H = (R - 1) / 2;
@@ -141,6 +170,7 @@ template <typename T, int R, bool INV> __device__ __forceinline__ void dft(cplx<
     if constexpr (R == 2) dft2<T, INV>(v);
     else if constexpr (R == 4) dft4<T, INV>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 8) dft8<T, INV>(v);
+    else if constexpr (R == 16) dft16<T, INV>(v);
     else dft_odd<T, R, INV>(v);
 }
 

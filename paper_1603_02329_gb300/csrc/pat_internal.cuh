@@ -121,6 +121,11 @@ template <typename T> struct DevPlan {
     // nullptr where the axis is not a power of two of 16 .. 2048 points)
     const cplx<T>* stw[3];
     int fixed_len;    // 1: launch the kernels compiled for this plan's line lengths where they exist
+    // per-stage twiddle tables of the two-stage schedule of 128- and 256-point lines (radices n/16
+    // and 16; p2x_stage_table), nullptr elsewhere; spec16: which 3-D spectral passes use it
+    // (0 none, 1 the plain transforms, 2 the fused multiply passes as well)
+    const cplx<T>* stw16[3];
+    int spec16;
 
     // state and workspaces (N each unless noted)
     T* u[3];

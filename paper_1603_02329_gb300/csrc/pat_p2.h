@@ -161,6 +161,19 @@ cudaError_t p2_launch(bool adjoint, const cudaLaunchConfig_t* lc, const DevPlan<
                       unsigned* gbar);
 template <typename T> const void* p2_kernel(bool adjoint, int lgx, int lgy, int fixed_len);
 
+// Stage tables of the two-stage schedule of an n = R1 x 16 point axis (n = 128 or 256; forward
+// radices R1, 16; inverse 16, R1): the forward radix-16 stage (span R1) [15][R1] at 0, then the
+// inverse radix-R1 stage (span 16) [R1 - 1][16]; entry (r, k) is tw[r k] in both (a gather).
+inline std::vector<std::complex<double>> p2x_stage_table(const std::vector<std::complex<double>>& tw, int lg) {
+    const int n = 1 << lg, R1 = n / 16;
+    std::vector<std::complex<double>> t((size_t)p2_tab_len(n), std::complex<double>(0.0, 0.0));
+    for (int r = 1; r < 16; ++r)
+        for (int k = 0; k < R1; ++k) t[(size_t)(r - 1) * R1 + k] = tw[(size_t)r * k];
+    for (int r = 1; r < R1; ++r)
+        for (int k = 0; k < 16; ++k) t[(size_t)15 * R1 + (r - 1) * 16 + k] = tw[(size_t)r * k];
+    return t;
+}
+
 // ---- kernels compiled for fixed lengths (float fields) ----
 // The 2-D persistent kernel for 256^2 and 512^2 grids, and the 3-D spectral and row kernels for
 // lines of 64, 128 and 256 points; a plan takes them unless it was created with PAT_P2SPEC=0

@@ -37,7 +37,7 @@ __device__ __forceinline__ int swz(int e) { return e ^ ((e >> 3) & 15); }
 template <typename T> __device__ __forceinline__ int lbase(int q, int n, int lgnl, int lp = 0) {
     return q * (n + lp) + (q >> lgnl) * p2_field_pad<T>();
 }
-template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : 3); };
+template <int R> struct Lg2 { static constexpr int v = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4)); };
 
 // The swizzle is linear over XOR: swz(a ^ b) = swz(a) ^ swz(b).  Element j + r m of a butterfly
 // (j < m, m a power of two) is j ^ (r m), and an output b + r Ns of a Stockham store is b ^ (r Ns)

@@ -1,12 +1,26 @@
 // pat_spec2_f32_n256.cu -- the 3-D power-of-two spectral kernels compiled for lines of 256 points,
-// float fields.
-#include "pat_spec2.cuh"
+// float fields: the two-stage schedule (k_spec16, radices 16 and 16) for the plain transforms, the
+// fixed schedule of k_spec2 for the fused multiply passes (DevPlan::spec16 selects).
+#include "pat_spec16.cuh"
 
 namespace pat {
 
 template <>
 cudaError_t spec2_launch_f32_3d<8>(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P, int W, int lgW,
                                     int lax, int F) {
+    const bool plain = (mode == SPEC_PLAIN_FWD || mode == SPEC_PLAIN_INV);
+    if (P.stw16[lax] && (P.spec16 >= 2 || (P.spec16 == 1 && plain))) {
+        switch (mode) {
+            case SPEC_PLAIN_FWD: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_PLAIN_FWD, 8>, P, W, lgW, lax, F);
+            case SPEC_PLAIN_INV: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_PLAIN_INV, 8>, P, W, lgW, lax, F);
+            case SPEC_GRAD: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_GRAD, 8>, P, W, lgW, lax, F);
+            case SPEC_DIV: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_DIV, 8>, P, W, lgW, lax, F);
+            case SPEC_ABS: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_ABS, 8>, P, W, lgW, lax, F);
+            case SPEC_DIVT: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_DIVT, 8>, P, W, lgW, lax, F);
+            case SPEC_GRADT: return cudaLaunchKernelEx(lc, k_spec16<float, 3, SPEC_GRADT, 8>, P, W, lgW, lax, F);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (mode) {
         case SPEC_PLAIN_FWD: return cudaLaunchKernelEx(lc, k_spec2<float, 3, SPEC_PLAIN_FWD, 8>, P, W, lgW, lax, F);
         case SPEC_PLAIN_INV: return cudaLaunchKernelEx(lc, k_spec2<float, 3, SPEC_PLAIN_INV, 8>, P, W, lgW, lax, F);
@@ -22,12 +36,19 @@ cudaError_t spec2_launch_f32_3d<8>(const cudaLaunchConfig_t* lc, int mode, const
 template <> cudaError_t spec2_set_attrs_f32_3d<8>(int bytes) {
     const void* ks[] = {
         (const void*)k_spec2<float, 3, SPEC_PLAIN_FWD, 8>,
+        (const void*)k_spec16<float, 3, SPEC_PLAIN_FWD, 8>,
         (const void*)k_spec2<float, 3, SPEC_PLAIN_INV, 8>,
+        (const void*)k_spec16<float, 3, SPEC_PLAIN_INV, 8>,
         (const void*)k_spec2<float, 3, SPEC_GRAD, 8>,
+        (const void*)k_spec16<float, 3, SPEC_GRAD, 8>,
         (const void*)k_spec2<float, 3, SPEC_DIV, 8>,
+        (const void*)k_spec16<float, 3, SPEC_DIV, 8>,
         (const void*)k_spec2<float, 3, SPEC_ABS, 8>,
+        (const void*)k_spec16<float, 3, SPEC_ABS, 8>,
         (const void*)k_spec2<float, 3, SPEC_DIVT, 8>,
+        (const void*)k_spec16<float, 3, SPEC_DIVT, 8>,
         (const void*)k_spec2<float, 3, SPEC_GRADT, 8>,
+        (const void*)k_spec16<float, 3, SPEC_GRADT, 8>,
     };
     for (const void* k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

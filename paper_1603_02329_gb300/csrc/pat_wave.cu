@@ -154,7 +154,14 @@ template <typename T> struct Plan : public PlanBase {
                 P.stw[a] = nullptr;
                 if (a < D && fa[a]->pow2 && fa[a]->lgn >= 4 && fa[a]->lgn <= 11)
                     CHK(P.stw[a] = upload_c(p2_stage_table(h.tw[a], fa[a]->lgn), &st));
+                P.stw16[a] = nullptr;
+                if (D == 3 && a >= 1 && fa[a]->pow2 && (fa[a]->lgn == 7 || fa[a]->lgn == 8))
+                    CHK(P.stw16[a] = upload_c(p2x_stage_table(h.tw[a], fa[a]->lgn), &st));
             }
+            // 1 (default): the plain y passes take the two-stage schedule; 2: the fused multiply
+            // passes too (measured slower at 256^3); 0: neither
+            const char* e16 = std::getenv("PAT_SPEC16");
+            P.spec16 = e16 ? std::max(0, std::min(2, std::atoi(e16))) : 1;
         }
         for (int a = 0; a < 3; ++a) {
             if (a < D) {

@@ -415,6 +415,35 @@ def test_fixed_length_kernels_match_generic_and_oracle(dev, monkeypatch, name, k
     assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
 
 
+# 3-D lines of 128 and 256 points: the plain y transforms take the two-stage spectral schedule
+# (k_spec16: radices n/16 and 16); PAT_SPEC16=2 puts the fused multiply passes on it as well, 0
+# none (the fixed-length k_spec2, radices r0, 8, 8).  All against the oracle and each other.
+SPEC16_CASES = [
+    ("3d_128x32x16_lossy", dict(shape=(128, 32, 16), pml=3, Nt=24)),       # z 128 (8 x 16), y 32
+    ("3d_16x256x32_lossless", dict(shape=(16, 256, 32), pml=3, Nt=20, alpha0=0.0)),   # y 256 (16 x 16)
+]
+
+
+@pytest.mark.parametrize("name,kw", SPEC16_CASES, ids=[c[0] for c in SPEC16_CASES])
+def test_two_stage_spectral_schedule_matches_oracle(dev, monkeypatch, name, kw):
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(37).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    out = []
+    for flag in ("2", "1", "0"):   # every pass / the plain transforms / none on the two-stage schedule
+        monkeypatch.setenv("PAT_SPEC16", flag)
+        op = _gpu_op(pb, "f32", dev)
+        d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+        g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+        assert rel(d, d_ref) <= TOL32, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= TOL32, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    for a in out[:2]:
+        assert rel(a[0], out[2][0]) <= 1e-6 and rel(a[1], out[2][1]) <= 1e-6
+
+
 # Power-of-two y (and z) axes take the register-fused spectral kernel of the per-phase path
 # (k_spec2); PAT_SPEC2=0 selects the generic one.  3-D grids (always the per-phase path) and a
 # 2-D grid forced onto it; radix schedules 16 = 2.8, 32 = 4.8, 64 = 8.8, 128 = 2.8.8.

@@ -185,9 +185,34 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def dist_env():
+    """(world size, rank, local rank) from the launcher's environment (torchrun sets all three)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, dev=None):
+    """The largest x over all ranks (the slowest rank's time), by an all-reduce MAX; x itself on one
+    rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gpts(pt_steps_per_rank, world, total_s):
+    """Whole-job throughput: the grid-point-steps every rank processed (the same fixed work per rank,
+    weak scaling) over the slowest rank's time, in Gpt-steps/s."""
+    return pt_steps_per_rank * world / total_s / 1e9
+
+
 def run_reference(args):
     """FP64 CPU oracle, timed as it stands on the host cores, on a bounded sample of the workload."""
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = dist_env()
     if rank != 0:
         return
     from oracle.pat_oracle import Operator
@@ -414,9 +439,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -479,13 +502,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    units = 2.0 * pb.N * pb.Nt * args.steps * world
-    value = units / total_s / 1e9
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    units_rank = 2.0 * pb.N * pb.Nt * args.steps
+    value = aggregate_gpts(units_rank, world, total_s)
 
     # e2e: the same step through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -505,13 +524,11 @@ def main():
             op.adjoint(dh, out=gh, stream=stream)
             torch.cuda.synchronize()
             t_e2e += time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, world, dev)
         nb_in = pb.N * w + pb.Nt * op.Ns * w       # p0 for H, residual for H^T
         nb_out = pb.Nt * op.Ns * w + pb.N * w      # data from H, gradient from H^T
-        e2e = {"value": units / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb_in, "d2h_bytes_per_step": nb_out}
+        e2e = {"value": aggregate_gpts(units_rank, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": nb_in,
+               "d2h_bytes_per_step": nb_out}
 
     # roofline of the dominant kernel (largest share of the probed step time)
     peak, peak_kind = measured_peaks()

@@ -310,7 +310,7 @@ template <typename T> struct Plan : public PlanBase {
                 }
             }
         }
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = take_launch_err();
         if (e != cudaSuccess) return cuda_fail(e, "autotune (per-phase kernels)");
         cfg = best;
         row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
@@ -550,7 +550,7 @@ template <typename T> struct Plan : public PlanBase {
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             lc.attrs = attr;
             lc.numAttrs = 1;
-            row2_launch<T>(&lc, D, kind, Q, R, flag, data_row, h_row, qrow, gc2, p0c);
+            note_launch(row2_launch<T>(&lc, D, kind, Q, R, flag, data_row, h_row, qrow, gc2, p0c));
             return;
         }
         switch (kind) {
@@ -572,6 +572,19 @@ template <typename T> struct Plan : public PlanBase {
     // launch helpers (used while capturing, or directly on a stream)
     // ---------------------------------------------------------------------------------------
     int row_grid() const { return P.nlines / cfg.row_lines; }
+
+    // The launchers of the power-of-two kernels return an error without touching CUDA's last-error
+    // state when they have no kernel for the request; the first such error is kept here and
+    // reported where the launches are checked (capture, direct runs).
+    cudaError_t launch_err = cudaSuccess;
+    void note_launch(cudaError_t e) {
+        if (e != cudaSuccess && launch_err == cudaSuccess) launch_err = e;
+    }
+    cudaError_t take_launch_err() {
+        const cudaError_t e = launch_err;
+        launch_err = cudaSuccess;
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
 
     // Every kernel is launched with programmatic stream serialization: it may start (and run
     // its constant-data prologue) while its predecessor finishes; griddepcontrol.wait in the
@@ -609,7 +622,7 @@ template <typename T> struct Plan : public PlanBase {
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             lc.attrs = attr;
             lc.numAttrs = 1;
-            spec2_launch<T>(&lc, D, MODE, Q, cfg.col_w, lgw, lax, F);
+            note_launch(spec2_launch<T>(&lc, D, MODE, Q, cfg.col_w, lgw, lax, F));
             return;
         }
         launch(k_spec<T, D, MODE>, dim3(tiles, outer), cfg.col_threads, spec_smem, s, Q, cfg.col_w, lgw, lax, F);
@@ -755,7 +768,7 @@ template <typename T> struct Plan : public PlanBase {
             for (int n = top; n > lo; --n) adj_step_on<D>(n, qbuf + (size_t)(n - lo - 1) * N, gc2, p0buf, s);
         }
         if (Nt > 1) adj_step_on<D>(0, nullptr, gc2, p0buf, s);
-        e = cudaGetLastError();
+        e = take_launch_err();
         if (e == cudaSuccess) e = cudaMemcpyAsync(gc2_out, gc2, N * sizeof(T), cudaMemcpyDefault, s);
         if (e == cudaSuccess && gp0_out) e = cudaMemcpyAsync(gp0_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
         release();
@@ -888,7 +901,7 @@ template <typename T> struct Plan : public PlanBase {
             if (adjoint) record_adjoint<3>(cap_stream);
             else record_forward<3>(cap_stream);
         }
-        cudaError_t le = cudaGetLastError();
+        cudaError_t le = take_launch_err();
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap_stream, &g);
         if (le != cudaSuccess) {
@@ -942,7 +955,7 @@ PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap,
 template <typename T> static pat_status run_direct_t(Plan<T>* p, cudaStream_t s) {
     if (p->P.d == 2) p->template record_forward<2>(s);
     else p->template record_forward<3>(s);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = p->take_launch_err();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PAT_OK;
 }

@@ -1,4 +1,5 @@
-"""Oracle: gradient of the forward map with respect to the squared sound speed c0^2 (FP64, CPU).
+"""Oracle: gradients of the forward map with respect to the squared sound speed c0^2 and the
+ambient density rho0 (FP64, CPU).
 
 TEST INFRASTRUCTURE.  Like the rest of ``oracle/``, this module is imported only by the tests,
 by the smoke check and by the CPU-baseline leg of the benchmark; the library never calls it.
@@ -150,3 +151,89 @@ def homogeneous_uniform_derivative(shape, spacing, c0, dt, Nt, p0, weights):
         dpn = np.real(np.fft.ifftn(-n * np.sin(n * w) * dw * P0))
         total += float(np.sum(weights[n] * dpn))
     return total
+
+
+# ---------------------------------------------------------------------------------------------
+# Gradient with respect to the ambient density rho0 (readings D1-D3)
+# ---------------------------------------------------------------------------------------------
+# D1  Held fixed: c0, alpha0, y, the reference speed (kappa, PML, dt) and p0; tau and eta depend on
+#     c0 and alpha0 only (Eq. (Twelve)), so the equation of state does not move.
+# D2  rho0 enters the discrete step in three places: b_xi = 2 / (rho0 + rho0 shifted by one point
+#     along xi) in the u update and in u^(-1/2) = dt/2 b D+ p0 (readings R4, R5); -dt rho0 e_xi in the
+#     density update; and dd = rho0 sum e_xi in the absorption term (Sec. II.A).
+# D3  Adjoint-state form, with the adjoint variables of Operator.adjoint: per step n,
+#         dJ/db_xi   += u_bar_xi^{n+1/2} (-dt au_xi g_xi^n),  g^n = D+ p^n,
+#         dJ/drho0   += sum_xi e_xi^n (dd_bar - dt a_xi rho_bar_xi^{n+1}),  e^n = D- u^{n+1/2},
+#     plus dJ/db_xi += u_bar_xi^{-1/2} dt/2 D+_xi p0 for the initial state; then through b_xi,
+#     db_xi[j] / drho0[j] = db_xi[j] / drho0[j+1] = -b_xi[j]^2 / 2.
+# Pins (tests/test_oracle_medium.py): central finite differences of J in random directions of
+# rho0 (2-D absorbing with PML, 2-D lossless, 3-D), and the scaling invariant: J(lambda rho0) =
+# J(rho0) for every lambda > 0 (u scales as 1/lambda, the density and the pressure do not move),
+# hence <dJ/drho0, rho0> = 0 for every medium.
+
+
+def forward_with_fields(op: Operator, p0):
+    """Forward solve of ``op`` returning (data, g, e) with g[n][xi] = D+_xi p^n and
+    e[n][xi] = D-_xi u_xi^{n+1/2} for the steps n = 0 .. Nt-2 (D3)."""
+    d, dt = op.d, op.dt
+    p = np.array(p0, dtype=float)
+    data = np.zeros((op.Nt, op.Ns))
+    G, E = [], []
+    rho = [p / (d * op.c2) for _ in range(d)]
+    u = [0.5 * dt * op.b[a] * op.Dplus(a, p) for a in range(d)]
+    data[0] = op.gather(p)
+    for n in range(op.Nt - 1):
+        g = [op.Dplus(a, p) for a in range(d)]
+        u = [op.au[a] * (op.au[a] * u[a] - dt * op.b[a] * g[a]) for a in range(d)]
+        e = [op.Dminus(a, u[a]) for a in range(d)]
+        rho = [op.a[a] * (op.a[a] * rho[a] - dt * op.rho0 * e[a]) for a in range(d)]
+        dd = op.rho0 * sum(e)
+        p = op.pressure(sum(rho), dd)
+        G.append(g)
+        E.append(e)
+        data[n + 1] = op.gather(p)
+    return data, G, E
+
+
+def density_gradient(op: Operator, p0, h):
+    """g = dJ/drho0, J = <H p0, h> (readings D1-D3)."""
+    d, dt = op.d, op.dt
+    h = np.asarray(h, dtype=float).reshape(op.Nt, op.Ns)
+    _, G, E = forward_with_fields(op, p0)
+    g_rho = np.zeros(op.shape)
+    g_b = [np.zeros(op.shape) for _ in range(d)]
+    pbar = op.scatter(h[op.Nt - 1])
+    ubar = [np.zeros(op.shape) for _ in range(d)]
+    rhobar = [np.zeros(op.shape) for _ in range(d)]
+    for n in range(op.Nt - 2, -1, -1):
+        rbar = op.c2 * pbar
+        ddbar = np.zeros(op.shape)
+        if op.lossy:
+            rbar = rbar - op.ks.apply(op.Ly1, op.c2eta * pbar)
+            ddbar = op.ks.apply(op.Ly2, op.c2tau * pbar)
+        ebar = []
+        for a in range(d):
+            rhobar[a] = rhobar[a] + rbar          # adjoint of rho_xi^{n+1}
+            g_rho += E[n][a] * (ddbar - dt * op.a[a] * rhobar[a])
+            ebar.append(op.rho0 * ddbar - dt * op.rho0 * op.a[a] * rhobar[a])
+            rhobar[a] = op.a[a] ** 2 * rhobar[a]
+        gbar = []
+        for a in range(d):
+            ubar[a] = ubar[a] - op.Dplus(a, ebar[a])   # adjoint of u_xi^{n+1/2}
+            g_b[a] += ubar[a] * (-dt * op.au[a] * G[n][a])
+            gbar.append(-dt * op.b[a] * op.au[a] * ubar[a])
+            ubar[a] = op.au[a] ** 2 * ubar[a]
+        pbar = -sum(op.Dminus(a, gbar[a]) for a in range(d)) + op.scatter(h[n])
+    p0 = np.asarray(p0, dtype=float)
+    for a in range(d):
+        g_b[a] += ubar[a] * (0.5 * dt * op.Dplus(a, p0))    # u^(-1/2) = dt/2 b D+ p0
+        B = g_b[a] * (-0.5 * op.b[a] ** 2)
+        g_rho += B + np.roll(B, 1, axis=a)                   # b_xi[j] depends on rho0[j], rho0[j+1]
+    return g_rho
+
+
+def density_objective(pb, rho, h):
+    """J(rho0) = <H_{rho0} p0, h> with everything else of ``pb`` fixed (D1)."""
+    op = Operator(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, pb.c, rho, pb.alpha0, pb.y, pb.dt, pb.Nt,
+                  sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index)
+    return float(np.sum(op.forward(pb.p0) * h))

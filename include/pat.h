@@ -301,9 +301,15 @@ pat_status pat_mg_fista_levels(pat_plan* const* levels, int nlevels, const doubl
                                const void* x0, const pat_fista_opts* opts, void* x_out, pat_fista_report* report,
                                pat_iter_callback cb, void* cb_ctx, void* stream);
 
-/* pat_plan_status -- synchronise the device and return the status word of the plan's last solve:
- * PAT_OK, or PAT_ETIMEOUT if a bounded device-side wait (the grid barrier of the persistent
- * kernel) ran out; the kernel then stopped early and its outputs are not valid. */
+/* pat_plan_status -- synchronise the device and return the status of the plan's last solve
+ * through pat_forward_plan or pat_adjoint:
+ *   PAT_OK;
+ *   PAT_ETIMEOUT if a bounded device-side wait (the grid barrier of the persistent kernel) ran out,
+ *     so the kernel stopped early and its outputs are not valid;
+ *   PAT_ENONFINITE if the solve's output (the data record after H, the image after H^T) holds a
+ *     NaN or an infinity.  A device-side scan of the output sets it after every solve. It is cleared
+ *     before the next one.
+ * pat_forward_static returns PAT_ENONFINITE directly. */
 pat_status pat_plan_status(pat_plan* plan);
 
 /* Kernel-timing probe (tracing).  With stride S > 0, the next captured graphs bracket every kernel

@@ -35,6 +35,9 @@ PlanBase* make_plan_f64(const HostTables& h, pat_status* st);
 pat_status plan_capture(PlanBase* base, bool adjoint);
 pat_status plan_capture_graph(PlanBase* base, bool adjoint, cudaGraph_t* out);
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s);
+// zero the plan's non-finite flag / scan the solve's output (data after H, image after H^T) into it
+pat_status plan_clear_finite(PlanBase* base, cudaStream_t s);
+pat_status plan_finite_check(PlanBase* base, bool adjoint, cudaStream_t s);
 pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s);
 pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void* gc2, void* gp0, int K,
                             cudaStream_t s);

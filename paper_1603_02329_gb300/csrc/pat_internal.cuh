@@ -198,6 +198,8 @@ struct PlanBase {
     int persist_grid = 0;
     size_t persist_smem = 0;
     unsigned* gbar = nullptr;
+    // non-finite check of the last solve's output: 0, or PAT_ENONFINITE (zeroed before each solve)
+    unsigned* fstat = nullptr;
     unsigned long long* trace = nullptr;
     int trace_k0 = 0, trace_nk = 0;
 };

@@ -434,6 +434,8 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
     const size_t ndat = (size_t)b->info.Nt * b->info.Ns * b->elem;
     cudaError_t e = cudaMemcpyAsync(b->img_ptr, p0, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy p0");
+    st = plan_clear_finite(b, s);
+    if (st != PAT_OK) return st;
     if (b->persistent) {
         st = plan_run_persistent(b, false, s);
         if (st != PAT_OK) return st;
@@ -441,6 +443,8 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
         e = cudaGraphLaunch(b->fwd_exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (forward)");
     }
+    st = plan_finite_check(b, false, s);
+    if (st != PAT_OK) return st;
     e = cudaMemcpyAsync(data, b->data_ptr, ndat, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy data");
     return PAT_OK;
@@ -458,6 +462,8 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
     const size_t ndat = (size_t)b->info.Nt * b->info.Ns * b->elem;
     cudaError_t e = cudaMemcpyAsync(b->data_ptr, residual, ndat, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy residual");
+    st = plan_clear_finite(b, s);
+    if (st != PAT_OK) return st;
     if (b->persistent) {
         st = plan_run_persistent(b, true, s);
         if (st != PAT_OK) return st;
@@ -465,6 +471,8 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
         e = cudaGraphLaunch(b->adj_exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (adjoint)");
     }
+    st = plan_finite_check(b, true, s);
+    if (st != PAT_OK) return st;
     e = cudaMemcpyAsync(grad, b->img_ptr, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy gradient");
     return PAT_OK;
@@ -527,13 +535,23 @@ pat_status pat_plan_status(pat_plan* plan) {
     DeviceGuard g(b->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    if (!b->gbar) return PAT_OK;
-    unsigned w[4] = {0, 0, 0, 0};
-    e = cudaMemcpy(w, b->gbar, sizeof(w), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "read status word");
-    if (w[2] != 0) {
-        set_error("a bounded device-side wait ran out (grid barrier of the persistent kernel)");
-        return (pat_status)w[2];
+    if (b->gbar) {
+        unsigned w[4] = {0, 0, 0, 0};
+        e = cudaMemcpy(w, b->gbar, sizeof(w), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read status word");
+        if (w[2] != 0) {
+            set_error("a bounded device-side wait ran out (grid barrier of the persistent kernel)");
+            return (pat_status)w[2];
+        }
+    }
+    if (b->fstat) {
+        unsigned f = 0;
+        e = cudaMemcpy(&f, b->fstat, sizeof(f), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read status word");
+        if (f != 0) {
+            set_error("the last solve's output holds NaN or infinite values");
+            return (pat_status)f;
+        }
     }
     return PAT_OK;
 }

@@ -72,13 +72,24 @@ extern "C" pat_status pat_forward_static(const void* p0, const double* c, const 
     const size_t ndat = (size_t)h.Nt * h.Ns * plan->elem;
     cudaError_t e = cudaMemcpyAsync(plan->img_ptr, p0, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) st = cuda_fail(e, "copy p0");
+    if (st == PAT_OK) st = plan_clear_finite(plan, s);
     if (st == PAT_OK) st = plan_forward_direct(plan, s);
+    if (st == PAT_OK) st = plan_finite_check(plan, false, s);
     if (st == PAT_OK) {
         e = cudaMemcpyAsync(data, plan->data_ptr, ndat, cudaMemcpyDefault, s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy data");
     }
     e = cudaStreamSynchronize(s);
     if (st == PAT_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    if (st == PAT_OK) {
+        unsigned f = 0;
+        e = cudaMemcpy(&f, plan->fstat, sizeof(f), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "read status word");
+        else if (f != 0) {
+            set_error("the data record holds NaN or infinite values");
+            st = (pat_status)f;
+        }
+    }
     delete plan;
     return st;
 }

@@ -183,6 +183,7 @@ template <typename T> struct Plan : public PlanBase {
         }
         CHK(P.img = dalloc<T>(N, &st));
         CHK(P.data = dalloc<T>((size_t)h.Nt * h.Ns, &st));
+        CHK(fstat = dalloc<unsigned>(1, &st));
         img_ptr = P.img;
         data_ptr = P.data;
         // sensors
@@ -1010,6 +1011,33 @@ pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_li
         p->P.bar_limit_ns = ns;
     }
     return PAT_OK;
+}
+
+// PAT_ENONFINITE into *flag if x[0 .. n) holds a NaN or an infinity
+template <typename T> __global__ void k_finite_check(const T* x, long long n, unsigned* flag) {
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, (unsigned)PAT_ENONFINITE);
+}
+
+template <typename T> static pat_status finite_check_t(PlanBase* b, bool adjoint, cudaStream_t s) {
+    const long long n = adjoint ? b->info.N : (long long)b->info.Nt * b->info.Ns;
+    const T* x = static_cast<const T*>(adjoint ? b->img_ptr : b->data_ptr);
+    const int grid = (int)std::min<long long>(1024, (n + 255) / 256);
+    k_finite_check<T><<<std::max(grid, 1), 256, 0, s>>>(x, n, b->fstat);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "non-finite check");
+}
+
+pat_status plan_clear_finite(PlanBase* b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->fstat, 0, sizeof(unsigned), s);
+    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaMemsetAsync (status)");
+}
+
+pat_status plan_finite_check(PlanBase* b, bool adjoint, cudaStream_t s) {
+    if (b->info.precision == PAT_F32) return finite_check_t<float>(b, adjoint, s);
+    return finite_check_t<double>(b, adjoint, s);
 }
 
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {

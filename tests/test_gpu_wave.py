@@ -444,6 +444,39 @@ def test_two_stage_spectral_schedule_matches_oracle(dev, monkeypatch, name, kw):
         assert rel(a[0], out[2][0]) <= 1e-6 and rel(a[1], out[2][1]) <= 1e-6
 
 
+@pytest.mark.parametrize("persist", ["1", "0"])
+def test_non_finite_output_is_reported(dev, monkeypatch, persist):
+    # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual
+    # (adjoint) spreads through the transforms; the device-side scan of the output records
+    # PAT_ENONFINITE, pat_plan_status reports it, and the next clean solve clears it.  NaN arithmetic
+    # changes no control flow in the kernels.
+    from paper_1603_02329_gb300 import _lib
+
+    monkeypatch.setenv("PAT_PERSIST", persist)
+    pb = synth.small_lossy_2d(shape=(64, 64), pml=8, Nt=30, n_sensors=12)
+    op = _gpu_op(pb, "f32", dev)
+    assert op.info.path == (2 if persist == "1" else 0)
+    L = _lib.lib()
+    x = np.array(pb.p0)
+    d = op.forward(_t(x, "f32", dev))
+    assert L.pat_plan_status(op._plan) == 0
+    x[20, 30] = np.nan
+    op.forward(_t(x, "f32", dev))
+    assert L.pat_plan_status(op._plan) == _lib.PAT_ENONFINITE
+    assert "NaN" in L.pat_last_error().decode()
+    d2 = op.forward(_t(pb.p0, "f32", dev))
+    assert L.pat_plan_status(op._plan) == 0
+    assert torch.equal(d, d2)
+    h = np.random.default_rng(3).standard_normal((pb.Nt, op.Ns))
+    h[5, 2] = np.inf
+    op.adjoint(_t(h, "f32", dev))
+    assert L.pat_plan_status(op._plan) == _lib.PAT_ENONFINITE
+    h[5, 2] = 0.0
+    op.adjoint(_t(h, "f32", dev))
+    assert L.pat_plan_status(op._plan) == 0
+    op.close()
+
+
 # Power-of-two y (and z) axes take the register-fused spectral kernel of the per-phase path
 # (k_spec2); PAT_SPEC2=0 selects the generic one.  3-D grids (always the per-phase path) and a
 # 2-D grid forced onto it; radix schedules 16 = 2.8, 32 = 4.8, 64 = 8.8, 128 = 2.8.8.

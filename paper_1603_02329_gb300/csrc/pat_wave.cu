@@ -646,7 +646,6 @@ template <typename T> struct Plan : public PlanBase {
     // ---------------------------------------------------------------------------------------
     // forward step n -> n + 1 on the state of Q; q^{n+1} = d p^{n+1} / d c0^2 into qrow
     template <int D> void fwd_step_on(const DevPlan<T>& Q, int n, T* data_row, T* qrow, cudaStream_t s) {
-        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         const int last = (n + 2 == H.Nt);
         spectral_on<D, SPEC_GRAD>(Q, s);
         row_launch<D>(R2_FWD_U, Q, s, (int)(n == 0));
@@ -660,7 +659,6 @@ template <typename T> struct Plan : public PlanBase {
     // adjoint iteration that produces p_bar^n (the reverse of forward step n), accumulating
     // g_c2 += p_bar^n q^n (n >= 1) or, at n = 0, the initial-density term
     template <int D> void adj_step_on(int n, const T* qrow, T* gc2, const T* p0c, cudaStream_t s) {
-        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         if (P.lossy) {
             spectral_on<D, SPEC_ABS>(P, s);
             row_launch<D>(R2_ADJ_RHO, P, s, 0);

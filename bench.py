@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
     ap.add_argument("--mg-iters", type=int, default=20)
     ap.add_argument("--mg-levels", type=int, default=2, help="levels of MG-FISTA (2 or 3)")
+    ap.add_argument("--mg-data", default="same", choices=["same", "refined"],
+                    help="MG comparison data: from the reconstruction grid (inverse crime, stated) or from "
+                         "a 1.44x finer grid with 35 dB-contaminated maps (synth.refined_problem)")
     ap.add_argument("--batch", action="store_true",
                     help="also time 8 uneven 2-D instances as one batched launch vs one at a time")
     ap.add_argument("--trace", type=int, default=0,
@@ -371,7 +374,17 @@ def mg_vs_fista(args, dev, pb):
     opc = op.coarse()
     opc2 = opc.coarse() if args.mg_levels >= 3 else None
     x_true = torch.tensor(pb.p0, dtype=torch.float32, device=dev)
-    clean = op.forward(x_true).cpu().numpy()
+    if args.mg_data == "refined":
+        # data from a finer grid with perturbed maps, sensors at the same positions (no inverse crime)
+        pf = synth.refined_problem(pb, ratio=1.44, map_snr_db=35.0, seed=5)
+        opf = PATOperator.from_problem(pf, precision="f32", device=dev)
+        clean = opf.forward(torch.tensor(pf.p0, dtype=torch.float32, device=dev)).cpu().numpy()
+        data_desc = (f"forward of the phantom on a {'x'.join(map(str, pf.shape))} grid with 35 dB-contaminated "
+                     "sound-speed and density maps, sensors at the same positions, + 40 dB AWGN")
+        opf.close()
+    else:
+        clean = op.forward(x_true).cpu().numpy()
+        data_desc = "forward of the phantom on the same grid + 40 dB AWGN (inverse crime, stated)"
     noisy = synth.awgn(np.random.default_rng(2), clean, 40.0)
     data = torch.tensor(noisy, dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
@@ -427,7 +440,7 @@ def mg_vs_fista(args, dev, pb):
             "mgfista_s": t_m, "mgfista_iters": hit[0]["k"] if hit else None,
             "mgfista_recursive_iters": sum(1 for r in recs_m if r["branch"] == "recursive"),
             "speedup": (t_f / t_m) if t_m else None, "setup_s_power_method": setup_s,
-            "data": "forward of the phantom on the same grid + 40 dB AWGN (inverse crime, stated)",
+            "data": data_desc,
             "params": dict(common, lam=1e-2, L=L, L_coarse=Lc, L_coarse2=Lc2)}
 
 

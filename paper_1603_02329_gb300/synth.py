@@ -276,6 +276,58 @@ def tube_phantom_3d(seed=3, n=128, pml=10, h=0.0625e-3, Nt=1000, alpha0=0.75, y=
                    sensor_index=idx.ravel().astype(np.int64), seed=seed)
 
 
+def smooth_even_size(n):
+    """The smallest even size >= n whose prime factors are 2, 3, 5 and 7 (the FFT radices)."""
+    m = int(n) + (int(n) % 2)
+    while True:
+        k = m
+        for f in (2, 3, 5, 7):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            return m
+        m += 2
+
+
+def refined_problem(pb, ratio=1.44, map_snr_db=35.0, seed=0):
+    """Data-generation problem for the reconstruction problem ``pb`` that avoids the inverse crime,
+    a stand-in for the data grid of Sec. VI.A (data on 472^2 for a 328^2 reconstruction, maps
+    contaminated with 35 dB AWGN):
+      - about ``ratio`` times as many points per axis over the same physical extent (even sizes with
+        factors 2, 3, 5, 7);
+      - the PML scaled by the ratio;
+      - sound speed, density, alpha0 and p0 linearly interpolated onto the finer grid (clamped at the
+        ends);
+      - the sound-speed and density maps contaminated with AWGN at ``map_snr_db`` (None: none);
+      - the sensors at the same physical positions (off-grid points);
+      - the same dt and Nt, so the data are directly comparable."""
+    rng = np.random.default_rng(seed)
+    d = pb.ndim
+    shape_f = tuple(smooth_even_size(round(n * ratio)) for n in pb.shape)
+    spacing_f = tuple(n * h / nf for n, h, nf in zip(pb.shape, pb.spacing, shape_f))
+    pml_f = tuple(int(round(p * nf / n)) for p, n, nf in zip(pb.pml, pb.shape, shape_f))
+    xc = coords(pb.shape, pb.spacing)
+    xf = coords(shape_f, spacing_f)
+
+    def interp(a):
+        a = np.broadcast_to(np.asarray(a, dtype=float), pb.shape)
+        for ax in range(d):
+            a = np.apply_along_axis(lambda v: np.interp(xf[ax], xc[ax], v), ax, a)
+        return np.ascontiguousarray(a)
+
+    c_f, rho_f = interp(pb.c), interp(pb.rho)
+    if map_snr_db is not None:
+        c_f = awgn(rng, c_f, map_snr_db)
+        rho_f = awgn(rng, rho_f, map_snr_db)
+    if pb.sensor_pos is not None:
+        pos = np.array(pb.sensor_pos, dtype=float)
+    else:
+        idx = np.unravel_index(np.asarray(pb.sensor_index), pb.shape)
+        pos = np.stack([xc[a][idx[a]] for a in range(d)][::-1], axis=1)   # (x, y[, z]) order
+    return Problem(f"{pb.name}_refined_{'x'.join(map(str, shape_f))}", shape_f, spacing_f, pml_f, pb.pml_alpha,
+                   c_f, rho_f, interp(pb.alpha0), pb.y, pb.dt, pb.Nt, interp(pb.p0), sensor_pos=pos, seed=seed)
+
+
 def random_residual(seed, Nt, Ns):
     """A seeded random data-space vector (adjoint input for dot tests)."""
     return np.random.default_rng(seed).standard_normal((Nt, Ns))

@@ -32,7 +32,7 @@ homogeneous lossless periodic medium, where p^n = F^-1{cos(n w_k) F p0} with
 """
 import numpy as np
 
-from .pat_oracle import Operator
+from .pat_oracle import Operator, smooth_image
 
 
 def operator_with_c_ref(pb, c, c_ref):
@@ -41,7 +41,7 @@ def operator_with_c_ref(pb, c, c_ref):
     from .pat_oracle import KSpace, pml_factors
 
     op = Operator(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, c, pb.rho, pb.alpha0, pb.y, pb.dt, pb.Nt,
-                  sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index)
+                  sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index, smooth=getattr(pb, "smooth", False))
     # rebuild the pieces that depend on the reference speed with the fixed one
 
     op.c_ref = float(c_ref)
@@ -92,6 +92,7 @@ def sound_speed_gradient(op: Operator, p0, h, y):
     the ordinary adjoint H^T h (the same sweep)."""
     d, dt = op.d, op.dt
     h = np.asarray(h, dtype=float).reshape(op.Nt, op.Ns)
+    p0 = op.initial_pressure(p0)      # S p0 when the smoothing of R9 is on (S does not depend on c0)
     _, q = forward_with_q(op, p0, y)
     g = np.zeros(op.shape)
     pbar = op.scatter(h[op.Nt - 1])
@@ -121,6 +122,8 @@ def sound_speed_gradient(op: Operator, p0, h, y):
     g += -np.asarray(p0, float) / (d * op.c2 * op.c2) * sum(rhobar)     # M3
     grad_p0 = pbar + sum(rhobar) / (d * op.c2)
     grad_p0 = grad_p0 - sum(op.Dminus(a, 0.5 * dt * op.b[a] * ubar[a]) for a in range(d))
+    if op.smooth:
+        grad_p0 = smooth_image(grad_p0, op.spacing)
     return g, grad_p0
 
 
@@ -199,6 +202,7 @@ def density_gradient(op: Operator, p0, h):
     """g = dJ/drho0, J = <H p0, h> (readings D1-D3)."""
     d, dt = op.d, op.dt
     h = np.asarray(h, dtype=float).reshape(op.Nt, op.Ns)
+    p0 = op.initial_pressure(p0)      # S p0 when the smoothing of R9 is on (S does not depend on rho0)
     _, G, E = forward_with_fields(op, p0)
     g_rho = np.zeros(op.shape)
     g_b = [np.zeros(op.shape) for _ in range(d)]
@@ -224,7 +228,6 @@ def density_gradient(op: Operator, p0, h):
             gbar.append(-dt * op.b[a] * op.au[a] * ubar[a])
             ubar[a] = op.au[a] ** 2 * ubar[a]
         pbar = -sum(op.Dminus(a, gbar[a]) for a in range(d)) + op.scatter(h[n])
-    p0 = np.asarray(p0, dtype=float)
     for a in range(d):
         g_b[a] += ubar[a] * (0.5 * dt * op.Dplus(a, p0))    # u^(-1/2) = dt/2 b D+ p0
         B = g_b[a] * (-0.5 * op.b[a] ** 2)
@@ -235,5 +238,5 @@ def density_gradient(op: Operator, p0, h):
 def density_objective(pb, rho, h):
     """J(rho0) = <H_{rho0} p0, h> with everything else of ``pb`` fixed (D1)."""
     op = Operator(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, pb.c, rho, pb.alpha0, pb.y, pb.dt, pb.Nt,
-                  sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index)
+                  sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index, smooth=getattr(pb, "smooth", False))
     return float(np.sum(op.forward(pb.p0) * h))

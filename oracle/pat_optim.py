@@ -25,7 +25,8 @@ O6  Coarse level: n/2 points, spacing 2h, PML/2 points, dt_c = 2 dt, Nt_c = ceil
     (Sec. V: the time step follows the spacing), medium decimated (c_c = c[::2, ::2]), sensors at
     the same physical positions, data decimated in time (p_hat_c = p_hat[::2]).  A position
     beyond the first or last coarse node (a fine sensor on the last fine index) is clamped onto
-    that node, as P clamps at the last index.
+    that node, as P clamps at the last index.  When the fine operator smooths p0 (reading R9 of
+    the forward oracle), the coarse one applies its own window, cut at its own Nyquist radius.
 O7  Coarse iteration: FISTA (or ISTA) on phi_{h-1} with projection on {x >= phi} (Sec. V.E),
     step 1 / L_c, L_c = w L(H_c^T H_c) + lambda 4 d / rho (w of O11); its own t-sequence from 1; stop when
     (phi_k - phi_{k+1}) / max(|phi_k|, |phi_{k+1}|) < eps_c or after q_c iterations (the paper's
@@ -273,7 +274,7 @@ def coarse_problem(pb):
         pos[:, d - 1 - a] = np.clip(pos[:, d - 1 - a], lo, hi)
     return types.SimpleNamespace(ndim=d, shape=shape_c, spacing=spacing_c, pml=pml_c, pml_alpha=pb.pml_alpha,
                                  c=c_c, rho=rho_c, alpha0=a_c, y=pb.y, dt=2.0 * pb.dt, Nt=Nt_c,
-                                 sensor_pos=pos, sensor_index=None)
+                                 sensor_pos=pos, sensor_index=None, smooth=getattr(pb, "smooth", False))
 
 
 def coarse_operator(pb):

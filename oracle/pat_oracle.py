@@ -43,6 +43,13 @@ R7  the adjoint is the exact transpose of R5-R6 (so <Hx, h> = <x, H^T h> to roun
     variant (Sec. VI) differs from the transpose by O(dt) and is not what is computed here.
 R8  off-grid sensors: multilinear interpolation weights from the physical position; on-grid
     sensors: weight 1 at the given flat index.
+R9  optional smoothing of the initial pressure (Sec. VI.A: the high frequencies of p0 are
+    filtered by a self-adjoint operator before every forward solve, and the filter is part of
+    the adjoint).  The paper names no filter.  Reading: S = F^-1 diag(W) F with the radial
+    Blackman window W(k) = B(|k| / k_c), B(q) = 0.42 + 0.5 cos(pi q) + 0.08 cos(2 pi q) for
+    q < 1 and 0 for q >= 1, k_c = min over axes of the Nyquist wavenumber pi / h.  W is real,
+    even in k and in [0, 1], so S is real, symmetric and non-expansive; the smoothed operator
+    is H S and its transpose S H^T.
 """
 from __future__ import annotations
 
@@ -94,6 +101,28 @@ class KSpace:
 
     def apply(self, symbol, f):
         return irfftn(symbol * rfftn(f), s=self.shape, axes=tuple(range(len(self.shape))))
+
+
+def smoothing_window(shape, spacing):
+    """W(k) of reading R9 on the rfftn layout: the radial Blackman window in |k| / k_c."""
+    d = len(shape)
+    ks = []
+    for a in range(d):
+        k1 = axis_wavenumbers(shape[a], spacing[a], half=(a == d - 1))
+        bshape = [1] * d
+        bshape[a] = -1
+        ks.append(k1.reshape(bshape))
+    k_c = min(np.pi / h for h in spacing)
+    q = np.sqrt(sum(k * k for k in ks)) / k_c
+    w = 0.42 + 0.5 * np.cos(np.pi * q) + 0.08 * np.cos(2.0 * np.pi * q)
+    return np.where(q < 1.0, w, 0.0)
+
+
+def smooth_image(x, spacing):
+    """S x of reading R9 (Sec. VI.A)."""
+    shape = np.shape(x)
+    W = smoothing_window(shape, spacing)
+    return irfftn(W * rfftn(x), s=shape, axes=tuple(range(len(shape))))
 
 
 # ---------------------------------------------------------------------------------------------
@@ -178,8 +207,9 @@ class Operator:
     """H: p0 -> s[Nt][Ns] and its transpose, in FP64 (Sec. III; readings R1-R8)."""
 
     def __init__(self, shape, spacing, pml, pml_alpha, c, rho, alpha0, y, dt, Nt,
-                 sensor_pos=None, sensor_index=None):
+                 sensor_pos=None, sensor_index=None, smooth=False):
         self.shape = tuple(int(n) for n in shape)
+        self.smooth = bool(smooth)
         self.d = len(self.shape)
         self.spacing = tuple(float(h) for h in spacing)
         self.dt = float(dt)
@@ -211,7 +241,12 @@ class Operator:
     @classmethod
     def from_problem(cls, pb, Nt=None):
         return cls(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, pb.c, pb.rho, pb.alpha0, pb.y, pb.dt,
-                   pb.Nt if Nt is None else Nt, sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index)
+                   pb.Nt if Nt is None else Nt, sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index,
+                   smooth=getattr(pb, "smooth", False))
+
+    def initial_pressure(self, p0):
+        """p^0 of R5: p0 itself, or S p0 when the smoothing of R9 is on."""
+        return smooth_image(p0, self.spacing) if self.smooth else np.array(p0, dtype=float)
 
     # -- building blocks -------------------------------------------------------------------
     def Dplus(self, a, f):
@@ -238,7 +273,7 @@ class Operator:
         """Returns data [Nt][Ns]; with ``keep_fields`` also the lists p^n (n = 0..Nt-1) and
         u^(n-1/2) (n = 0..Nt-1, i.e. u^(-1/2) .. u^(Nt-3/2)) for invariant checks."""
         d, dt = self.d, self.dt
-        p = np.array(p0, dtype=float)
+        p = self.initial_pressure(p0)
         data = np.zeros((self.Nt, self.Ns))
         rho = [p / (d * self.c2) for _ in range(d)]
         g = [self.Dplus(a, p) for a in range(d)]
@@ -295,7 +330,8 @@ class Operator:
         # initial state R5: p^0 = p0, rho^0 = p0/(d c2), u^(-1/2) = dt/2 b D+ p0
         grad = pbar + sum(rhobar) / (d * self.c2)
         grad = grad - sum(self.Dminus(a, 0.5 * dt * self.b[a] * ubar[a]) for a in range(d))
-        return grad
+        # R9: (H S)^T = S^T H^T = S H^T
+        return smooth_image(grad, self.spacing) if self.smooth else grad
 
     # -- objective pieces (Sec. IV, Eqs. (two), (Six)) ------------------------------------------
     def data_misfit(self, x, p_hat):

@@ -46,6 +46,7 @@ class Problem:
     sensor_pos: Optional[np.ndarray] = None    # [Ns][d] (x,y[,z]) metres, off-grid (linear interpolation)
     sensor_index: Optional[np.ndarray] = None  # [Ns] flat C-order indices, on-grid sensors
     seed: int = 0
+    smooth: bool = False    # filter p0 with the plan's self-adjoint smoothing before each solve
 
     @property
     def ndim(self) -> int:

@@ -9,13 +9,15 @@ shift, a transposed operand, a wrong unit conversion) fails at least one of them
 * the staggered derivative of a sine,
 * the physical decay rate and dispersion sign of a plane mode under power-law absorption,
 * linear interpolation reproduces linear fields; an on-node sensor reads the node value,
-* finite differences of the quadratic data misfit.
+* finite differences of the quadratic data misfit,
+* the smoothing of p0: window values on chosen Fourier modes, symmetry, the dot test with it on,
+* the continuum solution of a smooth radial pulse (d'Alembert in 3-D, Hankel quadrature in 2-D).
 """
 import numpy as np
 import pytest
 from numpy.fft import irfftn, rfftn
 
-from oracle.pat_oracle import Operator, sensor_matrix
+from oracle.pat_oracle import Operator, sensor_matrix, smooth_image
 from paper_1603_02329_gb300 import synth
 
 
@@ -90,15 +92,17 @@ def test_derivative_transpose_and_sine():
     assert np.max(np.abs(op.Dplus(1, s) - ref[None, :])) < 1e-9 * k0
 
 
-@pytest.mark.parametrize("case", ["lossy2d_offgrid", "lossy3d_ongrid", "lossless2d"])
+@pytest.mark.parametrize("case", ["lossy2d_offgrid", "lossy3d_ongrid", "lossless2d", "smooth2d", "smooth3d"])
 def test_adjoint_dot_product(case):
-    if case == "lossy2d_offgrid":
+    if case in ("lossy2d_offgrid", "smooth2d"):
         pb = synth.small_lossy_2d(shape=(32, 40), pml=6, Nt=40, n_sensors=12)
-    elif case == "lossy3d_ongrid":
+    elif case in ("lossy3d_ongrid", "smooth3d"):
         pb = synth.small_lossy_3d(shape=(12, 16, 20), pml=3, Nt=20)
     else:
         pb = synth.disc_phantom_2d(interior=24, pml=6, Nt=40, n_sensors=10, sensor_radius=1e-3)
+    pb.smooth = case.startswith("smooth")
     op = Operator.from_problem(pb)
+    assert op.smooth == pb.smooth
     rng = np.random.default_rng(4)
     x = rng.standard_normal(pb.shape)
     hh = rng.standard_normal((pb.Nt, op.Ns))
@@ -196,3 +200,106 @@ def test_pml_damps_outgoing_energy():
     e_pml = np.sum(with_pml.forward(p0)[-1] ** 2)
     e_per = np.sum(no_pml.forward(p0)[-1] ** 2)
     assert e_pml < 1e-2 * e_per
+
+
+# Blackman window B(q) at the radii where it has a short closed form: B(0) = 1,
+# B(1/3) = 0.42 + 0.5/2 - 0.08/2 = 0.63, B(1/2) = 0.42 - 0.08 = 0.34, B(q >= 1) = 0.
+# Grid (Ny, Nx) = (24, 32) with spacing (1e-4, 2e-4): the cut-off radius is the Nyquist
+# wavenumber of the coarser x axis, pi / 2e-4, so a mode (my, mx) sits at
+# q = sqrt((mx / 16)^2 + (my / 6)^2).  A y mode with my = 6 is cut although it lies at half the
+# y axis' own Nyquist wavenumber; a window cut at the finer axis would keep 0.34 of it.
+@pytest.mark.parametrize("my,mx,gain", [(0, 0, 1.0), (0, 8, 0.34), (3, 0, 0.34), (2, 0, 0.63), (6, 0, 0.0),
+                                        (0, 16, 0.0), (12, 0, 0.0), (3, 16, 0.0), (5, 10, 0.0)])
+def test_smoothing_window_on_fourier_modes(my, mx, gain):
+    ny, nx = 24, 32
+    spacing = (1e-4, 2e-4)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    f = np.cos(2 * np.pi * (mx * ii / nx + my * jj / ny) + 0.3)
+    assert np.max(np.abs(smooth_image(f, spacing) - gain * f)) < 1e-13
+
+
+def test_smoothing_window_3d_mode_and_symmetry():
+    # 3-D: a z mode at half the (common) Nyquist radius keeps 0.34 of its amplitude
+    shape = (8, 12, 16)
+    h = 1e-4
+    kk = np.arange(8)[:, None, None] * np.ones(shape)
+    f = np.sin(2 * np.pi * 2 * kk / 8 + 0.1)
+    assert np.max(np.abs(smooth_image(f, (h, h, h)) - 0.34 * f)) < 1e-13
+    # S is symmetric and non-expansive (0 <= W <= 1), on anisotropic 2-D and 3-D grids
+    rng = np.random.default_rng(11)
+    for shape, sp in (((20, 28), (1e-4, 1.5e-4)), ((8, 10, 12), (1e-4, 2e-4, 1e-4))):
+        x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+        Sx, Sy = smooth_image(x, sp), smooth_image(y, sp)
+        assert abs(np.sum(Sx * y) - np.sum(x * Sy)) < 1e-13 * np.linalg.norm(x) * np.linalg.norm(y)
+        assert np.linalg.norm(Sx) < np.linalg.norm(x)
+        assert np.sum(x * Sx) >= 0.0
+
+
+def test_smoothing_enters_forward_and_adjoint():
+    # H S p0 = H (S p0): the smoothed operator's record equals the plain one's on S p0, and its
+    # adjoint ends with S
+    pb = synth.small_lossy_2d(shape=(24, 28), pml=5, Nt=20, n_sensors=8)
+    plain = Operator.from_problem(pb)
+    pb.smooth = True
+    op = Operator.from_problem(pb)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(pb.shape)
+    Sx = smooth_image(x, pb.spacing)
+    assert np.max(np.abs(op.forward(x) - plain.forward(Sx))) <= 1e-13 * np.max(np.abs(plain.forward(Sx)))
+    hh = rng.standard_normal((pb.Nt, op.Ns))
+    ref = smooth_image(plain.adjoint(hh), pb.spacing)
+    assert np.max(np.abs(op.adjoint(hh) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_continuum_radial_pulse_3d():
+    # Homogeneous lossless medium, periodic grid without PML, a Gaussian p0 of width s = 2.5 h:
+    # the continuum solution is r p(r, t) = [(r - ct) P(r - ct) + (r + ct) P(r + ct)] / 2
+    # (P the radial profile, even).  The k-space scheme is exact in time for this medium and
+    # the pulse is band-limited to ~1e-13 on the grid, so the discrete record matches the
+    # continuum solution until the wave reaches a periodic image.
+    n = 48
+    h = 1e-4
+    c = 1500.0
+    dt = 0.3 * h / c
+    s = 2.5 * h
+    Nt = 41                       # c t = 12 h at the last sample
+    ax = (np.arange(n) - n // 2) * h
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    r = np.sqrt(xx**2 + yy**2 + zz**2)
+    prof = lambda q: np.exp(-q * q / (2 * s * s))
+    sel = (r > 0.5 * h) & (r < 16 * h)
+    idx = np.flatnonzero(sel.ravel())
+    op = Operator((n, n, n), (h, h, h), (0, 0, 0), 2.0, c, 1000.0, 0.0, 1.5, dt, Nt, sensor_index=idx)
+    data = op.forward(prof(r))
+    rs = r.ravel()[idx]
+    for m in (10, 25, Nt - 1):
+        ct = c * m * dt
+        ref = ((rs - ct) * prof(rs - ct) + (rs + ct) * prof(rs + ct)) / (2 * rs)
+        assert np.max(np.abs(data[m] - ref)) < 1e-11    # a 0.1 % error in c gives ~1e-3
+
+
+def test_continuum_radial_pulse_2d():
+    # 2-D counterpart: p(r, t) = int_0^inf k P^(k) J0(k r) cos(c k t) dk with the Hankel
+    # transform P^(k) = s^2 exp(-k^2 s^2 / 2) of the Gaussian profile, by quadrature.
+    from scipy import integrate, special
+
+    n = 96
+    h = 1e-4
+    c = 1500.0
+    dt = 0.3 * h / c
+    s = 2.5 * h
+    Nt = 61                       # c t = 18 h at the last sample
+    ax = (np.arange(n) - n // 2) * h
+    yy, xx = np.meshgrid(ax, ax, indexing="ij")
+    r = np.sqrt(xx**2 + yy**2)
+    # sensors along the +x half line through the centre, out to 24 h
+    idx = (n // 2) * n + n // 2 + np.arange(0, 25)
+    op = Operator((n, n), (h, h), (0, 0), 2.0, c, 1000.0, 0.0, 1.5, dt, Nt, sensor_index=idx)
+    data = op.forward(np.exp(-r * r / (2 * s * s)))
+    rs = np.arange(0, 25) * h
+    kmax = 12.0 / s
+    for m in (20, Nt - 1):
+        ct = c * m * dt
+        ref = [integrate.quad(lambda k: k * s * s * np.exp(-(k * s) ** 2 / 2) * special.j0(k * q) * np.cos(k * ct),
+                              0.0, kmax, limit=400, epsabs=1e-13)[0] for q in rs]
+        assert np.max(np.abs(data[m] - np.array(ref))) < 1e-10    # a 0.1 % error in c gives ~1e-3

@@ -127,6 +127,23 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
  *   grad     [N]      output, overwritten (host or device, plan precision). */
 pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* stream);
 
+/* pat_plan_set_smoothing -- the optional smoothing of the initial pressure (Sec. VI.A: the high
+ * frequencies of p0 are filtered by a self-adjoint operator S before each forward solve, and S is
+ * included in the adjoint).  enable = 1: pat_forward_plan computes H S p0, pat_adjoint returns
+ * S H^T h, pat_gradient_c2 starts from S p0 and returns S H^T h, batches and pat_mg_fista follow
+ * (a coarse level made by pat_plan_create_coarse inherits the switch).  enable = 0 (the default
+ * after pat_plan_create) turns it off.  The paper names no filter; S = F^-1 diag(W) F with the
+ * radial Blackman window W(k) = 0.42 + 0.5 cos(pi q) + 0.08 cos(2 pi q), q = |k| / k_c < 1, and
+ * W = 0 for q >= 1, k_c = min over axes of pi / dx.  The first smoothing call allocates a
+ * workspace of N complex values (plan-owned).
+ * Errors: PAT_EINVAL (NULL plan, enable not 0 or 1). */
+pat_status pat_plan_set_smoothing(pat_plan* plan, int enable);
+
+/* pat_plan_smooth -- y = S x with the plan's window (whatever the switch), x and y [N] device
+ * fields of the plan's precision (y may equal x; caller-owned).  Enqueued on `stream`.
+ * Errors: PAT_EINVAL (NULL argument), PAT_ENOMEM / PAT_ECUDA (workspace, launch). */
+pat_status pat_plan_smooth(pat_plan* plan, const void* x, void* y, void* stream);
+
 /* pat_gradient_c2 -- medium sensitivity: grad_c2 = d<H p0, h>/d(c0^2) at every grid point, and
  * grad_p0 = H^T h from the same reverse sweep.  The paper has no medium gradient; it follows from
  * Sec. III's adjoint-state construction applied to the discrete forward map, for the joint

@@ -84,6 +84,10 @@ def lib() -> ctypes.CDLL:
     L.pat_adjoint.restype = i32
     L.pat_plan_set_fault.argtypes = [vp, i32, f64]
     L.pat_plan_set_fault.restype = i32
+    L.pat_plan_set_smoothing.argtypes = [vp, i32]
+    L.pat_plan_set_smoothing.restype = i32
+    L.pat_plan_smooth.argtypes = [vp, vp, vp, vp]
+    L.pat_plan_smooth.restype = i32
     L.pat_gradient_c2.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_c2.restype = i32
     L.pat_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]

@@ -54,7 +54,7 @@ class PATOperator:
     on the same device (CPU tensors go through the library's host-pointer path)."""
 
     def __init__(self, shape, spacing, pml, pml_alpha, c, rho, alpha0, y, dt, Nt,
-                 sensor_pos=None, sensor_index=None, precision="f32", device=None):
+                 sensor_pos=None, sensor_index=None, precision="f32", device=None, smooth=False):
         self.shape = tuple(int(n) for n in shape)
         self.N = int(np.prod(self.shape))
         self.Nt = int(Nt)
@@ -92,12 +92,33 @@ class PATOperator:
         check(lib().pat_plan_get_info(self._plan, ctypes.byref(info)))
         self.info = info
         self.lossy = bool(info.lossy)
+        self.smoothing = False
+        if smooth:
+            self.set_smoothing(True)
 
     @classmethod
     def from_problem(cls, pb, precision="f32", Nt=None, device=None):
         return cls(pb.shape, pb.spacing, pb.pml, pb.pml_alpha, pb.c, pb.rho, pb.alpha0, pb.y, pb.dt,
                    pb.Nt if Nt is None else Nt, sensor_pos=pb.sensor_pos, sensor_index=pb.sensor_index,
-                   precision=precision, device=device)
+                   precision=precision, device=device, smooth=getattr(pb, "smooth", False))
+
+    def set_smoothing(self, enable: bool):
+        """pat_plan_set_smoothing: H becomes H S and its transpose S H^T (Sec. VI.A)."""
+        check(lib().pat_plan_set_smoothing(self._plan, int(bool(enable))))
+        self.smoothing = bool(enable)
+
+    def smooth(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """pat_plan_smooth: S x with the plan's window (device tensors)."""
+        self._check_in(x, self.N, "x")
+        if x.device.type != "cuda":
+            raise ValueError("smooth takes a CUDA tensor")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=x.device)
+        self._check_in(out, self.N, "out")
+        with torch.cuda.device(self.device):
+            check(lib().pat_plan_smooth(self._plan, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        _stream_ptr(stream, self.device)))
+        return out
 
     # -- calls ---------------------------------------------------------------------------------
     def _check_in(self, t, n, name):
@@ -175,6 +196,7 @@ class PATOperator:
         op.dtype = self.dtype
         op.device = self.device
         op.lossy = bool(info.lossy)
+        op.smoothing = self.smoothing   # pat_plan_create_coarse carries the switch over
         return op
 
     # -- kernel-timing probe ------------------------------------------------------------------------

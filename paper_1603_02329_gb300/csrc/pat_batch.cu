@@ -125,9 +125,19 @@ static pat_status batch_run(pat_batch* b, bool adjoint, const void* const* in, v
         cudaError_t e = adjoint ? cudaMemcpyAsync(p->data_ptr, in[i], ndat, cudaMemcpyDefault, s)
                                 : cudaMemcpyAsync(p->img_ptr, in[i], nimg, cudaMemcpyDefault, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch input copy");
+        if (!adjoint && p->smooth) {   // p^0 = S p0 (Sec. VI.A)
+            st = plan_smooth(p, p->img_ptr, s);
+            if (st != PAT_OK) return st;
+        }
     }
     cudaError_t e = cudaGraphLaunch(b->exec[adjoint ? 1 : 0], s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (batch)");
+    for (size_t i = 0; i < b->plans.size() && adjoint; ++i) {   // (H S)^T = S H^T
+        PlanBase* p = b->plans[i]->impl;
+        if (!p->smooth) continue;
+        st = plan_smooth(p, p->img_ptr, s);
+        if (st != PAT_OK) return st;
+    }
     for (size_t i = 0; i < b->plans.size(); ++i) {
         PlanBase* p = b->plans[i]->impl;
         const size_t nimg = (size_t)p->info.N * p->elem, ndat = (size_t)p->info.Nt * p->info.Ns * p->elem;

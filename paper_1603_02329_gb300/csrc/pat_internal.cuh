@@ -200,6 +200,8 @@ struct PlanBase {
     unsigned* gbar = nullptr;
     // non-finite check of the last solve's output: 0, or PAT_ENONFINITE (zeroed before each solve)
     unsigned* fstat = nullptr;
+    // 1: the initial pressure is smoothed, p^0 = S p0, and the adjoint ends with S (Sec. VI.A)
+    int smooth = 0;
     unsigned long long* trace = nullptr;
     int trace_k0 = 0, trace_nk = 0;
 };

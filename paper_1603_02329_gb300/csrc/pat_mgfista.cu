@@ -461,8 +461,11 @@ pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** out) {
         }
     pat_sensors sc{in.Ns, pos.data(), nullptr};
     const int Ntc = (in.Nt + 1) / 2;
-    return pat_plan_create(&gc, c.data(), rho.data(), a0.data(), in.alpha0_is_scalar, in.y, &sc, 2.0 * in.dt, Ntc,
-                           in.prec, out);
+    const pat_status st = pat_plan_create(&gc, c.data(), rho.data(), a0.data(), in.alpha0_is_scalar, in.y, &sc,
+                                          2.0 * in.dt, Ntc, in.prec, out);
+    // a smoothing fine level has a smoothing coarse level, with its own (half) cut-off radius
+    if (st == PAT_OK) (*out)->impl->smooth = fine->impl->smooth;
+    return st;
 }
 
 pat_status pat_mg_fista_levels(pat_plan* const* levels, int nlevels, const double* L_levels, const void* data,

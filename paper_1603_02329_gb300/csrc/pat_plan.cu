@@ -434,6 +434,10 @@ pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* st
     const size_t ndat = (size_t)b->info.Nt * b->info.Ns * b->elem;
     cudaError_t e = cudaMemcpyAsync(b->img_ptr, p0, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy p0");
+    if (b->smooth) {   // p^0 = S p0 (Sec. VI.A)
+        st = plan_smooth(b, b->img_ptr, s);
+        if (st != PAT_OK) return st;
+    }
     st = plan_clear_finite(b, s);
     if (st != PAT_OK) return st;
     if (b->persistent) {
@@ -471,11 +475,36 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
         e = cudaGraphLaunch(b->adj_exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch (adjoint)");
     }
+    if (b->smooth) {   // (H S)^T = S H^T
+        st = plan_smooth(b, b->img_ptr, s);
+        if (st != PAT_OK) return st;
+    }
     st = plan_finite_check(b, true, s);
     if (st != PAT_OK) return st;
     e = cudaMemcpyAsync(grad, b->img_ptr, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy gradient");
     return PAT_OK;
+}
+
+pat_status pat_plan_set_smoothing(pat_plan* plan, int enable) {
+    set_error("");
+    if (!plan || enable < 0 || enable > 1) return fail(PAT_EINVAL, "NULL plan or enable not 0 / 1");
+    if (plan->impl->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans do not smooth p0");
+    plan->impl->smooth = enable;
+    return PAT_OK;
+}
+
+pat_status pat_plan_smooth(pat_plan* plan, const void* x, void* y, void* stream) {
+    set_error("");
+    if (!plan || !x || !y) return fail(PAT_EINVAL, "NULL argument");
+    PlanBase* b = plan->impl;
+    DeviceGuard g(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (x != y) {
+        const cudaError_t e = cudaMemcpyAsync(y, x, (size_t)b->info.N * b->elem, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy x");
+    }
+    return plan_smooth(b, y, s);
 }
 
 pat_status pat_plan_set_fault(pat_plan* plan, int barrier_extra, double wait_limit_s) {

@@ -9,6 +9,7 @@
 #include "pat_host.h"
 #include "pat_persist.cuh"
 #include "pat_p2.h"
+#include "pat_smooth.h"
 
 namespace pat {
 
@@ -642,6 +643,48 @@ template <typename T> struct Plan : public PlanBase {
     }
 
     // ---------------------------------------------------------------------------------------
+    // smoothing S of the initial pressure (Sec. VI.A; pat_smooth.cu): x <- S x in place
+    // ---------------------------------------------------------------------------------------
+    cplx<T>* sm_Z = nullptr;   // complex workspace of N values, allocated on first use
+    pat_status smooth_inplace(T* x, cudaStream_t s) {
+        if (arena) {
+            set_error("static-arena plans do not smooth p0");
+            return PAT_EUNSUPPORTED;
+        }
+        if (!sm_Z) {
+            pat_status st = PAT_OK;
+            sm_Z = dalloc<cplx<T>>((size_t)P.N, &st);
+            if (!sm_Z) return st;
+        }
+        SmoothArgs<T> A{};
+        A.d = H.d;
+        A.nx = H.nx;
+        A.ny = H.ny;
+        A.nz = H.nz;
+        A.ax[0] = P.fx;
+        A.ax[1] = P.fy;
+        A.ax[2] = P.fz;
+        A.tw[0] = P.twx;
+        A.tw[1] = P.twy;
+        A.tw[2] = P.twz;
+        const int n[3] = {H.nx, H.ny, H.nz};
+        double kc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            A.dk[a] = 0.0;
+            if (a >= H.d) continue;
+            const double dx = in.grid.dx[a];
+            A.dk[a] = 2.0 * M_PI / ((double)n[a] * dx);
+            const double kn = M_PI / dx;
+            kc = (a == 0) ? kn : std::min(kc, kn);
+        }
+        A.inv_kc2 = 1.0 / (kc * kc);
+        A.invN = 1.0 / (double)P.N;
+        A.Z = sm_Z;
+        const cudaError_t e = smooth_apply<T>(A, x, s);
+        return e == cudaSuccess ? PAT_OK : cuda_fail(e, "smoothing of p0");
+    }
+
+    // ---------------------------------------------------------------------------------------
     // medium gradient with checkpoints (direct launches of the per-phase kernels)
     // ---------------------------------------------------------------------------------------
     // forward step n -> n + 1 on the state of Q; q^{n+1} = d p^{n+1} / d c0^2 into qrow
@@ -725,6 +768,13 @@ template <typename T> struct Plan : public PlanBase {
             release();
             return cuda_fail(e, "gradient setup");
         }
+        if (smooth) {   // the initial pressure is S p0 (Sec. VI.A)
+            const pat_status sst = smooth_inplace(p0buf, s);
+            if (sst != PAT_OK) {
+                release();
+                return sst;
+            }
+        }
         const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
         auto save = [&](int j) {
             T* c = ckpt + (size_t)j * ck_elems;
@@ -768,6 +818,13 @@ template <typename T> struct Plan : public PlanBase {
         }
         if (Nt > 1) adj_step_on<D>(0, nullptr, gc2, p0buf, s);
         e = take_launch_err();
+        if (e == cudaSuccess && gp0_out && smooth) {   // (H S)^T = S H^T
+            const pat_status sst = smooth_inplace(P.img, s);
+            if (sst != PAT_OK) {
+                release();
+                return sst;
+            }
+        }
         if (e == cudaSuccess) e = cudaMemcpyAsync(gc2_out, gc2, N * sizeof(T), cudaMemcpyDefault, s);
         if (e == cudaSuccess && gp0_out) e = cudaMemcpyAsync(gp0_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
         release();
@@ -1036,6 +1093,11 @@ pat_status plan_clear_finite(PlanBase* b, cudaStream_t s) {
 pat_status plan_finite_check(PlanBase* b, bool adjoint, cudaStream_t s) {
     if (b->info.precision == PAT_F32) return finite_check_t<float>(b, adjoint, s);
     return finite_check_t<double>(b, adjoint, s);
+}
+
+pat_status plan_smooth(PlanBase* base, void* x, cudaStream_t s) {
+    if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->smooth_inplace((float*)x, s);
+    return static_cast<Plan<double>*>(base)->smooth_inplace((double*)x, s);
 }
 
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s) {

@@ -303,3 +303,48 @@ def test_continuum_radial_pulse_2d():
         ref = [integrate.quad(lambda k: k * s * s * np.exp(-(k * s) ** 2 / 2) * special.j0(k * q) * np.cos(k * ct),
                               0.0, kmax, limit=400, epsabs=1e-13)[0] for q in rs]
         assert np.max(np.abs(data[m] - np.array(ref))) < 1e-10    # a 0.1 % error in c gives ~1e-3
+
+
+def _dft_all_axes(f, inverse=False):
+    """Multi-dimensional DFT by its definition, one O(n^2) matrix product per axis."""
+    out = np.asarray(f, dtype=complex)
+    for a, n in enumerate(out.shape):
+        j = np.arange(n)
+        F = np.exp((2j if inverse else -2j) * np.pi * np.outer(j, j) / n)
+        if inverse:
+            F = F / n
+        out = np.moveaxis(np.tensordot(F, np.moveaxis(out, a, 0), axes=(1, 0)), 0, a)
+    return out
+
+
+@pytest.mark.parametrize("shape", [(6, 7), (12, 10), (8, 9, 10), (6, 5, 14)])
+def test_spectral_operators_match_brute_force_dft(shape):
+    # D+, D-, the fractional Laplacians and the smoothing window, computed by the oracle through
+    # rfftn / irfftn on the half-spectrum layout, against full complex DFTs by definition with the
+    # symbols written on the whole grid (radices 2, 3, 5, 7; odd and even lengths)
+    rng = np.random.default_rng(13)
+    d = len(shape)
+    h = tuple(1e-4 * (1 + 0.25 * a) for a in range(d))
+    c, dt, y = 1500.0, 2e-8, 1.5
+    op = Operator(shape, h, (0,) * d, 2.0, c, 1000.0, 0.75, y, dt, 2, sensor_index=[0])
+    f = rng.standard_normal(shape)
+    grids = np.meshgrid(*[2 * np.pi * np.where(np.arange(n) > n // 2, np.arange(n) - n, np.arange(n)) / (n * h[a])
+                          for a, n in enumerate(shape)], indexing="ij")
+    kmag = np.sqrt(sum(k * k for k in grids))
+    z = c * kmag * dt / 2
+    kappa = np.where(z > 0, np.sin(z) / np.where(z > 0, z, 1.0), 1.0)
+    Ff = _dft_all_axes(f)
+
+    def brute(symbol):
+        return np.real(_dft_all_axes(symbol * Ff, inverse=True))
+
+    for a in range(d):
+        k = grids[a]
+        assert np.max(np.abs(op.Dplus(a, f) - brute(1j * k * kappa * np.exp(0.5j * k * h[a])))) < 1e-12 * np.abs(k).max()
+        assert np.max(np.abs(op.Dminus(a, f) - brute(1j * k * kappa * np.exp(-0.5j * k * h[a])))) < 1e-12 * np.abs(k).max()
+    for s in (y - 2.0, y - 1.0):
+        sym = np.where(kmag > 0, np.where(kmag > 0, kmag, 1.0) ** s, 0.0)
+        assert np.max(np.abs(op.ks.apply(op.Ly2 if s < -0.1 else op.Ly1, f) - brute(sym))) < 1e-12 * sym.max()
+    q = kmag / min(np.pi / hh for hh in h)
+    W = np.where(q < 1, 0.42 + 0.5 * np.cos(np.pi * q) + 0.08 * np.cos(2 * np.pi * q), 0.0)
+    assert np.max(np.abs(smooth_image(f, h) - brute(W))) < 1e-13

@@ -320,3 +320,51 @@ def test_coarse_level_clamps_edge_sensors():
     assert M[31, last] == 1.0          # fine x = 31 -> clamped onto coarse x = 15
     assert M[30, last] == 1.0          # fine x = 30 -> coarse node 15
     assert M[29, last - 1] == 0.5 and M[29, last] == 0.5
+
+
+def test_forward_operator_is_linear():
+    # the cost-saving identity (O9) rests on H being linear, smoothing and absorption included
+    pb = synth.small_lossy_2d(shape=(24, 28), pml=5, Nt=25, n_sensors=8)
+    pb.smooth = True
+    op = Operator.from_problem(pb)
+    rng = np.random.default_rng(41)
+    x, z = rng.standard_normal(pb.shape), rng.standard_normal(pb.shape)
+    a, b = 1.7, -0.4
+    lhs = op.forward(a * x + b * z)
+    rhs = a * op.forward(x) + b * op.forward(z)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(lhs))
+
+
+def test_data_space_momentum_equals_direct_forward():
+    # O9: FISTA forms H y_{k+1} = (1 + theta_k) H x_k - theta_k H x_{k-1} in data space.  Record
+    # what the solver hands to H and H^T, rebuild y_3 = x_2 + theta_2 (x_2 - x_1) with the
+    # momentum of Beck and Teboulle's t-rule (t_1 = 1, t_2 = (1 + sqrt 5) / 2, theta_2 =
+    # (t_2 - 1) / t_3 = 0.28175...), and compare the residual the solver used at iteration 3 with
+    # a direct forward solve of y_3.
+    pb, op, phat, L, _ = _mg_setup()
+
+    class Recorder:
+        def __init__(self, inner):
+            self.inner, self.fwd_in, self.adj_in = inner, [], []
+
+        def forward(self, x):
+            self.fwd_in.append(np.array(x))
+            return self.inner.forward(x)
+
+        def adjoint(self, r):
+            self.adj_in.append(np.array(r))
+            return self.inner.adjoint(r)
+
+    rec = Recorder(op)
+    po.mg_fista(rec, phat, np.zeros(pb.shape), L, po.FistaOpts(variant=1, max_iter=4, eps_d=-1.0))
+    x1, x2 = rec.fwd_in[1], rec.fwd_in[2]            # forward inputs: x_0, x_1, x_2, ...
+    t2 = (1 + math.sqrt(5)) / 2
+    t3 = (1 + math.sqrt(1 + 4 * t2 * t2)) / 2
+    theta2 = (t2 - 1) / t3
+    assert abs(theta2 - 0.2817529) < 1e-6
+    y3 = x2 + theta2 * (x2 - x1)
+    Hy3_used = rec.adj_in[2] + phat                  # adjoint inputs: H y_k - p_hat, k = 1, 2, 3
+    Hy3 = op.forward(y3)
+    assert np.max(np.abs(Hy3_used - Hy3)) <= 1e-12 * np.max(np.abs(Hy3))
+    # iteration 2 has theta_1 = 0: y_2 = x_1 exactly
+    assert np.max(np.abs(rec.adj_in[1] + phat - op.forward(x1))) <= 1e-12 * np.max(np.abs(Hy3))

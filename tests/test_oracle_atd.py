@@ -7,6 +7,8 @@ absorbing medium; a wrong sign, factor, operator order or source timing leaves a
 Two deviations do not vanish and are stated (readings A4, A5): inside the PML layer, where the
 split of the adjoint densities differs, and between the paper's gradient rho*(T) / rho0 and the
 gradient of the forward map's own initial state, which differ by O(alpha0)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -79,3 +81,24 @@ def test_paper_gradient_differs_by_order_alpha0():
     lossless, _ = _family(0.0, pml=0, levels=1, initial="paper")
     lossless_r5, _ = _family(0.0, pml=0, levels=1, initial="R5")
     assert lossless[0] == lossless_r5[0]
+
+
+@pytest.mark.skipif(not os.environ.get("PAT_SLOW_ORACLE"), reason="about 6 minutes of FP64 CPU work; set PAT_SLOW_ORACLE=1")
+def test_deviation_on_the_512_vessel_workload():
+    # The paper's adjoint against the transpose on the 512^2 absorbing workload (Nt 2000, sensors
+    # on the first row inside the 20-point PML), residual = the 40 dB data itself.  Measured:
+    # 65 % over the whole grid (the PML layer, A4), 6.1 % inside it, dot-test mismatch 1.5 %
+    # (transpose: 2e-16).
+    pb = synth.vessel_phantom_2d()
+    op = Operator.from_problem(pb)
+    d = op.forward(pb.p0)
+    h = d + 0.01 * np.sqrt(np.mean(d * d)) * np.random.default_rng(7).standard_normal(d.shape)
+    gt = op.dt * op.adjoint(h)
+    ga = adjoint_then_discretize(op, h)
+    P = pb.pml[0]
+    sl = (slice(P, pb.shape[0] - P), slice(P, pb.shape[1] - P))
+    inner = np.linalg.norm((ga - gt)[sl]) / np.linalg.norm(gt[sl])
+    lhs = float(np.sum(d * h))
+    mismatch = abs(lhs - np.sum(pb.p0 * ga) / op.dt) / abs(lhs)
+    assert 0.01 < inner < 0.1
+    assert 1e-3 < mismatch < 0.05

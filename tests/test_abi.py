@@ -111,3 +111,6 @@ def test_host_side_argument_validation(L):
     assert L.pat_mg_fista_levels(None, 2, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL
     assert "nlevels" in L.pat_last_error().decode()
     assert L.pat_mg_fista(None, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL
+    # p0 smoothing: NULL plan / arguments (checked before any device work)
+    assert L.pat_plan_set_smoothing(None, 1) == PAT_EINVAL
+    assert L.pat_plan_smooth(None, None, None, None) == PAT_EINVAL

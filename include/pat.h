@@ -140,7 +140,8 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
 pat_status pat_plan_set_smoothing(pat_plan* plan, int enable);
 
 /* pat_plan_smooth -- y = S x with the plan's window (whatever the switch), x and y [N] device
- * fields of the plan's precision (y may equal x; caller-owned).  Enqueued on `stream`.
+ * fields of the plan's precision (y may equal x, otherwise the two must not overlap;
+ * caller-owned).  Enqueued on `stream`.
  * Errors: PAT_EINVAL (NULL argument), PAT_ENOMEM / PAT_ECUDA (workspace, launch). */
 pat_status pat_plan_smooth(pat_plan* plan, const void* x, void* y, void* stream);
 

@@ -102,3 +102,26 @@ def test_deviation_on_the_512_vessel_workload():
     mismatch = abs(lhs - np.sum(pb.p0 * ga) / op.dt) / abs(lhs)
     assert 0.01 < inner < 0.1
     assert 1e-3 < mismatch < 0.05
+
+
+def test_atd_converges_in_3d():
+    # the source split 1/d and the 3-D derivative set: first order on a 3-D absorbing medium
+    pb = synth.small_lossy_3d(shape=(12, 16, 20), pml=3, Nt=21)
+    T = (pb.Nt - 1) * pb.dt
+    rng = np.random.default_rng(4)
+    Ns = len(pb.sensor_index)
+    amp, t0 = rng.standard_normal(Ns), rng.uniform(0.3 * T, 0.7 * T, Ns)
+    width, om = 0.12 * T, 2 * np.pi / (0.3 * T)
+    diffs = []
+    for k in range(3):
+        dt = pb.dt / 2**k
+        Nt = (pb.Nt - 1) * 2**k + 1
+        op = Operator(pb.shape, pb.spacing, (0, 0, 0), pb.pml_alpha, pb.c, pb.rho, pb.alpha0, pb.y, dt, Nt,
+                      sensor_index=pb.sensor_index)
+        t = np.arange(Nt)[:, None] * dt
+        h = amp * np.exp(-((t - t0) / width) ** 2) * np.sin(om * (t - t0))
+        gt = dt * op.adjoint(h)
+        diffs.append(np.linalg.norm(adjoint_then_discretize(op, h) - gt) / np.linalg.norm(gt))
+    diffs = np.array(diffs)
+    assert np.all(diffs[:-1] / diffs[1:] > 1.8), diffs
+    assert diffs[-1] < 3e-3

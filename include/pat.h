@@ -134,9 +134,10 @@ pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* s
  * (a coarse level made by pat_plan_create_coarse inherits the switch).  enable = 0 (the default
  * after pat_plan_create) turns it off.  The paper names no filter; S = F^-1 diag(W) F with the
  * radial Blackman window W(k) = 0.42 + 0.5 cos(pi q) + 0.08 cos(2 pi q), q = |k| / k_c < 1, and
- * W = 0 for q >= 1, k_c = min over axes of pi / dx.  The first smoothing call allocates a
- * workspace of N complex values (plan-owned).
- * Errors: PAT_EINVAL (NULL plan, enable not 0 or 1). */
+ * W = 0 for q >= 1, k_c = min over axes of pi / dx.  enable = 1 allocates a workspace of N
+ * complex values (plan-owned, kept until the plan is destroyed), so the solves never allocate.
+ * Errors: PAT_EINVAL (NULL plan, enable not 0 or 1), PAT_EUNSUPPORTED (static-arena plan),
+ * PAT_ENOMEM. */
 pat_status pat_plan_set_smoothing(pat_plan* plan, int enable);
 
 /* pat_plan_smooth -- y = S x with the plan's window (whatever the switch), x and y [N] device

@@ -37,6 +37,8 @@ pat_status plan_capture_graph(PlanBase* base, bool adjoint, cudaGraph_t* out);
 pat_status plan_run_persistent(PlanBase* base, bool adjoint, cudaStream_t s);
 // x <- S x (the p0 smoothing of Sec. VI.A) in place, x a device field of the plan's precision
 pat_status plan_smooth(PlanBase* base, void* x, cudaStream_t s);
+// allocate the smoothing workspace (no-op when present)
+pat_status plan_smooth_alloc(PlanBase* base);
 // zero the plan's non-finite flag / scan the solve's output (data after H, image after H^T) into it
 pat_status plan_clear_finite(PlanBase* base, cudaStream_t s);
 pat_status plan_finite_check(PlanBase* base, bool adjoint, cudaStream_t s);

@@ -464,7 +464,16 @@ pat_status pat_plan_create_coarse(const pat_plan* fine, pat_plan** out) {
     const pat_status st = pat_plan_create(&gc, c.data(), rho.data(), a0.data(), in.alpha0_is_scalar, in.y, &sc,
                                           2.0 * in.dt, Ntc, in.prec, out);
     // a smoothing fine level has a smoothing coarse level, with its own (half) cut-off radius
-    if (st == PAT_OK) (*out)->impl->smooth = fine->impl->smooth;
+    if (st == PAT_OK && fine->impl->smooth) {
+        const pat_status sst = pat_plan_set_smoothing(*out, 1);
+        if (sst != PAT_OK) {
+            const std::string msg = pat_last_error();
+            pat_plan_destroy(*out);
+            *out = nullptr;
+            set_error(msg);
+            return sst;
+        }
+    }
     return st;
 }
 

@@ -490,6 +490,11 @@ pat_status pat_plan_set_smoothing(pat_plan* plan, int enable) {
     set_error("");
     if (!plan || enable < 0 || enable > 1) return fail(PAT_EINVAL, "NULL plan or enable not 0 / 1");
     if (plan->impl->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans do not smooth p0");
+    if (enable) {
+        DeviceGuard g(plan->impl->device);
+        const pat_status st = plan_smooth_alloc(plan->impl);
+        if (st != PAT_OK) return st;
+    }
     plan->impl->smooth = enable;
     return PAT_OK;
 }

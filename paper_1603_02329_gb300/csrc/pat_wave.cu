@@ -645,8 +645,10 @@ template <typename T> struct Plan : public PlanBase {
     // ---------------------------------------------------------------------------------------
     // smoothing S of the initial pressure (Sec. VI.A; pat_smooth.cu): x <- S x in place
     // ---------------------------------------------------------------------------------------
-    cplx<T>* sm_Z = nullptr;   // complex workspace of N values, allocated on first use
-    pat_status smooth_inplace(T* x, cudaStream_t s) {
+    cplx<T>* sm_Z = nullptr;   // complex workspace of N values (smooth_alloc)
+    // allocate the workspace if it is missing: called when smoothing is switched on, so that the
+    // solves themselves never allocate (they may run inside a caller's stream capture)
+    pat_status smooth_alloc() {
         if (arena) {
             set_error("static-arena plans do not smooth p0");
             return PAT_EUNSUPPORTED;
@@ -656,6 +658,11 @@ template <typename T> struct Plan : public PlanBase {
             sm_Z = dalloc<cplx<T>>((size_t)P.N, &st);
             if (!sm_Z) return st;
         }
+        return PAT_OK;
+    }
+    pat_status smooth_inplace(T* x, cudaStream_t s) {
+        const pat_status ast = smooth_alloc();
+        if (ast != PAT_OK) return ast;
         SmoothArgs<T> A{};
         A.d = H.d;
         A.nx = H.nx;
@@ -1093,6 +1100,11 @@ pat_status plan_clear_finite(PlanBase* b, cudaStream_t s) {
 pat_status plan_finite_check(PlanBase* b, bool adjoint, cudaStream_t s) {
     if (b->info.precision == PAT_F32) return finite_check_t<float>(b, adjoint, s);
     return finite_check_t<double>(b, adjoint, s);
+}
+
+pat_status plan_smooth_alloc(PlanBase* base) {
+    if (base->info.precision == PAT_F32) return static_cast<Plan<float>*>(base)->smooth_alloc();
+    return static_cast<Plan<double>*>(base)->smooth_alloc();
 }
 
 pat_status plan_smooth(PlanBase* base, void* x, cudaStream_t s) {

@@ -102,7 +102,8 @@ typedef struct {
  * Eq. (Twelve), PML factors, k-space tables, interpolation weights) are computed here in FP64
  * on the host and stored on the current device in the plan's precision.
  * Errors: PAT_EINVAL (bad sizes, NULLs, y = 1, sensor outside grid), PAT_EUNSUPPORTED (FFT
- * length not 2^a 3^b 5^c 7^d, or odd), PAT_ENOMEM, PAT_ECUDA. */
+ * length not 2^a 3^b 5^c 7^d, or odd, or above 1024; more than 2^27 grid points; Nt * Ns above
+ * 2^31 - 1), PAT_ENOMEM, PAT_ECUDA. */
 pat_status pat_plan_create(const pat_grid* grid, const double* c, const double* rho,
                            const double* alpha0, int alpha0_is_scalar, double y,
                            const pat_sensors* sensors, double dt, int Nt, pat_precision prec,

@@ -221,6 +221,10 @@ pat_status build_tables(const pat_grid* grid, const double* c, const double* rho
     h.nxh = h.nx / 2 + 1;
     h.ldh = (h.nxh + 7) / 8 * 8;
     h.N = (long long)h.nx * h.ny * h.nz;
+    // the kernels index fields and records with 32-bit offsets in places; the largest grids and
+    // records run so far are 256^3 points and 1500 x 16384 samples
+    if (h.N > (1LL << 27)) return fail(PAT_EUNSUPPORTED, "grid above 2^27 points (512^3)");
+    if ((long long)Nt * sensors->count > 0x7fffffffLL) return fail(PAT_EUNSUPPORTED, "Nt * Ns above 2^31 - 1");
     h.Nt = Nt;
     h.Ns = sensors->count;
     h.dt = dt;

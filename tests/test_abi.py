@@ -111,6 +111,13 @@ def test_host_side_argument_validation(L):
     assert L.pat_mg_fista_levels(None, 2, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL
     assert "nlevels" in L.pat_last_error().decode()
     assert L.pat_mg_fista(None, None, None, None, None, None, None, ITER_CB(0), None, None) == PAT_EINVAL
+    # size limits, checked before the medium arrays are read: 1024^3 points, Nt * Ns >= 2^31
+    from paper_1603_02329_gb300.api import make_grid
+
+    g3 = make_grid((1024, 1024, 1024), (1e-4,) * 3, (4,) * 3, 2.0)
+    assert _call_create(L, g3, c, rho, a0, sens_idx=[0])[0] == PAT_EUNSUPPORTED
+    assert "2^27" in L.pat_last_error().decode()
+    assert _call_create(L, _grid(), c, rho, a0, sens_idx=list(range(256)), Nt=1 << 24)[0] == PAT_EUNSUPPORTED
     # p0 smoothing: NULL plan / arguments (checked before any device work)
     assert L.pat_plan_set_smoothing(None, 1) == PAT_EINVAL
     assert L.pat_plan_smooth(None, None, None, None) == PAT_EINVAL

@@ -221,8 +221,8 @@ pat_status build_tables(const pat_grid* grid, const double* c, const double* rho
     h.nxh = h.nx / 2 + 1;
     h.ldh = (h.nxh + 7) / 8 * 8;
     h.N = (long long)h.nx * h.ny * h.nz;
-    // the kernels index fields and records with 32-bit offsets in places; the largest grids and
-    // records run so far are 256^3 points and 1500 x 16384 samples
+    // the kernels index fields and records with 32-bit offsets in places: these limits keep every
+    // flat index of a field (and of a complex half spectrum) or of the record below 2^31
     if (h.N > (1LL << 27)) return fail(PAT_EUNSUPPORTED, "grid above 2^27 points (512^3)");
     if ((long long)Nt * sensors->count > 0x7fffffffLL) return fail(PAT_EUNSUPPORTED, "Nt * Ns above 2^31 - 1");
     h.Nt = Nt;

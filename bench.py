@@ -1,9 +1,18 @@
 """Benchmark of the forward + adjoint solve pair (one H^T H product) on GB300.
 
-Workload (default): 2-D 512^2 heterogeneous absorbing medium (c = 1500 +/- 100 m/s, rho = 1000
-+/- 5 %, alpha0 = 0.75 dB MHz^-1.5 cm^-1, y = 1.5), 20-point PML, 512 on-grid line sensors,
-Nt = 2000, FP32 fields.  One step = pat_forward_plan + pat_adjoint through the C ABI: 2 N Nt
-grid-point-steps.  value = grid-point-steps per second over all ranks (Gpt-steps/s).
+Workload (default): 3-D 256^3 heterogeneous absorbing medium (c = 1500 +/- 100 m/s, rho = 1000
++/- 5 %, alpha0 = 0.75 dB MHz^-1.5 cm^-1, y = 1.5), 20-point PML, a 128 x 128 on-grid planar
+sensor array at stride 2, Nt = 1500, FP32 fields (about 1 GB of state: larger than L2).  One step =
+pat_forward_plan + pat_adjoint through the C ABI: 2 N Nt grid-point-steps.  value = grid-point-steps
+per second over all ranks (Gpt-steps/s).
+
+The default run adds three records to the JSON line:
+  - "vessel2d_512": the same measurement on the 2-D 512^2 absorbing workload (Nt = 2000, 512 line
+    sensors), whose state stays in shared memory (one persistent kernel per solve);
+  - "mg_vs_fista": wall time of 3-level MG-FISTA (256^3 / 128^3 / 64^3) and of single-grid FISTA to
+    the same relative error on 40 dB data, 12 iterations of FISTA at most;
+  - "mg_precision": relative L2 distance of the FP32 iterates from the FP64 iterates of the same
+    MG-FISTA and FISTA runs on a small 2-D case, per iteration.
 
 Multi-GPU: one independent instance per rank (weak scaling, no collective on the data path).
 
@@ -36,16 +45,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="vessel2d_512",
+    ap.add_argument("--workload", default="tube3d_256",
                     choices=["vessel2d_512", "disc2d_168", "tube3d_128", "tube3d_256"])
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 2-D 512^2 record that the default 256^3 run adds")
+    ap.add_argument("--no-mg", action="store_true",
+                    help="skip the MG-FISTA vs FISTA and FP32-vs-FP64 records of the default 256^3 run")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the workload's time axis (small cases for profiler captures only)")
     ap.add_argument("--probe-stride", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mg", action="store_true", help="also time MG-FISTA vs FISTA to a target RE")
-    ap.add_argument("--mg-iters", type=int, default=20)
-    ap.add_argument("--mg-levels", type=int, default=2, help="levels of MG-FISTA (2 or 3)")
+    ap.add_argument("--mg-iters", type=int, default=0,
+                    help="FISTA iterations of the MG comparison (0: 12 at 256^3, else 20)")
+    ap.add_argument("--mg-levels", type=int, default=0, help="levels of MG-FISTA (0: 3 at 256^3, else 2)")
     ap.add_argument("--mg-data", default="same", choices=["same", "refined"],
                     help="MG comparison data: from the reconstruction grid (inverse crime, stated) or from "
                          "a 1.44x finer grid with 35 dB-contaminated maps (synth.refined_problem)")
@@ -56,7 +70,14 @@ def parse():
                          "in the middle of one forward solve (pat_plan_set_trace) and report its medians")
     ap.add_argument("--c2grad", type=int, default=0,
                     help="also time the checkpointed c0^2 gradient with this checkpoint interval")
-    return ap.parse_args()
+    a = ap.parse_args()
+    big = a.workload == "tube3d_256"
+    if a.mg_iters <= 0:
+        a.mg_iters = 12 if big else 20
+    if a.mg_levels <= 0:
+        a.mg_levels = 3 if big else 2
+    a.mg_default = big and not a.no_mg
+    return a
 
 
 def workload(name, rank):
@@ -444,28 +465,62 @@ def mg_vs_fista(args, dev, pb):
             "params": dict(common, lam=1e-2, L=L, L_coarse=Lc, L_coarse2=Lc2)}
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
+def mg_precision(dev, iters=5):
+    """FP32 against FP64 for the optimisation results: the relative L2 distance of the FP32 iterate
+    x_k from the FP64 iterate x_k (k = 1 .. iters) of single-grid FISTA and of two-level MG-FISTA, run
+    through the C ABI on a small 2-D absorbing case (64^2, 8-pt PML, 48 off-grid circle sensors,
+    Nt = 120, 40 dB data; Sec. VI.A parameters).  The FP64 GPU path itself matches the FP64 CPU oracle
+    iterate by iterate to 1e-9 (tests/test_gpu_optim.py), so this is the error of the FP32 results
+    against the FP64 oracle up to that."""
+    import torch
+
+    from paper_1603_02329_gb300 import synth
+    from paper_1603_02329_gb300.api import PATOperator, mg_fista
+
+    pb = synth.small_lossy_2d(shape=(64, 64), pml=8, Nt=120, n_sensors=48)
+    ops = {p: PATOperator.from_problem(pb, precision=p, device=dev) for p in ("f64", "f32")}
+    opc = {p: ops[p].coarse() for p in ops}
+    dts = {"f64": torch.float64, "f32": torch.float32}
+    clean = ops["f64"].forward(torch.tensor(pb.p0, dtype=torch.float64, device=dev)).cpu().numpy()
+    noisy = synth.awgn(np.random.default_rng(2), clean, 40.0)
+    L = ops["f64"].power_iteration(torch.tensor(synth.random_image(11, pb.shape), device=dev), 30)
+    Lc = opc["f64"].power_iteration(torch.tensor(synth.random_image(12, opc["f64"].shape), device=dev), 30)
+    out = {"case": "2-D 64^2 absorbing, 8-pt PML, 48 circle sensors, Nt=120, 40 dB AWGN; lambda=1e-2, n_tv=20",
+           "reference": "FP64 GPU iterates (equal to the FP64 oracle's to 1e-9)"}
+    for label, rec in (("fista", False), ("mgfista", True)):
+        errs, branches = [], []
+        for k in range(1, iters + 1):
+            xs = {}
+            for p in ("f64", "f32"):
+                d = torch.tensor(noisy, dtype=dts[p], device=dev)
+                x0 = torch.zeros(pb.shape, dtype=dts[p], device=dev)
+                x, _, recs = mg_fista(ops[p], opc[p] if rec else None, d, x0, L, L_coarse=Lc, recursion=rec,
+                                      max_iter=k, eps_d=-1.0, variant=1, lam=1e-2, step_scale=1.0, kappa=0.25)
+                xs[p] = x.double()
+                if p == "f64" and k == iters:
+                    branches = [r["branch"] for r in recs]
+            errs.append(float(torch.linalg.norm(xs["f32"] - xs["f64"]) / torch.linalg.norm(xs["f64"])))
+        out[label] = {"rel_l2_per_iter": errs, "branches": branches}
+    for o in list(ops.values()) + list(opc.values()):
+        o.close()
+    return out
+
+
+PATH_NAMES = {0: "CUDA graph of per-phase kernels", 1: "persistent kernel per solve",
+              2: "persistent kernel per solve, register-fused power-of-two transforms"}
+
+
+def measure(args, name, dev, world, rank, local, with_e2e=True):
+    """Time args.steps forward + adjoint pairs of workload ``name`` after args.warmup untimed ones
+    (CUDA events on the launching stream, L2 flushed between timed steps, clocks sampled), with the
+    dominant kernel's roofline and the end-to-end variant through host buffers.  Returns
+    (record, operator, problem)."""
     import torch
     import torch.distributed as dist
 
-    world, rank, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_1603_02329_gb300 import build
     from paper_1603_02329_gb300.api import PATOperator
 
-    if rank == 0:
-        build.build()
-    if world > 1:
-        dist.barrier()
-    pb, prec, desc = workload(args.workload, rank)
+    pb, prec, desc = workload(name, rank)
     if args.nt > 0:
         pb.Nt = args.nt
         desc = dict(desc, Nt=args.nt, workload=desc["workload"] + f" [time axis cut to Nt={args.nt}]")
@@ -480,12 +535,9 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    for _ in range(max(args.warmup, 1)):
         op.forward(x, out=data, stream=stream)
         op.adjoint(data, out=grad, stream=stream)
-
-    for _ in range(max(args.warmup, 1)):
-        step()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -499,15 +551,14 @@ def main():
         flush.zero_()                       # evict L2 between timed steps (outside the events)
         ev[k][0].record(stream)
         op.forward(x, out=data, stream=stream)
-        fwd_probe_ready = True
         op.adjoint(data, out=grad, stream=stream)
         ev[k][1].record(stream)
         torch.cuda.synchronize()
-        if args.probe_stride > 0 and fwd_probe_ready:
-            # the forward graph's probe events are final once the step has completed; the adjoint's too
+        if args.probe_stride > 0:
+            # the probe events of both graphs are final once the step has completed
             for g, tag in ((0, "fwd"), (1, "adj")):
-                for name, ms, cnt in op.probe(bool(g)):
-                    acc = probe_acc.setdefault((tag, name), [0.0, 0])
+                for kname, ms, cnt in op.probe(bool(g)):
+                    acc = probe_acc.setdefault((tag, kname), [0.0, 0])
                     acc[0] += ms * cnt
                     acc[1] += cnt
     torch.cuda.synchronize()
@@ -521,7 +572,7 @@ def main():
 
     # e2e: the same step through the C ABI with host buffers (pinned), copies inside the timing
     e2e = None
-    if not args.no_e2e:
+    if with_e2e and not args.no_e2e:
         xh = torch.tensor(pb.p0, dtype=dtype).pin_memory()
         dh = torch.empty((pb.Nt, op.Ns), dtype=dtype).pin_memory()
         gh = torch.empty(pb.shape, dtype=dtype).pin_memory()
@@ -542,6 +593,7 @@ def main():
         nb_out = pb.Nt * op.Ns * w + pb.N * w      # data from H, gradient from H^T
         e2e = {"value": aggregate_gpts(units_rank, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": nb_in,
                "d2h_bytes_per_step": nb_out}
+    del flush
 
     # roofline of the dominant kernel (largest share of the probed step time)
     peak, peak_kind = measured_peaks()
@@ -550,28 +602,28 @@ def main():
     roof = None
     kernels = {}
     if probe_acc:
-        for (tag, name), (sm, cnt) in probe_acc.items():
-            kernels[f"{tag}:{name}"] = sm / max(cnt, 1)
+        for (tag, kname), (sm, cnt) in probe_acc.items():
+            kernels[f"{tag}:{kname}"] = sm / max(cnt, 1)
         dom = max(kernels, key=lambda k: kernels[k])
-        tag, name = dom.split(":")
-        if name.startswith("k_persist"):
+        tag, kname = dom.split(":")
+        if kname.startswith("k_persist"):
             b = solve_bytes(pb.N, pb.Nt, w, D=len(pb.shape), lossy=op.lossy)
         else:
-            b = kernel_bytes(name, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
+            b = kernel_bytes(kname, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
         ms = kernels[dom]
         ach = b / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": measured_traffic(args.workload, name) if not args.nt else None,
+                "traffic": measured_traffic(name, kname) if not args.nt else None,
                 "kernel": dom, "kernel_ms": ms, "algorithmic_bytes": b,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "note": ("one persistent launch per solve keeps the state in shared memory (DRAM traffic: "
                          "the set-up loads); the fraction is effective bandwidth of the algorithmic bytes"
-                         if name.startswith("k_persist") else
+                         if kname.startswith("k_persist") else
                          "algorithmic bytes of this kernel's operands (read and written once) per launch")}
     # whole-step roofline by the per-point-step algorithmic bytes (state once + medium once)
     B_pt = (2 * (2 * len(pb.shape) + 1) + (4 if op.lossy else 2)) * w
     step_roof = {"bytes_per_pt_step": B_pt, "achieved_gbs": value * 1e9 * B_pt / 1e9 / world,
-                 "frac": value * B_pt / world / peak}
+                 "frac": value * B_pt / world / peak, "peak": peak, "unit": "GB/s"}
 
     # per time step of the graph path: (3 or 2) spectral operations of 1 (2-D) or 3 (3-D: y, z, y)
     # launches, and as many row kernels
@@ -580,31 +632,72 @@ def main():
     persistent = int(op.info.path) >= 1
     # per solve: the persistent kernel or the graph's kernels, and the non-finite scan of the output
     launches = args.steps * 2 * ((1 if persistent else (1 + (pb.Nt - 1) * slots_f)) + 1)
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+    rec = {"value": value, "unit": UNIT, "ms_per_step": total_s * 1e3 / args.steps, "dtype": prec,
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
                           layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
-                          parallelism=f"replicas x{world}",
-                          path={0: "CUDA graph of per-phase kernels", 1: "persistent kernel per solve",
-                                2: "persistent kernel per solve, register-fused power-of-two transforms"}[int(op.info.path)]),
-           "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels,
-           "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+                          parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)]),
+           "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels, "e2e": e2e,
+           "gpu_launches": launches, "clocks": clk}
+    return rec, op, pb
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_02329_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    rec, op, pb = measure(args, args.workload, dev, world, rank, local)
+    out = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic"}
+    out.update({k: rec[k] for k in ("config", "roofline", "step_roofline", "kernel_ms", "e2e", "gpu_launches",
+                                    "clocks")})
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, pb)
-    if args.mg and rank == 0:
+    x = None
+    if args.trace > 0 and rank == 0 and int(op.info.path) >= 1:
+        import torch as _t
+
+        dtype = _t.float32 if rec["dtype"] == "f32" else _t.float64
+        x = _t.tensor(pb.p0, dtype=dtype, device=dev)
+        data = _t.empty((pb.Nt, op.Ns), dtype=dtype, device=dev)
+        out["phase_trace"] = phase_trace(op, x, data, _t.cuda.current_stream(dev), args.trace)
+    if args.c2grad > 0 and rank == 0:
+        out["c2_gradient"] = c2_gradient_timing(op, pb, args.c2grad, dev,
+                                                torch.float32 if rec["dtype"] == "f32" else torch.float64)
+    op.close()
+    del op
+    torch.cuda.empty_cache()
+    if rank == 0 and args.workload == "tube3d_256" and not args.no_secondary and not args.nt:
+        rec2, op2, _ = measure(args, "vessel2d_512", dev, 1, 0, local, with_e2e=True)
+        op2.close()
+        rec2["steps"], rec2["warmup"] = args.steps, args.warmup
+        out["vessel2d_512"] = rec2
+    if (args.mg or args.mg_default) and rank == 0:
         out["mg_vs_fista"] = mg_vs_fista(args, dev, pb)
+        out["mg_precision"] = mg_precision(dev)
     if args.batch and rank == 0:
         out["batch"] = batch_vs_sequential(dev)
-    if args.c2grad > 0 and rank == 0:
-        out["c2_gradient"] = c2_gradient_timing(op, pb, args.c2grad, dev, dtype)
-    if args.trace > 0 and rank == 0 and persistent:
-        out["phase_trace"] = phase_trace(op, x, data, stream, args.trace)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
-    op.close()
 
 
 if __name__ == "__main__":

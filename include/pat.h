@@ -119,7 +119,9 @@ pat_status pat_plan_get_info(const pat_plan* plan, pat_plan_info_t* info);
 /* pat_forward_plan -- data = H p0 (Sec. III: H[p0] = M w p; forward model of Sec. II.A).
  *   p0    [N]      initial pressure (host or device, plan precision).
  *   data  [Nt][Ns] output, overwritten (host or device, plan precision).
- * Runs the whole Nt-step solve as one CUDA-graph launch on `stream`. */
+ * Runs the whole Nt-step solve on `stream` as one launch: a persistent kernel for 2-D plans whose
+ * state fits in the GPU's shared memory (pat_plan_info_t.path 1 or 2), otherwise one CUDA-graph
+ * launch of the per-phase kernels (path 0). */
 pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* stream);
 
 /* pat_adjoint -- grad = H^T residual (Sec. III, Eq. (adjj); Sec. IV, Eq. (Six) uses it as
@@ -343,8 +345,9 @@ int pat_plan_probe_slots(const pat_plan* plan, int adjoint);
 pat_status pat_plan_probe_read(pat_plan* plan, int adjoint, int slot, const char** name, double* mean_ms,
                                int* samples);
 
-/* Size of the fixed device scratch array that pat_forward_static works in: 32 MiB in every GPU's
- * memory, held from the first use of the library on that GPU until the process exits. */
+/* Size of the fixed device scratch array that pat_forward_static works in: 32 MiB in the memory of
+ * every GPU where the library's device code is loaded, held until the process exits.  With lazy
+ * module loading (CUDA's default) that happens at the first pat_forward_static call on the GPU. */
 #define PAT_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
 /* pat_forward_static -- pat_forward for callers that cannot allocate device memory.  The paper
@@ -363,7 +366,12 @@ pat_status pat_plan_probe_read(pat_plan* plan, int adjoint, int slot, const char
  *     before any device work (for scale: a 2-D 512^2 FP32 absorbing problem with Nt = 2000 and
  *     512 sensors needs about 21 MB).
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture on the device.
+ *     with that device current.  That lookup loads the library's device code and the array on the
+ *     GPU, so the driver reserves the array's memory then: make one call at start-up, before a pool
+ *     allocator takes the device's memory and before any stream capture on the device.  If the
+ *     device has no room left for it, the call returns PAT_ENOMEM.
+ *   - The plan tables are written with the legacy default stream and waited for before the solve,
+ *     so `stream` may be any stream, non-blocking ones included.
  *   - Every call on a device shares that device's array, and the array keeps the last call's
  *     contents.  Calls that overlap on the same GPU (for example from several host threads) race
  *     on it: serialise them. */

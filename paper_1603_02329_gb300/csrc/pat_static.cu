@@ -37,8 +37,16 @@ static pat_status static_scratch_address(unsigned char** out) {
     }
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_addr[dev]) {
+        // With lazy module loading (the default), this lookup is what loads the library's device
+        // module on this GPU, and with it the array: the driver reserves the array's memory here.
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_pat_static_scratch);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            set_error("cudaGetSymbolAddress (static scratch): the device has no room left to load the "
+                      "library's scratch array; make the first call at start-up, before a pool takes the memory");
+            return PAT_ENOMEM;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
         g_static_addr[dev] = p;
     }
@@ -67,10 +75,19 @@ extern "C" pat_status pat_forward_static(const void* p0, const double* c, const 
     if (st != PAT_OK) return st;
     PlanBase* plan = make_plan_arena(h, arena, (size_t)PAT_STATIC_SCRATCH_BYTES, &st);
     if (!plan) return st;
+    // Building the plan wrote its tables with cudaMemcpy from pageable memory and cleared the
+    // spectra with cudaMemset, both on the legacy default stream: either may still be in flight
+    // when it returns.  The caller's stream may be a non-blocking one that does not order after
+    // the legacy stream, so wait for that work here, before the first kernel reads it.
+    cudaError_t e = cudaStreamSynchronize(cudaStreamLegacy);
+    if (e != cudaSuccess) {
+        delete plan;
+        return cuda_fail(e, "cudaStreamSynchronize (plan set-up)");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nimg = (size_t)h.info.N * plan->elem;
     const size_t ndat = (size_t)h.Nt * h.Ns * plan->elem;
-    cudaError_t e = cudaMemcpyAsync(plan->img_ptr, p0, nimg, cudaMemcpyDefault, s);
+    e = cudaMemcpyAsync(plan->img_ptr, p0, nimg, cudaMemcpyDefault, s);
     if (e != cudaSuccess) st = cuda_fail(e, "copy p0");
     if (st == PAT_OK) st = plan_clear_finite(plan, s);
     if (st == PAT_OK) st = plan_forward_direct(plan, s);

@@ -124,17 +124,51 @@ def test_mg_fista_matches_oracle_f64(dev, variant, recursion, iters):
     assert x.cpu().numpy().min() >= -1e-12
 
 
-def test_mg_fista_f32_close_to_oracle(dev):
+@pytest.mark.parametrize("recursion", [False, True])
+def test_mg_fista_f32_iterates_match_oracle(dev, recursion):
+    # FP32 fields with FP64 scalars: every iterate x_1 .. x_5 of FISTA and of two-level MG-FISTA within
+    # 1e-5 relative L2 of the FP64 oracle's, with the same branch sequence
     from paper_1603_02329_gb300.api import mg_fista
 
     pb, ref, phat, L, coarse, op, opc = _mg_setup(dev, "f32")
-    oo = po.FistaOpts(variant=1, max_iter=5, eps_d=-1.0)
+    errs = []
+    for k in range(1, 6):
+        oo = po.FistaOpts(variant=1, max_iter=k, eps_d=-1.0, recursion=recursion)
+        x_ref, recs = po.mg_fista(ref, phat, np.zeros(pb.shape), L, oo, coarse=coarse if recursion else None,
+                                  p_exact=pb.p0)
+        x, rep, grecs = mg_fista(op, opc if recursion else None, T(phat, dev, torch.float32),
+                                 T(np.zeros(pb.shape), dev, torch.float32), L, L_coarse=coarse[2], max_iter=k,
+                                 eps_d=-1.0, recursion=recursion, p_exact=T(pb.p0, dev, torch.float32))
+        assert [r["branch"] for r in grecs] == [r.branch for r in recs]
+        assert rep["iters"] == k
+        errs.append(rel(x.cpu().numpy(), x_ref))
+        for a, b in zip(grecs, recs):
+            assert abs(a["F"] - b.F) <= 1e-5 * abs(b.F)
+    print("FP32 iterate error vs FP64 oracle (recursion=%s):" % recursion, ["%.2e" % e for e in errs])
+    if recursion:
+        assert any(r.branch == "recursive" for r in recs)
+    assert max(errs) <= 1e-5, errs
+
+
+def test_mg_fista_unweighted_coarse_term_matches_oracle_f64(dev):
+    # the coarse objective exactly as Eq. (Fourteen) prints it: data term weight 1 (coarse_weight = 1)
+    # instead of reading O11's 2^(1-d)
+    from paper_1603_02329_gb300.api import mg_fista
+
+    pb, ref, phat, L, coarse, op, opc = _mg_setup(dev, "f64")
+    oo = po.FistaOpts(variant=1, max_iter=6, eps_d=-1.0, coarse_weight=1.0, kappa=0.25)
     x_ref, recs = po.mg_fista(ref, phat, np.zeros(pb.shape), L, oo, coarse=coarse, p_exact=pb.p0)
-    x, rep, grecs = mg_fista(op, opc, T(phat, dev, torch.float32), T(np.zeros(pb.shape), dev, torch.float32), L,
-                             L_coarse=coarse[2], max_iter=5, eps_d=-1.0, p_exact=T(pb.p0, dev, torch.float32))
+    x, rep, grecs = mg_fista(op, opc, T(phat, dev), T(np.zeros(pb.shape), dev), L, L_coarse=coarse[2],
+                             p_exact=T(pb.p0, dev), max_iter=6, eps_d=-1.0, coarse_weight=1.0, kappa=0.25)
     assert [r["branch"] for r in grecs] == [r.branch for r in recs]
-    assert rel(x.cpu().numpy(), x_ref) <= 1e-4
-    assert rep["iters"] == 5 and rep["fwd_solves"] >= 6
+    assert any(r.branch == "recursive" for r in recs)
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-9
+    for a, b in zip(grecs, recs):
+        assert abs(a["F"] - b.F) <= 1e-9 * abs(b.F)
+    # and it is a different run from the default weight's
+    x_w, _, _ = mg_fista(op, opc, T(phat, dev), T(np.zeros(pb.shape), dev), L, L_coarse=coarse[2],
+                         p_exact=T(pb.p0, dev), max_iter=6, eps_d=-1.0, kappa=0.25)
+    assert rel(x_w.cpu().numpy(), x.cpu().numpy()) > 1e-6
 
 
 @pytest.mark.parametrize("q_c", [8, 1])

@@ -178,25 +178,24 @@ def test_disc_phantom_168_f64_full_size(dev):
     assert rel(g, ref.adjoint(d_ref)) <= TOL64
 
 
-def test_vessel_512_full_size_prefix_and_dot(dev):
+def test_vessel_512_full_size_and_dot(dev):
     # 512^2 heterogeneous absorbing medium, Nt = 2000, 512 line sensors: the launch configuration
-    # the benchmark times.  Prefix of K samples vs the oracle (causality), adjoint of a residual
-    # supported on that prefix vs the oracle, and the dot identity over all 2000 samples.  The first
-    # arrival at the sensor row is near step 300 (the phantom starts 76 px away, ~4 steps per px);
-    # K = 500 puts 200 steps of arrived signal in the prefix, so the comparison is not dominated by
-    # the pre-arrival floor (data ~1e-4 of the field, where FP32 rounding of the field dominates).
+    # the benchmark times, compared with the oracle over the whole record (all 2000 samples, about
+    # 35 s of oracle per solve): the forward data, the adjoint of a residual over all 2000 samples,
+    # and the dot identity.  The late part of the record (after the first arrival near step 300:
+    # the phantom starts 76 px away, ~4 steps per px) is also compared on its own.
     pb = synth.vessel_phantom_2d()
-    K = 500
-    ref = Operator.from_problem(pb, Nt=K)
+    ref = Operator.from_problem(pb)
     op = _gpu_op(pb, "f32", dev)
     d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
     assert d.shape == (2000, 512)
-    assert rel(d[:K], ref.forward(pb.p0)) <= TOL32
+    d_ref = ref.forward(pb.p0)
+    assert rel(d, d_ref) <= TOL32
+    assert rel(d[1000:], d_ref[1000:]) <= TOL32
     rng = np.random.default_rng(12)
-    h = np.zeros((pb.Nt, op.Ns))
-    h[:K] = rng.standard_normal((K, op.Ns))
+    h = rng.standard_normal((pb.Nt, op.Ns))
     g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
-    assert rel(g, ref.adjoint(h[:K])) <= TOL32
+    assert rel(g, ref.adjoint(h)) <= TOL32
     x = _t(rng.standard_normal(pb.shape), "f32", dev)
     hh = _t(rng.standard_normal((pb.Nt, op.Ns)), "f32", dev)
     Hx = op.forward(x).double()

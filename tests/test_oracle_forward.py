@@ -202,6 +202,58 @@ def test_pml_damps_outgoing_energy():
     assert e_pml < 1e-2 * e_per
 
 
+# PML pins (reading R3; Sec. VI.A fixes the thickness, 20 points, and the maximum, 2 Np per grid
+# point).  (1) One step from a constant field: D+ of a constant is zero, so u stays zero and each
+# split density only decays, rho_x^1 = exp(-sigma dt) rho_x^0, while rho_y^1 = rho_y^0; in 2-D
+# p^1 = p0 (1 + exp(-sigma dt)) / 2 in closed form.  From the recorded p^1 the damping rate per grid
+# point of travel, sigma h / c_ref, is read back at every node of a 64-point x axis: the paper's
+# 2 Np at the outer node of each side, alpha (depth / P)^4 inside the layer, and exactly P damped
+# nodes per side (a shifted depth or a wrong c_ref / h scaling moves the edge value).
+def test_pml_damping_rate_from_one_step_closed_form():
+    nx, ny, P, alpha = 64, 4, 20, 2.0
+    h, c = 1e-4, 1500.0
+    dt = 0.3 * h / c
+    idx = np.arange(nx)                       # row y = 0, every x
+    op = Operator((ny, nx), (h, h), (0, P), alpha, c, 1000.0, 0.0, 1.5, dt, 2, sensor_index=idx)
+    s1 = op.forward(np.ones((ny, nx)))[1]
+    rate = -np.log(2.0 * s1 - 1.0) * h / (c * dt)     # sigma h / c_ref [Np per grid point]
+    assert abs(rate[0] - 2.0) < 1e-9 and abs(rate[-1] - 2.0) < 1e-9
+    depth = np.maximum(np.maximum(P - idx, idx - (nx - 1 - P)), 0)
+    assert np.allclose(rate, alpha * (depth / P) ** 4, atol=1e-9)
+    assert np.count_nonzero(rate[: nx // 2] > 1e-12) == P and np.count_nonzero(rate[nx // 2:] > 1e-12) == P
+
+
+# (2) A plane pulse crossing the layer.  A Gaussian pulse (width 6 h, uniform in y) splits into two
+# halves that run through the x layers on both sides of the periodic grid and meet again at the
+# centre after one period, attenuated by exp(-G) with G = int sigma / c dx over both layers.  For
+# the quartic profile the continuum integral is 2 alpha P / 5 (alpha in Np per point, P points); the
+# sampled profile adds an edge term that does not depend on P, so thickening the layer from P to 2P
+# adds exactly 2 alpha P / 5.  Measured with alpha = 0.05 and P = 20, 40: 0.399 against 0.4.  A
+# profile exponent m would add 2 alpha P / (m + 1); a c_ref / h slip scales it.  With the paper's
+# 2 Np per point the pulse is absorbed and what returns from the layer's inner edge is below 1e-5.
+def _pml_pulse(alpha, P, nx=512, ny=4, h=1e-4, c=1500.0):
+    dt = 0.3 * h / c
+    n_period = int(round(nx * h / (c * dt)))
+    x = np.arange(nx)
+    p0 = np.repeat(np.exp(-0.5 * ((x - nx // 2) / 6.0) ** 2)[None, :], ny, axis=0)
+    op = Operator((ny, nx), (h, h), (0, P), alpha, c, 1000.0, 0.0, 1.5, dt, n_period + 40,
+                  sensor_index=np.array([nx // 2]))
+    s = op.forward(p0)[:, 0]
+    n_refl = int(round(2 * (nx // 2 - P) * h / (c * dt)))
+    return s[n_period - 30:n_period + 30].max(), np.abs(s[n_refl - 40:n_refl + 40]).max()
+
+
+def test_pml_attenuation_grows_by_the_continuum_integral():
+    alpha = 0.05
+    t20, _ = _pml_pulse(alpha, 20)
+    t40, _ = _pml_pulse(alpha, 40)
+    extra = np.log(t20) - np.log(t40)
+    assert abs(extra - 2 * alpha * 20 / 5) < 0.01 * (2 * alpha * 20 / 5)
+    assert 0.5 < t20 < 0.8                            # it does cross the layer
+    t_paper, refl = _pml_pulse(2.0, 20)
+    assert t_paper < 1e-6 and refl < 1e-5
+
+
 # Blackman window B(q) at the radii where it has a short closed form: B(0) = 1,
 # B(1/3) = 0.42 + 0.5/2 - 0.08/2 = 0.63, B(1/2) = 0.42 - 0.08 = 0.34, B(q >= 1) = 0.
 # Grid (Ny, Nx) = (24, 32) with spacing (1e-4, 2e-4): the cut-off radius is the Nyquist

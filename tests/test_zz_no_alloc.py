@@ -37,21 +37,34 @@ def _args(pb, dev, dtype):
     return keep
 
 
-def _call(fn, k, pb, prec, dev, dtype):
+def _call(fn, k, pb, prec, dev, dtype, stream=None):
     dp = ctypes.POINTER(ctypes.c_double)
-    out = torch.full((pb.Nt, k["sens"].count), float("nan"), dtype=dtype, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(s):
+        out = torch.full((pb.Nt, k["sens"].count), float("nan"), dtype=dtype, device=dev)
     st = fn(ctypes.c_void_p(k["p0"].data_ptr()), k["c"].ctypes.data_as(dp), k["rho"].ctypes.data_as(dp),
             k["a0"].ctypes.data_as(dp), 0, float(pb.y), ctypes.byref(k["grid"]), ctypes.byref(k["sens"]),
-            float(pb.dt), int(pb.Nt), prec, ctypes.c_void_p(out.data_ptr()),
-            ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+            float(pb.dt), int(pb.Nt), prec, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
     torch.cuda.synchronize(dev)
     return st, out
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_static_forward_matches_allocating_forward(prec):
-    from paper_1603_02329_gb300 import build, _lib
+def _problem(kind):
     from paper_1603_02329_gb300 import synth
+
+    if kind == "2d":
+        return synth.small_lossy_2d(shape=(64, 72), pml=8, Nt=150, n_sensors=24)
+    # 3-D: x-lines of 32 points (the register-fused row kernels), an on-grid planar array
+    return synth.small_lossy_3d(shape=(28, 24, 32), pml=4, Nt=40)
+
+
+# "nonblocking": the caller's stream does not order after the legacy default stream, on which the
+# plan's tables are written; the entry point must wait for them itself
+@pytest.mark.parametrize("stream_kind", ["default", "nonblocking"])
+@pytest.mark.parametrize("kind", ["2d", "3d"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_static_forward_matches_allocating_forward(prec, kind, stream_kind):
+    from paper_1603_02329_gb300 import build, _lib
 
     build.build()
     L = _lib.lib()
@@ -60,12 +73,14 @@ def test_static_forward_matches_allocating_forward(prec):
     dtype = torch.float64 if prec == "f64" else torch.float32
     code = _lib.PAT_F64 if prec == "f64" else _lib.PAT_F32
     tol = 1e-11 if prec == "f64" else 1e-5
-    pb = synth.small_lossy_2d(shape=(64, 72), pml=8, Nt=150, n_sensors=24)
+    pb = _problem(kind)
     k = _args(pb, dev, dtype)
     st, ref = _call(L.pat_forward, k, pb, code, dev, dtype)
     assert st == 0, L.pat_last_error()
+    assert torch.isfinite(ref).all() and ref.abs().max() > 0
+    stream = torch.cuda.Stream(dev) if stream_kind == "nonblocking" else None
     for _ in range(2):  # two calls in a row share (and reuse) the scratch array
-        st, out = _call(L.pat_forward_static, k, pb, code, dev, dtype)
+        st, out = _call(L.pat_forward_static, k, pb, code, dev, dtype, stream=stream)
         assert st == 0, L.pat_last_error()
         err = (torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double())).item()
         assert err <= tol

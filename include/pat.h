@@ -172,6 +172,31 @@ pat_status pat_plan_smooth(pat_plan* plan, const void* x, void* y, void* stream)
 pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_p0,
                            int checkpoint_every, void* stream);
 
+/* pat_gradient_rho -- density sensitivity: grad_rho = d<H p0, h>/d(rho0) at every grid point, and
+ * grad_p0 = H^T h from the same reverse sweep.  Like pat_gradient_c2, this follows from Sec. III's
+ * adjoint-state construction applied to the discrete forward map, for the joint reconstruction of
+ * the medium that Sec. VII motivates; the paper states no medium gradient.  Held fixed: c0, alpha0,
+ * y, p0 and the plan's reference speed, dt, kappa and PML; tau and eta depend on c0 only
+ * (Eq. (Twelve)).  rho0 enters the step in three places: b_xi = 2 / (rho0 + rho0 shifted by one point
+ * along xi) in the momentum update and in u^{-1/2} = (dt/2) b D+ p0, -dt rho0 e_xi in the mass
+ * update (e_xi = D-_xi u_xi), and dd = rho0 sum e_xi in the absorption term (Sec. II.A).  With
+ * g_xi^n = D+_xi p^n, e_xi^n = D-_xi u_xi^{n+1/2} of the forward solve and the adjoint variables
+ * u_bar, rho_bar, dd_bar of the exact transpose:
+ *     dJ/db_xi  = sum_n u_bar_xi^{n+1/2} (-dt au_xi g_xi^n) + u_bar_xi^{-1/2} (dt/2) g_xi^0,
+ *     dJ/drho0  = sum_n sum_xi e_xi^n (dd_bar^n - dt a_xi rho_bar_xi^{n+1}) + (the dJ/db part, through
+ *                 db_xi[j]/drho0[j] = db_xi[j]/drho0[j + e_xi] = -b_xi[j]^2 / 2).
+ * Checkpoints as in pat_gradient_c2 (the same K, the same extra forward solve); each recomputed
+ * segment stores g_xi and e_xi of its K steps: (K + 1) 2d N values, plus d N accumulators.  The
+ * result does not depend on K.  Arguments, memory and errors as in pat_gradient_c2 (grad_rho in
+ * place of grad_c2). */
+pat_status pat_gradient_rho(pat_plan* plan, const void* p0, const void* residual, void* grad_rho, void* grad_p0,
+                            int checkpoint_every, void* stream);
+
+/* pat_gradient_medium -- pat_gradient_c2 and pat_gradient_rho in one sweep (one extra forward solve in
+ * all): any of grad_c2, grad_rho, grad_p0 may be NULL, not all three.  Memory is the sum of the two. */
+pat_status pat_gradient_medium(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_rho,
+                               void* grad_p0, int checkpoint_every, void* stream);
+
 /* ===========================================================================================
  * Batches: several independent instances in one launch
  * ===========================================================================================

@@ -90,6 +90,10 @@ def lib() -> ctypes.CDLL:
     L.pat_plan_smooth.restype = i32
     L.pat_gradient_c2.argtypes = [vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_c2.restype = i32
+    L.pat_gradient_rho.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.pat_gradient_rho.restype = i32
+    L.pat_gradient_medium.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+    L.pat_gradient_medium.restype = i32
     L.pat_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     L.pat_batch_create.restype = i32
     L.pat_batch_destroy.argtypes = [vp]

@@ -168,6 +168,32 @@ class PATOperator:
                                         int(checkpoint_every), _stream_ptr(stream, self.device)))
         return (g, gp) if with_p0_grad else g
 
+    def gradient_rho(self, p0: torch.Tensor, residual: torch.Tensor, checkpoint_every: int = 50,
+                     with_p0_grad: bool = False, stream=None):
+        """pat_gradient_rho: d<H p0, h>/d(rho0) per grid point with forward checkpoints every
+        ``checkpoint_every`` time levels (and H^T h when ``with_p0_grad``)."""
+        g, _, gp = self.gradient_medium(p0, residual, checkpoint_every, want=("rho", "p0") if with_p0_grad else ("rho",),
+                                        stream=stream)
+        return (g, gp) if with_p0_grad else g
+
+    def gradient_medium(self, p0: torch.Tensor, residual: torch.Tensor, checkpoint_every: int = 50,
+                        want=("c2", "rho", "p0"), stream=None):
+        """pat_gradient_medium: (d<H p0, h>/d rho0, d<H p0, h>/d c0^2, H^T h) from one checkpointed sweep;
+        the entries not in ``want`` are None.  Returns (grad_rho, grad_c2, grad_p0)."""
+        self._check_in(p0, self.N, "p0")
+        self._check_in(residual, self.Nt * self.Ns, "residual")
+        mk = lambda key: torch.empty(self.shape, dtype=self.dtype, device=p0.device) if key in want else None
+        gr, gc, gp = mk("rho"), mk("c2"), mk("p0")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        with torch.cuda.device(self.device):
+            if gc is None and gr is not None:
+                check(lib().pat_gradient_rho(self._plan, ptr(p0), ptr(residual), ptr(gr), ptr(gp),
+                                             int(checkpoint_every), _stream_ptr(stream, self.device)))
+            else:
+                check(lib().pat_gradient_medium(self._plan, ptr(p0), ptr(residual), ptr(gc), ptr(gr), ptr(gp),
+                                                int(checkpoint_every), _stream_ptr(stream, self.device)))
+        return gr, gc, gp
+
     # -- optimisation shell ---------------------------------------------------------------------
     def power_iteration(self, v0: torch.Tensor, n_iter: int = 30, stream=None) -> float:
         """pat_power_iteration: sigma_max(H^T H) from the start vector v0 (device, plan dtype)."""

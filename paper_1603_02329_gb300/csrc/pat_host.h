@@ -43,8 +43,8 @@ pat_status plan_smooth_alloc(PlanBase* base);
 pat_status plan_clear_finite(PlanBase* base, cudaStream_t s);
 pat_status plan_finite_check(PlanBase* base, bool adjoint, cudaStream_t s);
 pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s);
-pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void* gc2, void* gp0, int K,
-                            cudaStream_t s);
+pat_status plan_gradient_medium(PlanBase* base, const void* p0, const void* h, void* gc2, void* grho, void* gp0,
+                                int K, cudaStream_t s);
 PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap, pat_status* st);
 pat_status plan_forward_direct(PlanBase* base, cudaStream_t s);
 pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,

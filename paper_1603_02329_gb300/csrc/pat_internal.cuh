@@ -138,6 +138,20 @@ template <typename T> struct DevPlan {
 
     DevSensors<T> sens;
 
+    // Hooks of the density-gradient sweep (readings D2-D3; nullptr = off, the default):
+    //   forward: fwd_u stores g_xi = D+_xi p^n into hk_g[xi], fwd_rho stores e_xi = D-_xi u_xi^{n+1/2}
+    //            into hk_e[xi] (the recomputed step's fields);
+    //   adjoint: adj_rho (lossy) and the lossless adjoint tail add sum_xi e_xi (dd_bar - dt a rho_bar_xi)
+    //            to hk_grho, with e_xi read from hk_ein[xi]; adj_u adds u_bar_xi (-dt au g_xi) to
+    //            hk_gb[xi] (dJ/db_xi), g_xi read from hk_gin[xi], and on the final level also
+    //            u_bar_xi^{-1/2} (dt/2) g_xi (the transpose of u^{-1/2} = (dt/2) b D+ p0).
+    T* hk_g[3];
+    T* hk_e[3];
+    const T* hk_gin[3];
+    const T* hk_ein[3];
+    T* hk_grho;
+    T* hk_gb[3];
+
     // phase-timeline trace of the persistent kernel (nullptr = off): globaltimer at entry and
     // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA
     unsigned long long* trace;

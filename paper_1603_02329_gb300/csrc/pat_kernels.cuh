@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(256) k_fwd_u(DevPlan<T> P, int R, int first) {
             const T un = au * (au * uo - dt * bb * g);
             P.u[xi][idx] = un;
             slot(out, xi * R + r, i, nx) = un;
+            if (P.hk_g[0]) P.hk_g[xi][idx] = g;
         }
     }
     __syncthreads();
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, 
             P.rh[xi][idx] = rh;
             rs += rh;
             es += e;
+            if (P.hk_e[0]) P.hk_e[xi][idx] = e;
         }
         if (P.lossy) {
             P.rsum[idx] = rs;
@@ -518,13 +520,16 @@ __device__ void adj_tail(const RowSm<T, D>& sm, const DevPlan<T>& P, cplx<T>* pb
         } else {
             const T rbar = sm.row(0)[t] * pv;
             const T rho0 = sm.row(1)[t];
+            T gr = 0;
 #pragma unroll
             for (int xi = 0; xi < D; ++xi) {
                 const T a = sm.pml_at(xi, r, i);
                 const T rb = sm.row(2 + xi)[t] + rbar;
                 slot(other, xi * R + r, i, nx) = -dt * rho0 * a * rb;
                 P.rh[xi][idx] = a * a * rb;
+                if (P.hk_grho) gr += P.hk_ein[xi][idx] * (-dt * a * rb);
             }
+            if (P.hk_grho) P.hk_grho[idx] += gr;
         }
     }
     __syncthreads();
@@ -589,13 +594,16 @@ __global__ void __launch_bounds__(256) k_adj_rho(DevPlan<T> P, int R) {
         const T w = slot(res, R + r, i, nx);
         const T rbar = sm.row(0)[t] * sm.row(2)[t] - w;
         const T rho0 = sm.row(1)[t];
+        T gr = 0;
 #pragma unroll
         for (int xi = 0; xi < D; ++xi) {
             const T a = sm.pml_at(xi, r, i);
             const T rb = sm.row(3 + xi)[t] + rbar;
             slot(out, xi * R + r, i, nx) = rho0 * ddbar - dt * rho0 * a * rb;
             P.rh[xi][idx] = a * a * rb;
+            if (P.hk_grho) gr += P.hk_ein[xi][idx] * (ddbar - dt * a * rb);
         }
+        if (P.hk_grho) P.hk_grho[idx] += gr;
     }
     __syncthreads();
     res = fft_rows<T, false>(out, res, P.fx, sm.tw, D * R / 2);
@@ -636,10 +644,17 @@ __global__ void __launch_bounds__(256) k_adj_u(DevPlan<T> P, int R, int final_) 
             const T au = sm.pml_at(xi, r, i);
             T ub = sm.row(D + xi)[t] + slot(res, xi * R + r, i, nx);
             T g = -dt * bb * au * ub;
+            const T ubn = ub;
             ub = au * au * ub;
             if (final_) g += (T)0.5 * dt * bb * ub;
             P.u[xi][idx] = ub;
             slot(out, xi * R + r, i, nx) = g;
+            if (P.hk_gb[0]) {
+                const T gv = P.hk_gin[xi][idx];
+                T add = ubn * (-dt * au * gv);
+                if (final_) add += ub * (T)0.5 * dt * gv;
+                P.hk_gb[xi][idx] += add;
+            }
         }
     }
     __syncthreads();

@@ -531,7 +531,30 @@ pat_status pat_gradient_c2(pat_plan* plan, const void* p0, const void* residual,
     PlanBase* b = plan->impl;
     if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
     DeviceGuard g(b->device);
-    return plan_gradient_c2(b, p0, residual, grad_c2, grad_p0, checkpoint_every, (cudaStream_t)stream);
+    return plan_gradient_medium(b, p0, residual, grad_c2, nullptr, grad_p0, checkpoint_every, (cudaStream_t)stream);
+}
+
+pat_status pat_gradient_rho(pat_plan* plan, const void* p0, const void* residual, void* grad_rho, void* grad_p0,
+                            int checkpoint_every, void* stream) {
+    set_error("");
+    if (!plan || !p0 || !residual || !grad_rho) return fail(PAT_EINVAL, "NULL argument");
+    if (checkpoint_every < 1) return fail(PAT_EINVAL, "checkpoint_every must be >= 1");
+    PlanBase* b = plan->impl;
+    if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
+    DeviceGuard g(b->device);
+    return plan_gradient_medium(b, p0, residual, nullptr, grad_rho, grad_p0, checkpoint_every, (cudaStream_t)stream);
+}
+
+pat_status pat_gradient_medium(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_rho,
+                               void* grad_p0, int checkpoint_every, void* stream) {
+    set_error("");
+    if (!plan || !p0 || !residual) return fail(PAT_EINVAL, "NULL argument");
+    if (!grad_c2 && !grad_rho && !grad_p0) return fail(PAT_EINVAL, "no output requested");
+    if (checkpoint_every < 1) return fail(PAT_EINVAL, "checkpoint_every must be >= 1");
+    PlanBase* b = plan->impl;
+    if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
+    DeviceGuard g(b->device);
+    return plan_gradient_medium(b, p0, residual, grad_c2, grad_rho, grad_p0, checkpoint_every, (cudaStream_t)stream);
 }
 
 pat_status pat_forward(const void* p0, const double* c, const double* rho, const double* alpha0,

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                         const T un = au * (au * uo - dt * bq * g);
                         P.u[xi][idx] = un;
                         out[xi] = un;
+                        if (P.hk_g[0]) P.hk_g[xi][idx] = g;
                     }
                 });
                 break;
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                         P.rh[xi][idx] = rh;
                         rs += rh;
                         es += e;
+                        if (P.hk_e[0]) P.hk_e[xi][idx] = e;
                     }
                     if (lossy) {
                         P.rsum[idx] = rs;
@@ -281,13 +283,16 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                     const T ddbar = in[0];
                     const T rbar = row(0)[t] * row(2)[t] - in[1];
                     const T rho0 = row(1)[t];
+                    T gr = 0;
 #pragma unroll
                     for (int xi = 0; xi < D; ++xi) {
                         const T aa = pml(xi, r, x);
                         const T rb = row(3 + xi)[t] + rbar;
                         out[xi] = rho0 * ddbar - dt * rho0 * aa * rb;
                         P.rh[xi][idx] = aa * aa * rb;
+                        if (P.hk_grho) gr += P.hk_ein[xi][idx] * (ddbar - dt * aa * rb);
                     }
+                    if (P.hk_grho) P.hk_grho[idx] += gr;
                 });
                 break;
             case R2_ADJ_U:
@@ -300,10 +305,17 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                         const T au = pml(xi, r, x);
                         T ub = row(D + xi)[t] + in[xi];
                         T g = -dt * bq * au * ub;
+                        const T ubn = ub;
                         ub = au * au * ub;
                         if (first) g += (T)0.5 * dt * bq * ub;
                         P.u[xi][idx] = ub;
                         out[xi] = g;
+                        if (P.hk_gb[0]) {
+                            const T gv = P.hk_gin[xi][idx];
+                            T add = ubn * (-dt * au * gv);
+                            if (first) add += ub * (T)0.5 * dt * gv;
+                            P.hk_gb[xi][idx] += add;
+                        }
                     }
                 });
                 break;
@@ -329,13 +341,16 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                     } else {
                         const T rbar = row(0)[t] * pv;
                         const T rho0 = row(1)[t];
+                        T gr = 0;
 #pragma unroll
                         for (int xi = 0; xi < D; ++xi) {
                             const T aa = pml(xi, r, x);
                             const T rb = row(2 + xi)[t] + rbar;
                             out[xi] = -dt * rho0 * aa * rb;
                             P.rh[xi][idx] = aa * aa * rb;
+                            if (P.hk_grho) gr += P.hk_ein[xi][idx] * (-dt * aa * rb);
                         }
+                        if (P.hk_grho) P.hk_grho[idx] += gr;
                     }
                 });
                 break;

@@ -13,6 +13,29 @@
 
 namespace pat {
 
+// dJ/drho0 += the part through b_xi[j] = 2 / (rho0[j] + rho0[j + e_xi]) (periodic): with
+// B_xi = dJ/db_xi * (-b_xi^2 / 2), point j receives B_xi[j] (its own b) + B_xi[j - e_xi] (the b of
+// the point before it along xi) (reading D3).
+template <typename T> __global__ void k_rho_chain(DevPlan<T> P, const T* gb, T* grho) {
+    const long long N = P.N;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(j % P.nx);
+        const long long yz = j / P.nx;
+        const int y = (int)(yz % P.ny), z = (int)(yz / P.ny);
+        T acc = 0;
+        for (int a = 0; a < P.d; ++a) {
+            long long jm;
+            if (a == 0) jm = j - x + (x == 0 ? P.nx - 1 : x - 1);
+            else if (a == 1) jm = j + (long long)((y == 0 ? P.ny - 1 : y - 1) - y) * P.nx;
+            else jm = j + (long long)((z == 0 ? P.nz - 1 : z - 1) - z) * P.nx * P.ny;
+            const T* g = gb + (size_t)a * N;
+            const T b0 = P.b[a][j], b1 = P.b[a][jm];
+            acc += g[j] * (T(-0.5) * b0 * b0) + g[jm] * (T(-0.5) * b1 * b1);
+        }
+        grho[j] += acc;
+    }
+}
+
 template <typename T> struct Plan : public PlanBase {
     DevPlan<T> P{};
     HostTables H;   // kept for the FP64 tables' sizes and for rebuilding
@@ -709,27 +732,40 @@ template <typename T> struct Plan : public PlanBase {
     // adjoint iteration that produces p_bar^n (the reverse of forward step n), accumulating
     // g_c2 += p_bar^n q^n (n >= 1) or, at n = 0, the initial-density term
     template <int D> void adj_step_on(int n, const T* qrow, T* gc2, const T* p0c, cudaStream_t s) {
-        if (P.lossy) {
-            spectral_on<D, SPEC_ABS>(P, s);
-            row_launch<D>(R2_ADJ_RHO, P, s, 0);
+        adj_step_q<D>(P, n, qrow, gc2, p0c, s);
+    }
+    // the same on the state of Q (P with the density-gradient hooks of this level set)
+    template <int D> void adj_step_q(const DevPlan<T>& Q, int n, const T* qrow, T* gc2, const T* p0c, cudaStream_t s) {
+        if (Q.lossy) {
+            spectral_on<D, SPEC_ABS>(Q, s);
+            row_launch<D>(R2_ADJ_RHO, Q, s, 0);
         }
-        spectral_on<D, SPEC_DIVT>(P, s);
-        row_launch<D>(R2_ADJ_U, P, s, (int)(n == 0));
-        spectral_on<D, SPEC_GRADT>(P, s);
-        row_launch<D>(R2_ADJ_P, P, s, (int)(n == 0), nullptr, (const T*)(P.data + (size_t)n * H.Ns),
+        spectral_on<D, SPEC_DIVT>(Q, s);
+        row_launch<D>(R2_ADJ_U, Q, s, (int)(n == 0));
+        spectral_on<D, SPEC_GRADT>(Q, s);
+        row_launch<D>(R2_ADJ_P, Q, s, (int)(n == 0), nullptr, (const T*)(Q.data + (size_t)n * H.Ns),
                       n == 0 ? (T*)nullptr : (T*)qrow, gc2, p0c);
     }
 
-    // g_c2 = d<H p0, h>/d c0^2 and grad_p0 = H^T h in one reverse sweep; forward states are
-    // checkpointed every K levels (levels 0, K, 2K, ...) and each segment (jK, (j+1)K] is recomputed
-    // from its checkpoint, storing q^n, right before the adjoint iterations that consume it.
-    template <int D> pat_status gradient_c2(const void* p0, const void* h, void* gc2_out, void* gp0_out, int K,
-                                            cudaStream_t s) {
+    // Medium gradients and grad_p0 = H^T h in one reverse sweep: g_c2 = d<H p0, h>/d c0^2 (readings
+    // M1-M3) and g_rho = d<H p0, h>/d rho0 (readings D1-D3), either output optional.  Forward states
+    // are checkpointed every K levels (levels 0, K, 2K, ...); each segment (jK, (j+1)K] is recomputed
+    // from its checkpoint right before the adjoint iterations that consume it, storing q^n = dp^n/dc0^2
+    // (c0^2 gradient) and g_xi = D+ p^n, e_xi = D- u^{n+1/2} of its steps (density gradient).
+    //
+    // The adjoint iteration of step n (level n -> n+1) reads g and e of step n; the lossless adjoint
+    // tail that ends it does the density part of step n - 1 and reads e of step n - 1.  Segment j
+    // recomputes steps lo .. hi-1 into slots 0 .. K-1 and its adjoint iterations run steps hi .. lo+1,
+    // so step hi (slot 0 of segment j+1, recomputed earlier) is carried into slot K first.
+    template <int D> pat_status gradient_medium(const void* p0, const void* h, void* gc2_out, void* grho_out,
+                                                void* gp0_out, int K, cudaStream_t s) {
         const int Nt = H.Nt, Ns = H.Ns;
         const size_t N = (size_t)P.N, Nh = (size_t)H.nz * H.ny * H.ldh;
         const int nspec = std::max(D, 2);
         const int nseg = (Nt > 1) ? (Nt - 2) / K + 1 : 0;    // segments of levels 1 .. Nt-1
         const size_t ck_elems = 2 * D * N + Nh * 2;           // u, rho (real) and the p spectrum
+        const bool want_c2 = gc2_out != nullptr, want_rho = grho_out != nullptr;
+        const size_t ge_slot = 2 * (size_t)D * N;             // g_xi, e_xi of one step
         std::vector<void*> own;
         auto alloc = [&](size_t bytes) -> void* {
             void* ptr = nullptr;
@@ -742,12 +778,26 @@ template <typename T> struct Plan : public PlanBase {
             for (void* ptr : own) cudaFree(ptr);
         };
         T* p0buf = (T*)alloc(N * sizeof(T));
-        T* gc2 = (T*)alloc(N * sizeof(T));
         T* junk = (T*)alloc((size_t)std::max(Ns, 1) * sizeof(T));
-        T* qbuf = (T*)alloc((size_t)std::max(1, std::min(K, Nt)) * N * sizeof(T));
         T* ckpt = (T*)alloc((size_t)std::max(nseg, 1) * ck_elems * sizeof(T));
+        T* gc2 = nullptr;
+        T* qbuf = nullptr;
+        T* grho = nullptr;
+        T* gbx = nullptr;
+        T* gebuf = nullptr;
+        bool ok = p0buf && junk && ckpt;
+        if (ok && want_c2) {
+            gc2 = (T*)alloc(N * sizeof(T));
+            qbuf = (T*)alloc((size_t)std::max(1, std::min(K, Nt)) * N * sizeof(T));
+            ok = gc2 && qbuf;
+        }
+        if (ok && want_rho) {
+            grho = (T*)alloc(N * sizeof(T));
+            gbx = (T*)alloc((size_t)D * N * sizeof(T));
+            gebuf = (T*)alloc((size_t)(std::min(K, std::max(Nt - 1, 1)) + 1) * ge_slot * sizeof(T));
+            ok = grho && gbx && gebuf;
+        }
         DevPlan<T> Pf = P;
-        bool ok = p0buf && gc2 && junk && qbuf && ckpt;
         for (int a = 0; a < D && ok; ++a) {
             ok = ok && (Pf.u[a] = (T*)alloc(N * sizeof(T))) && (Pf.rh[a] = (T*)alloc(N * sizeof(T)));
         }
@@ -766,7 +816,9 @@ template <typename T> struct Plan : public PlanBase {
         Pf.data = junk;
         cudaError_t e = cudaMemcpyAsync(p0buf, p0, N * sizeof(T), cudaMemcpyDefault, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(P.data, h, (size_t)Nt * Ns * sizeof(T), cudaMemcpyDefault, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(gc2, 0, N * sizeof(T), s);
+        if (e == cudaSuccess && gc2) e = cudaMemsetAsync(gc2, 0, N * sizeof(T), s);
+        if (e == cudaSuccess && grho) e = cudaMemsetAsync(grho, 0, N * sizeof(T), s);
+        if (e == cudaSuccess && gbx) e = cudaMemsetAsync(gbx, 0, (size_t)D * N * sizeof(T), s);
         for (int a = 0; a < D && e == cudaSuccess; ++a) {
             e = cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(P.rh[a], 0, N * sizeof(T), s);
@@ -799,6 +851,29 @@ template <typename T> struct Plan : public PlanBase {
             }
             cudaMemcpyAsync(Pf.spec[0], c + 2 * D * N, Nh * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s);
         };
+        // density hooks: slot k of gebuf holds g_xi (xi < D) then e_xi of step lo + k
+        auto gslot = [&](int k, int a) { return gebuf + (size_t)k * ge_slot + (size_t)a * N; };
+        auto eslot = [&](int k, int a) { return gebuf + (size_t)k * ge_slot + (size_t)(D + a) * N; };
+        auto fwd_hooks = [&](DevPlan<T>& Q, int k) {
+            for (int a = 0; a < 3; ++a) {
+                Q.hk_g[a] = (want_rho && a < D) ? gslot(k, a) : nullptr;
+                Q.hk_e[a] = (want_rho && a < D) ? eslot(k, a) : nullptr;
+            }
+        };
+        // adjoint hooks of the iteration of step n in a segment starting at lo (lossless tails read
+        // e of step n - 1)
+        auto adj_hooks = [&](int n, int lo) {
+            DevPlan<T> Q = P;
+            if (!want_rho) return Q;
+            const int ke = P.lossy ? n - lo : std::max(n - 1 - lo, 0);
+            for (int a = 0; a < D; ++a) {
+                Q.hk_gin[a] = gslot(n - lo, a);
+                Q.hk_ein[a] = eslot(ke, a);
+                Q.hk_gb[a] = gbx + (size_t)a * N;
+            }
+            Q.hk_grho = grho;
+            return Q;
+        };
         // (1) forward sweep to level (nseg - 1) K, checkpointing levels 0, K, ...
         launch(k_fwd_init<T, D>, dim3(G), B, row_smem, s, Pf, R, (int)(Nt == 1));
         if (nseg > 0) save(0);
@@ -813,17 +888,32 @@ template <typename T> struct Plan : public PlanBase {
         }
         for (int j = nseg - 1; j >= 0; --j) {
             const int lo = j * K, hi = std::min((j + 1) * K, Nt - 1);
+            if (want_rho && j < nseg - 1)   // step hi = slot 0 of the segment above -> slot hi - lo
+                for (int a = 0; a < 2 * D; ++a)
+                    cudaMemcpyAsync(gebuf + (size_t)(hi - lo) * ge_slot + (size_t)a * N, gebuf + (size_t)a * N,
+                                    N * sizeof(T), cudaMemcpyDeviceToDevice, s);
             restore(j);
-            for (int n = lo; n < hi; ++n) fwd_step_on<D>(Pf, n, junk, qbuf + (size_t)(n - lo) * N, s);
+            for (int n = lo; n < hi; ++n) {
+                DevPlan<T> Q = Pf;
+                fwd_hooks(Q, n - lo);
+                fwd_step_on<D>(Q, n, junk, qbuf ? qbuf + (size_t)(n - lo) * N : (T*)nullptr, s);
+            }
             int top = hi;
             if (hi == Nt - 1) {
-                launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, P, R, 0, (const T*)(P.data + (size_t)(Nt - 1) * Ns),
-                       (const T*)(qbuf + (size_t)(hi - lo - 1) * N), gc2, (const T*)p0buf);
+                DevPlan<T> Q = adj_hooks(Nt - 1, lo);   // lossless tail: density part of step Nt - 2
+                launch(k_adj_init<T, D>, dim3(G), B, row_smem, s, Q, R, 0, (const T*)(P.data + (size_t)(Nt - 1) * Ns),
+                       (const T*)(qbuf ? qbuf + (size_t)(hi - lo - 1) * N : nullptr), gc2, (const T*)p0buf);
                 top = Nt - 2;
             }
-            for (int n = top; n > lo; --n) adj_step_on<D>(n, qbuf + (size_t)(n - lo - 1) * N, gc2, p0buf, s);
+            for (int n = top; n > lo; --n)
+                adj_step_q<D>(adj_hooks(n, lo), n, qbuf ? qbuf + (size_t)(n - lo - 1) * N : nullptr, gc2, p0buf, s);
         }
-        if (Nt > 1) adj_step_on<D>(0, nullptr, gc2, p0buf, s);
+        if (Nt > 1) adj_step_q<D>(adj_hooks(0, 0), 0, nullptr, gc2, p0buf, s);
+        if (want_rho) {   // through b_xi = 2 / (rho0 + rho0 shifted along xi) (reading D3)
+            const int threads = 256;
+            const int blocks = (int)std::min<size_t>((N + threads - 1) / threads, 8192);
+            k_rho_chain<T><<<blocks, threads, 0, s>>>(P, (const T*)gbx, grho);
+        }
         e = take_launch_err();
         if (e == cudaSuccess && gp0_out && smooth) {   // (H S)^T = S H^T
             const pat_status sst = smooth_inplace(P.img, s);
@@ -832,7 +922,8 @@ template <typename T> struct Plan : public PlanBase {
                 return sst;
             }
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(gc2_out, gc2, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && gc2_out) e = cudaMemcpyAsync(gc2_out, gc2, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e == cudaSuccess && grho_out) e = cudaMemcpyAsync(grho_out, grho, N * sizeof(T), cudaMemcpyDefault, s);
         if (e == cudaSuccess && gp0_out) e = cudaMemcpyAsync(gp0_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
         release();
         if (e != cudaSuccess) return cuda_fail(e, "checkpointed gradient");
@@ -1049,16 +1140,16 @@ pat_status plan_probe_read(PlanBase* b, int g, int slot, const char** name, doub
     return PAT_OK;
 }
 
-pat_status plan_gradient_c2(PlanBase* base, const void* p0, const void* h, void* gc2, void* gp0, int K,
-                            cudaStream_t s) {
+pat_status plan_gradient_medium(PlanBase* base, const void* p0, const void* h, void* gc2, void* grho, void* gp0,
+                                int K, cudaStream_t s) {
     if (base->info.precision == PAT_F32) {
         auto* p = static_cast<Plan<float>*>(base);
-        return p->P.d == 2 ? p->template gradient_c2<2>(p0, h, gc2, gp0, K, s)
-                           : p->template gradient_c2<3>(p0, h, gc2, gp0, K, s);
+        return p->P.d == 2 ? p->template gradient_medium<2>(p0, h, gc2, grho, gp0, K, s)
+                           : p->template gradient_medium<3>(p0, h, gc2, grho, gp0, K, s);
     }
     auto* p = static_cast<Plan<double>*>(base);
-    return p->P.d == 2 ? p->template gradient_c2<2>(p0, h, gc2, gp0, K, s)
-                       : p->template gradient_c2<3>(p0, h, gc2, gp0, K, s);
+    return p->P.d == 2 ? p->template gradient_medium<2>(p0, h, gc2, grho, gp0, K, s)
+                       : p->template gradient_medium<3>(p0, h, gc2, grho, gp0, K, s);
 }
 
 pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s) {

@@ -89,3 +89,82 @@ def test_gradient_c2_edge_cases(dev):
     # invalid interval
     with pytest.raises(_lib.PatError):
         op.gradient_c2(_T(pb.p0, "f64", dev), _T(h, "f64", dev), checkpoint_every=0)
+
+
+# Density gradient (pat_gradient_rho, readings D1-D3) against oracle/pat_medium.density_gradient,
+# which is pinned by central finite differences and the scaling invariant <dJ/drho0, rho0> = 0.
+# Intervals K below Nt - 1 make several segments, so the step at each segment's top comes from the
+# segment above (the carried slot); x-lines of 48 / 36 points take the generic row kernels, 64 / 16
+# the register-fused ones.
+RHO_CASES = [
+    ("2d_lossy_f64", lambda: synth.small_lossy_2d(shape=(40, 48), pml=6, Nt=61, n_sensors=16), "f64", (7, 1, 60)),
+    ("2d_lossless_f64", lambda: synth.small_lossy_2d(shape=(32, 36), pml=4, Nt=40, n_sensors=12, alpha0=0.0),
+     "f64", (5, 39)),
+    ("2d_pow2_lossy_f64", lambda: synth.small_lossy_2d(shape=(32, 64), pml=6, Nt=45, n_sensors=16), "f64", (6, 44)),
+    ("2d_pow2_lossless_f64", lambda: synth.small_lossy_2d(shape=(32, 32), pml=4, Nt=33, n_sensors=12, alpha0=0.0),
+     "f64", (4,)),
+    ("2d_pow2_lossy_f32", lambda: synth.small_lossy_2d(shape=(64, 64), pml=8, Nt=90, n_sensors=24), "f32", (10, 13)),
+    ("3d_lossy_f64", lambda: synth.small_lossy_3d(shape=(16, 20, 24), pml=3, Nt=30), "f64", (4, 29)),
+    ("3d_pow2_lossy_f64", lambda: synth.small_lossy_3d(shape=(16, 16, 16), pml=3, Nt=25), "f64", (3,)),
+    ("3d_lossy_f32", lambda: synth.small_lossy_3d(shape=(16, 16, 16), pml=3, Nt=33), "f32", (8,)),
+]
+
+
+@pytest.mark.parametrize("name,make,prec,Ks", RHO_CASES, ids=[c[0] for c in RHO_CASES])
+def test_gradient_rho_matches_oracle(dev, name, make, prec, Ks):
+    from paper_1603_02329_gb300.api import PATOperator
+
+    pb = make()
+    ref = Operator.from_problem(pb)
+    rng = np.random.default_rng(37)
+    h = rng.standard_normal((pb.Nt, ref.Ns))
+    g_ref = pm.density_gradient(ref, pb.p0, h)
+    gp_ref = ref.adjoint(h)
+    op = PATOperator.from_problem(pb, precision=prec, device=dev)
+    tol = 1e-10 if prec == "f64" else 1e-5
+    first = None
+    for K in Ks:
+        g, gp = op.gradient_rho(_T(pb.p0, prec, dev), _T(h, prec, dev), checkpoint_every=K, with_p0_grad=True)
+        g, gp = g.cpu().numpy(), gp.cpu().numpy()
+        assert rel(g, g_ref) <= tol, (K, rel(g, g_ref))
+        assert rel(gp, gp_ref) <= tol, (K, rel(gp, gp_ref))
+        if first is None:
+            first = g
+        else:
+            assert np.array_equal(g, first)   # independent of the checkpoint interval
+    if prec == "f64":   # J(lambda rho0) = J(rho0): <dJ/drho0, rho0> = 0 (reading D3's invariant)
+        assert abs(float(np.sum(first * pb.rho))) <= 1e-9 * float(np.sum(np.abs(first * pb.rho)))
+
+
+def test_gradient_medium_one_sweep_equals_separate_sweeps(dev):
+    from paper_1603_02329_gb300.api import PATOperator
+
+    pb = synth.small_lossy_2d(shape=(32, 64), pml=6, Nt=37, n_sensors=16)
+    op = PATOperator.from_problem(pb, precision="f64", device=dev)
+    h = _T(np.random.default_rng(5).standard_normal((pb.Nt, op.Ns)), "f64", dev)
+    x = _T(pb.p0, "f64", dev)
+    gr, gc, gp = op.gradient_medium(x, h, checkpoint_every=9)
+    assert torch.equal(gr, op.gradient_rho(x, h, checkpoint_every=9))
+    assert torch.equal(gc, op.gradient_c2(x, h, checkpoint_every=9))
+    assert rel(gp.cpu().numpy(), op.adjoint(h).cpu().numpy()) <= 1e-12
+
+
+def test_gradient_rho_edge_cases(dev):
+    from paper_1603_02329_gb300 import _lib
+    from paper_1603_02329_gb300.api import PATOperator
+
+    # Nt = 1: p^0 = p0 does not depend on rho0
+    pb = synth.small_lossy_2d(shape=(24, 24), pml=3, Nt=1, n_sensors=6)
+    op = PATOperator.from_problem(pb, precision="f64", device=dev)
+    h = np.random.default_rng(2).standard_normal((1, op.Ns))
+    g = op.gradient_rho(_T(pb.p0, "f64", dev), _T(h, "f64", dev), checkpoint_every=3)
+    assert float(g.abs().max()) == 0.0
+    # Nt = 2 with K beyond the time axis: one segment of one step
+    pb = synth.small_lossy_2d(shape=(24, 24), pml=3, Nt=2, n_sensors=6)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(3).standard_normal((2, ref.Ns))
+    op = PATOperator.from_problem(pb, precision="f64", device=dev)
+    g = op.gradient_rho(_T(pb.p0, "f64", dev), _T(h, "f64", dev), checkpoint_every=50).cpu().numpy()
+    assert rel(g, pm.density_gradient(ref, pb.p0, h)) <= 1e-10
+    with pytest.raises(_lib.PatError):
+        op.gradient_rho(_T(pb.p0, "f64", dev), _T(h, "f64", dev), checkpoint_every=0)

@@ -197,6 +197,47 @@ pat_status pat_gradient_rho(pat_plan* plan, const void* p0, const void* residual
 pat_status pat_gradient_medium(pat_plan* plan, const void* p0, const void* residual, void* grad_c2, void* grad_rho,
                                void* grad_p0, int checkpoint_every, void* stream);
 
+/* pat_time_reversal -- time-reversal image (Sec. II.B.1), the paper's comparison baseline and a warm
+ * start for the iterative methods.  The measured pressure is enforced at the sensors in reversed
+ * time, p(r_s, t) = data(r_s, T - t), on the plan's grid, medium, PML, time step and reference speed,
+ * and the image is the pressure at the end (original time 0).  Readings:
+ *   - the scheme is the forward one with tau replaced by -tau, eta kept (Sec. II.B.1 reverses the
+ *     sign of the absorption term and keeps the dispersion term);
+ *   - sensors must be on grid nodes, one per node (on-grid sensors; PAT_EINVAL otherwise);
+ *   - start: p^0 = 0 except the last datum at the sensors, rho_xi^0 = p^0 / (d c0^2), u^{-1/2} = 0;
+ *     after every step the pressure at the sensor nodes is set to the next reversed datum and the
+ *     split densities to datum / (d c0^2);
+ *   - compensate = 1: with the sign reversed the absorption term amplifies each mode at the rate the
+ *     forward model damped it, which grows like |k|^y, and high-|k| rounding noise grows without
+ *     bound.  The reversed term is therefore band-limited by the radial Blackman window
+ *     W(q) = 0.42 + 0.5 cos(pi q) + 0.08 cos(2 pi q), q = |k| / k_c < 1 (0 beyond), with
+ *     k_c = k_cut * min over axes of pi / dx (0 < k_cut <= 1; 0.5 recommended).  compensate = 0 keeps
+ *     the forward sign (no window, k_cut ignored).
+ *   data  [Nt][Ns] measured data (host or device, plan precision); image [N] output.
+ * The plan's smoothing switch is not applied.  Runs the per-phase kernels on the plan's own state
+ * (the first call allocates a node map of N ints and (Nt + 1) Ns values, kept by the plan). */
+pat_status pat_time_reversal(pat_plan* plan, const void* data, void* image, int compensate, double k_cut,
+                             void* stream);
+
+/* pat_adjoint_atd -- the paper's own adjoint, "adjoint-then-discretize" (Sec. VI): the continuous
+ * adjoint system of Sec. III (Eqs. (moma), (massa), (statea), (adjj)) discretised with the same
+ * k-space staggered scheme, for comparison with the exact transpose pat_adjoint.  Readings:
+ *   - the system runs forward in adjoint time on the reversed residual h~^n = h^{Nt-1-n}, from a
+ *     zero state; the source M^T (h~^n + h~^{n+1}) / 2 enters the mass update at the half step,
+ *     shared equally by the d split densities: rho*_xi <- a (a rho*_xi - dt rho0 e*_xi + dt rho0 s / d);
+ *   - in the state equation tau and eta act before the fractional Laplacians:
+ *     p* = c0^2 sum rho* - rho0 L_{y-2}(c0^2 tau (s - sum e*)) - rho0 L_{y-1}(c0^2 eta sum rho* / rho0);
+ *   - the same split-field PML factors as the forward solve;
+ *   - initial_paper = 1: the image is rho*(T) / rho0 (Eq. (adjj)), the gradient for the paper's
+ *     initial condition c0^2 {1 - eta (-lap)^((y-1)/2)} rho(0) = p0; initial_paper = 0: the gradient
+ *     for the forward map's rho^0 = p0 / (d c0^2), g - L_{y-1}(c0^2 eta g) / c0^2 with g = rho*(T)/rho0
+ *     (identical when lossless).
+ * The data term is a plain sum over samples (no dt weight), so dt * pat_adjoint converges to this
+ * image as dt -> 0; it is not the transpose and fails the dot test by O(dt) and inside the PML.
+ *   residual [Nt][Ns] (host or device, plan precision); image [N] output.  The smoothing switch
+ * applies (S at the end).  The first call allocates (Nt + 1) Ns values kept by the plan. */
+pat_status pat_adjoint_atd(pat_plan* plan, const void* residual, void* image, int initial_paper, void* stream);
+
 /* ===========================================================================================
  * Batches: several independent instances in one launch
  * ===========================================================================================

@@ -94,6 +94,10 @@ def lib() -> ctypes.CDLL:
     L.pat_gradient_rho.restype = i32
     L.pat_gradient_medium.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_medium.restype = i32
+    L.pat_time_reversal.argtypes = [vp, vp, vp, i32, ctypes.c_double, vp]
+    L.pat_time_reversal.restype = i32
+    L.pat_adjoint_atd.argtypes = [vp, vp, vp, i32, vp]
+    L.pat_adjoint_atd.restype = i32
     L.pat_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     L.pat_batch_create.restype = i32
     L.pat_batch_destroy.argtypes = [vp]

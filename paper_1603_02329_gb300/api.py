@@ -194,6 +194,35 @@ class PATOperator:
                                                 int(checkpoint_every), _stream_ptr(stream, self.device)))
         return gr, gc, gp
 
+    def time_reversal(self, data: torch.Tensor, compensate: bool = True, k_cut: float = 0.5,
+                      out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """pat_time_reversal: the time-reversal image of data [Nt][Ns] (Sec. II.B.1; on-grid sensors),
+        with the band-limited absorption compensation when ``compensate``."""
+        self._check_in(data, self.Nt * self.Ns, "data")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=data.device)
+        self._check_in(out, self.N, "out")
+        with torch.cuda.device(self.device):
+            check(lib().pat_time_reversal(self._plan, ctypes.c_void_p(data.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          int(bool(compensate)), float(k_cut), _stream_ptr(stream, self.device)))
+        return out
+
+    def adjoint_atd(self, residual: torch.Tensor, initial: str = "R5", out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+        """pat_adjoint_atd: the paper's adjoint-then-discretize image of residual [Nt][Ns] (Sec. VI);
+        ``initial`` "R5" (the forward map's initial state) or "paper" (Eq. (adjj))."""
+        if initial not in ("R5", "paper"):
+            raise ValueError("initial must be 'R5' or 'paper'")
+        self._check_in(residual, self.Nt * self.Ns, "residual")
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device=residual.device)
+        self._check_in(out, self.N, "out")
+        with torch.cuda.device(self.device):
+            check(lib().pat_adjoint_atd(self._plan, ctypes.c_void_p(residual.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), int(initial == "paper"),
+                                        _stream_ptr(stream, self.device)))
+        return out
+
     # -- optimisation shell ---------------------------------------------------------------------
     def power_iteration(self, v0: torch.Tensor, n_iter: int = 30, stream=None) -> float:
         """pat_power_iteration: sigma_max(H^T H) from the start vector v0 (device, plan dtype)."""

@@ -45,6 +45,9 @@ pat_status plan_finite_check(PlanBase* base, bool adjoint, cudaStream_t s);
 pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s);
 pat_status plan_gradient_medium(PlanBase* base, const void* p0, const void* h, void* gc2, void* grho, void* gp0,
                                 int K, cudaStream_t s);
+pat_status plan_time_reversal(PlanBase* base, const void* data, void* img, int compensate, double k_cut,
+                              cudaStream_t s);
+pat_status plan_adjoint_atd(PlanBase* base, const void* resid, void* img, int initial_paper, cudaStream_t s);
 PlanBase* make_plan_arena(const HostTables& h, unsigned char* arena, size_t cap, pat_status* st);
 pat_status plan_forward_direct(PlanBase* base, cudaStream_t s);
 pat_status build_tables(const pat_grid* grid, const double* c, const double* rho, const double* alpha0,

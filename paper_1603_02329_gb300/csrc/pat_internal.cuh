@@ -152,6 +152,23 @@ template <typename T> struct DevPlan {
     T* hk_grho;
     T* hk_gb[3];
 
+    // Hooks of the time-reversal solve (Sec. II.B.1, readings T1-T5; off by default):
+    //   tr_kc2 > 0: the absorption multiplier |k|^(y-2) becomes -W(|k| / k_c) |k|^(y-2), the reversed
+    //     and band-limited absorption term (W the radial Blackman window, tr_kc2 = 1 / k_c^2);
+    //   tr_node [N]: the sensor enforced at each node (-1: none); after the step the pressure there is
+    //     set to tr_row[sensor] and the split densities to tr_row[sensor] / (d c0^2);
+    //   tr_img: the pressure of the step launched with the last-step flag is stored there.
+    T tr_kc2;
+    const int* tr_node;
+    const T* tr_row;
+    T* tr_img;
+    // Adjoint-then-discretize solve (Sec. III Eqs. (moma), (massa), (statea); readings A1-A2; atd = 1):
+    // the mass update takes the source dt rho0 s / d with s = M^T atd_row, and tau, eta act before the
+    // fractional Laplacians: (dd, r) = (c0^2 tau (s - sum e), c0^2 eta sum rho / rho0) and
+    // p = c0^2 sum rho - rho0 L_{y-2} dd - rho0 L_{y-1} r.
+    int atd;
+    const T* atd_row;
+
     // phase-timeline trace of the persistent kernel (nullptr = off): globaltimer at entry and
     // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA
     unsigned long long* trace;

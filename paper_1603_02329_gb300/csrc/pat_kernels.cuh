@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, 
     stage_pml(sm, P.a, P, line0);
     cp_commit();
     int2 g = make_int2(0, 0);
-    if (!P.lossy) g = gather_prologue(sm, P, line0);
+    if (P.atd) g = scatter_prologue(sm, P, line0, P.atd_row);
+    else if (!P.lossy) g = gather_prologue(sm, P, line0);
     pdl_trigger();
     pdl_wait();
     stage_spectra(sm.S, P.spec, D, line0, R, P.ldh);
@@ -371,35 +372,52 @@ __global__ void __launch_bounds__(256) k_fwd_rho(DevPlan<T> P, int R, int last, 
     __syncthreads();
     cplx<T>* res = fft_rows<T, true>(sm.A, sm.B, P.fx, sm.tw, D * R / 2);
     cplx<T>* out = (res == sm.A) ? sm.B : sm.A;
+    if (P.atd) {   // s = M^T atd_row into items 0 .. R-1 of `out`, read back by the pointwise step
+        for (int q = threadIdx.x; q < (R / 2) * nx; q += blockDim.x) out[q] = mkc<T>(0, 0);
+        __syncthreads();
+        scatter_rows(sm, P, g, out, line0, P.atd_row);
+        __syncthreads();
+    }
     const T dt = P.dt;
     for (int r = 0; r < R; ++r)
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int t = r * nx + i;
         const size_t idx = (size_t)(line0 + r) * nx + i;
         const T rho0 = sm.row(0)[t];
+        const T src = P.atd ? slot(out, r, i, nx) : (T)0;
+        const int trj = P.tr_node ? P.tr_node[idx] : -1;
         T rs = 0, es = 0;
 #pragma unroll
         for (int xi = 0; xi < D; ++xi) {
             const T e = slot(res, xi * R + r, i, nx);
             const T a = sm.pml_at(xi, r, i);
-            const T rh = a * (a * sm.row(2 + xi)[t] - dt * rho0 * e);
-            P.rh[xi][idx] = rh;
+            const T rh = P.atd ? a * (a * sm.row(2 + xi)[t] - dt * rho0 * e + dt * rho0 * src / T(D))
+                               : a * (a * sm.row(2 + xi)[t] - dt * rho0 * e);
+            P.rh[xi][idx] = (trj >= 0) ? P.tr_row[trj] / (T(D) * P.c2[idx]) : rh;
             rs += rh;
             es += e;
             if (P.hk_e[0]) P.hk_e[xi][idx] = e;
         }
         if (P.lossy) {
             P.rsum[idx] = rs;
-            slot(out, r, i, nx) = rho0 * es;
-            slot(out, R + r, i, nx) = rs;
+            if (P.atd) {
+                slot(out, r, i, nx) = P.c2tau[idx] * (src - es);
+                slot(out, R + r, i, nx) = P.c2eta[idx] * rs / rho0;
+            } else {
+                slot(out, r, i, nx) = rho0 * es;
+                slot(out, R + r, i, nx) = rs;
+            }
         } else {
-            slot(out, r, i, nx) = sm.row(1)[t] * rs;
+            T pv = sm.row(1)[t] * rs;
+            if (trj >= 0) pv = P.tr_row[trj];
+            if (P.tr_img && last) P.tr_img[idx] = pv;
+            slot(out, r, i, nx) = pv;
             if (qrow) qrow[idx] = rs;   // d p / d c0^2 (lossless)
         }
     }
     __syncthreads();
     if (!P.lossy) {
-        gather_rows(sm, P, g, line0, out, data_row);
+        if (!P.atd) gather_rows(sm, P, g, line0, out, data_row);
         if (last) return;
         __syncthreads();
     }
@@ -436,7 +454,20 @@ __global__ void __launch_bounds__(256) k_fwd_p(DevPlan<T> P, int R, int last, T*
         const int t = r * nx + i;
         const T Ld = slot(res, r, i, nx);
         const T Lr = slot(res, R + r, i, nx);
-        slot(out, r, i, nx) = sm.row(0)[t] * sm.row(3)[t] + sm.row(1)[t] * Ld - sm.row(2)[t] * Lr;
+        const size_t idx = (size_t)(line0 + r) * nx + i;
+        T pv;
+        if (P.atd) {
+            const T rho0 = P.rho0[idx];
+            pv = sm.row(0)[t] * sm.row(3)[t] - rho0 * Ld - rho0 * Lr;
+        } else {
+            pv = sm.row(0)[t] * sm.row(3)[t] + sm.row(1)[t] * Ld - sm.row(2)[t] * Lr;
+        }
+        if (P.tr_node) {
+            const int trj = P.tr_node[idx];
+            if (trj >= 0) pv = P.tr_row[trj];
+        }
+        if (P.tr_img && last) P.tr_img[idx] = pv;
+        slot(out, r, i, nx) = pv;
         if (qrow) {
             // d p / d c0^2 with tau, eta following c0 (Eq. (Twelve)): d(c0^2 tau)/d c0^2 = (y+1)/2 tau,
             // d(c0^2 eta)/d c0^2 = (y+2)/2 eta; (y+1)/2 = phb + 1, (y+2)/2 = pha + 2
@@ -700,6 +731,24 @@ __global__ void __launch_bounds__(256) k_adj_p(DevPlan<T> P, int R, int final_, 
 // Symbols: kappa = sinc(c_ref |k| dt / 2) (k-space correction), |k|^(y-2), |k|^(y-1)
 // (Eq. (state)), D+-_xi = i k_xi exp(+-i k_xi dx_xi / 2) (staggered grid); all scaled by 1/N.
 // ------------------------------------------------------------------------------------------
+// Multiplier of the first absorption channel: |k|^(y-2) / N (Eq. (state); zero at k = 0), or, in
+// the time-reversal solve (tr_kc2 = 1 / k_c^2 > 0), -W(|k| / k_c) |k|^(y-2) / N with the radial
+// Blackman window W(q) = 0.42 + 0.5 cos(pi q) + 0.08 cos(2 pi q) for q < 1 and 0 beyond (readings T1,
+// T5: the absorption term reversed in sign and band-limited).
+template <typename T> __device__ __forceinline__ T abs_mult0(const DevPlan<T>& P, T k2) {
+    T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+    if (P.tr_kc2 > (T)0) {
+        const T q2 = k2 * P.tr_kc2;
+        T w = 0;
+        if (q2 < (T)1) {
+            const T q = sqrt(q2);
+            w = (T)0.42 + (T)0.5 * cospi(q) + (T)0.08 * cospi((T)2 * q);
+        }
+        s0 = -w * s0;
+    }
+    return s0;
+}
+
 template <typename T> size_t spec_smem_bytes(int D, int L, int W) {
     const int Lpad = (L + 3) & ~3;
     return (size_t)(3 * L + 16 + 3 * L * D * W) * sizeof(cplx<T>) + (size_t)(Lpad + 8) * sizeof(T);
@@ -847,7 +896,7 @@ __global__ void __launch_bounds__(256) k_spec(DevPlan<T> P, int W, int lgW, int 
             const int i = t >> lgW, c = t & (W - 1);
             const T k2 = ckx2[c] + kl2[i] + ko2;
             if constexpr (MODE == SPEC_ABS) {
-                const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+                const T s0 = abs_mult0(P, k2);
                 const T s1 = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
                 const size_t b0 = (size_t)i * LWin + c;
                 O[b0] = cscale(res[b0], s0);

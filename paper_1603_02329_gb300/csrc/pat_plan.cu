@@ -557,6 +557,28 @@ pat_status pat_gradient_medium(pat_plan* plan, const void* p0, const void* resid
     return plan_gradient_medium(b, p0, residual, grad_c2, grad_rho, grad_p0, checkpoint_every, (cudaStream_t)stream);
 }
 
+pat_status pat_time_reversal(pat_plan* plan, const void* data, void* image, int compensate, double k_cut,
+                             void* stream) {
+    set_error("");
+    if (!plan || !data || !image) return fail(PAT_EINVAL, "NULL argument");
+    if (compensate != 0 && compensate != 1) return fail(PAT_EINVAL, "compensate must be 0 or 1");
+    if (compensate && !(k_cut > 0.0 && k_cut <= 1.0)) return fail(PAT_EINVAL, "k_cut must lie in (0, 1]");
+    PlanBase* b = plan->impl;
+    if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
+    DeviceGuard g(b->device);
+    return plan_time_reversal(b, data, image, compensate, k_cut, (cudaStream_t)stream);
+}
+
+pat_status pat_adjoint_atd(pat_plan* plan, const void* residual, void* image, int initial_paper, void* stream) {
+    set_error("");
+    if (!plan || !residual || !image) return fail(PAT_EINVAL, "NULL argument");
+    if (initial_paper != 0 && initial_paper != 1) return fail(PAT_EINVAL, "initial_paper must be 0 or 1");
+    PlanBase* b = plan->impl;
+    if (b->arena) return fail(PAT_EUNSUPPORTED, "static-arena plans run the forward operator only");
+    DeviceGuard g(b->device);
+    return plan_adjoint_atd(b, residual, image, initial_paper, (cudaStream_t)stream);
+}
+
 pat_status pat_forward(const void* p0, const double* c, const double* rho, const double* alpha0,
                        int alpha0_is_scalar, double y, const pat_grid* grid, const pat_sensors* sensor_mask,
                        double dt, int Nt, pat_precision prec, void* data, void* stream) {

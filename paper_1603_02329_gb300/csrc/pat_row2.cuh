@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
             if (!lossy) stage_rows(row(1), P.c2, line0, R, nx);
             FO = lossy ? 2 : 1;
             fwd = lossy || !flag;
-            gath = !lossy;
+            gath = !lossy && !P.atd;
+            scat = P.atd != 0;   // adjoint-then-discretize: the source M^T atd_row
             break;
         case R2_FWD_P:
             stage_rows(row(0), P.c2, line0, R, nx);
@@ -155,12 +156,13 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
     // adjoint solve; segments are distinct points), read back by the pointwise step
     const DevSensors<T>& S = P.sens;
     if (scat) {
+        const T* hr = (KIND == R2_FWD_RHO) ? P.atd_row : h_row;
         for (int t = threadIdx.x; t < np * nx; t += blockDim.x) gb[t] = mkc<T>(0, 0);
         __syncthreads();
         const int s0 = S.s_lineptr[line0], s1 = S.s_lineptr[line0 + R];
         for (int q = s0 + threadIdx.x; q < s1; q += blockDim.x) {
             T acc = 0;
-            for (int e = S.s_seg_e0[q]; e < S.s_seg_e0[q + 1]; ++e) acc += S.s_ent_w[e] * h_row[S.s_ent_sensor[e]];
+            for (int e = S.s_seg_e0[q]; e < S.s_seg_e0[q + 1]; ++e) acc += S.s_ent_w[e] * hr[S.s_ent_sensor[e]];
             const int pos = (S.s_seg_line[q] - line0) * nx + S.s_seg_x[q];
             const int r = pos / nx, x = pos - r * nx;
             slot(gb, r, x, nx) += acc;
@@ -241,23 +243,33 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                     const int t = r * nx + x;
                     const size_t idx = gidx(r, x);
                     const T rho0 = row(0)[t];
+                    const T src = P.atd ? slot(gb, r, x, nx) : (T)0;
+                    const int trj = P.tr_node ? P.tr_node[idx] : -1;
                     T rs = 0, es = 0;
 #pragma unroll
                     for (int xi = 0; xi < D; ++xi) {
                         const T e = in[xi];
                         const T aa = pml(xi, r, x);
-                        const T rh = aa * (aa * row(2 + xi)[t] - dt * rho0 * e);
-                        P.rh[xi][idx] = rh;
+                        const T rh = P.atd ? aa * (aa * row(2 + xi)[t] - dt * rho0 * e + dt * rho0 * src / T(D))
+                                           : aa * (aa * row(2 + xi)[t] - dt * rho0 * e);
+                        P.rh[xi][idx] = (trj >= 0) ? P.tr_row[trj] / (T(D) * P.c2[idx]) : rh;
                         rs += rh;
                         es += e;
                         if (P.hk_e[0]) P.hk_e[xi][idx] = e;
                     }
                     if (lossy) {
                         P.rsum[idx] = rs;
-                        out[0] = rho0 * es;
-                        out[1] = rs;
+                        if (P.atd) {
+                            out[0] = P.c2tau[idx] * (src - es);
+                            out[1] = P.c2eta[idx] * rs / rho0;
+                        } else {
+                            out[0] = rho0 * es;
+                            out[1] = rs;
+                        }
                     } else {
-                        const T pv = row(1)[t] * rs;
+                        T pv = row(1)[t] * rs;
+                        if (trj >= 0) pv = P.tr_row[trj];
+                        if (P.tr_img && flag) P.tr_img[idx] = pv;
                         slot(gb, r, x, nx) = pv;
                         if (qrow) qrow[idx] = rs;   // d p / d c0^2 (lossless)
                         out[0] = pv;
@@ -268,7 +280,19 @@ __global__ void __launch_bounds__(256) k_row2(DevPlan<T> P, int R, int flag, T* 
                 r2_each<T, RR, FIM, FOM, 2, 1>(p, j, m, z, o, [&](int r, int x, const T* in, T* out) {
                     const int t = r * nx + x;
                     const T c2 = row(0)[t], rs = row(3)[t];
-                    const T pv = c2 * rs + row(1)[t] * in[0] - row(2)[t] * in[1];
+                    const size_t idx = gidx(r, x);
+                    T pv;
+                    if (P.atd) {
+                        const T rho0 = P.rho0[idx];
+                        pv = c2 * rs - rho0 * in[0] - rho0 * in[1];
+                    } else {
+                        pv = c2 * rs + row(1)[t] * in[0] - row(2)[t] * in[1];
+                    }
+                    if (P.tr_node) {
+                        const int trj = P.tr_node[idx];
+                        if (trj >= 0) pv = P.tr_row[trj];
+                    }
+                    if (P.tr_img && flag) P.tr_img[idx] = pv;
                     slot(gb, r, x, nx) = pv;
                     if (qrow)   // d p / d c0^2 with tau, eta following c0 (Eq. (Twelve))
                         qrow[gidx(r, x)] =

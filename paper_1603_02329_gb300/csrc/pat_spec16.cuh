@@ -93,7 +93,7 @@ __device__ void s16_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, 
                     const int i = j + r * m;
                     const T kl = kl_s[i];
                     const T k2 = ckx2 + kl * kl + ko2;
-                    const T sc = (k2 > (T)0) ? pow(k2, f == 0 ? P.pha : P.phb) * P.invN : (T)0;
+                    const T sc = (f == 0) ? abs_mult0(P, k2) : ((k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0);
                     z[r] = cscale(z[r], sc);
                 } else {
                     const T kap = kap_at(r);

@@ -96,7 +96,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
             const T kl = kl_s[i];
             const T k2 = ckx2 + kl * kl + ko2;
             if constexpr (MODE == SPEC_ABS) {
-                const T s0 = (k2 > (T)0) ? pow(k2, P.pha) * P.invN : (T)0;
+                const T s0 = abs_mult0(P, k2);
                 const T s1 = (k2 > (T)0) ? pow(k2, P.phb) * P.invN : (T)0;
                 o[0][r] = cscale(z[0][r], s0);
                 o[FO - 1][r] = cscale(z[FI - 1][r], s1);

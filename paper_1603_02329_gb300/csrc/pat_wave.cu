@@ -36,6 +36,74 @@ template <typename T> __global__ void k_rho_chain(DevPlan<T> P, const T* gb, T* 
     }
 }
 
+// time reversal: p^0 = the last datum at each sensor's node (the rest of the image is zero)
+template <typename T> __global__ void k_tr_start(T* img, const int* node, const T* row, int Ns) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < Ns) img[node[j]] = row[j];
+}
+
+// adjoint-then-discretize source rows: src[n] = (h^{Nt-1-n} + h^{Nt-2-n}) / 2, n = 0 .. Nt-2, the
+// reversed data averaged over the half step (reading A2)
+template <typename T> __global__ void k_atd_source(T* src, const T* h, int Nt, int Ns) {
+    const long long cnt = (long long)(Nt - 1) * Ns;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt; q += (long long)gridDim.x * blockDim.x) {
+        const long long n = q / Ns, j = q - n * Ns;
+        src[q] = (T)0.5 * (h[(size_t)(Nt - 1 - n) * Ns + j] + h[(size_t)(Nt - 2 - n) * Ns + j]);
+    }
+}
+
+// g = sum_xi rho*_xi / rho0 (Eq. (adjj))
+template <typename T> __global__ void k_atd_image(DevPlan<T> P, T* img) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < P.N; j += (long long)gridDim.x * blockDim.x) {
+        T acc = 0;
+        for (int a = 0; a < P.d; ++a) acc += P.rh[a][j];
+        img[j] = acc / P.rho0[j];
+    }
+}
+
+// reading A5, first half: x-transform of the channels (0, c0^2 eta g) into spectra 0 and 1
+template <typename T, int D> __global__ void __launch_bounds__(256) k_atd_a5_fwd(DevPlan<T> P, int R) {
+    RowSm<T, D> sm(P.nx, P.ldh, R);
+    const int nx = P.nx, line0 = blockIdx.x * R;
+    stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
+    cp_commit();
+    pdl_trigger();
+    pdl_wait();
+    cp_wait_all();
+    __syncthreads();
+    for (int r = 0; r < R; ++r)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const size_t idx = (size_t)(line0 + r) * nx + i;
+            slot(sm.A, r, i, nx) = (T)0;
+            slot(sm.A, R + r, i, nx) = P.c2eta[idx] * P.img[idx];
+        }
+    __syncthreads();
+    cplx<T>* res = fft_rows<T, false>(sm.A, sm.B, P.fx, sm.tw, R);
+    r2c_unpack(res, P.spec, 2, R, line0, nx, P.ldh);
+}
+
+// reading A5, second half: inverse x-transform; g <- g - L_{y-1}(c0^2 eta g) / c0^2
+template <typename T, int D> __global__ void __launch_bounds__(256) k_atd_a5_inv(DevPlan<T> P, int R) {
+    RowSm<T, D> sm(P.nx, P.ldh, R);
+    const int nx = P.nx, line0 = blockIdx.x * R;
+    stage16(sm.tw, P.twx, (size_t)nx * sizeof(cplx<T>));
+    cp_commit();
+    pdl_trigger();
+    pdl_wait();
+    stage_spectra(sm.S, P.spec, 2, line0, R, P.ldh);
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+    c2r_pack(sm.A, sm.S, 2, R, nx, P.ldh);
+    __syncthreads();
+    cplx<T>* res = fft_rows<T, true>(sm.A, sm.B, P.fx, sm.tw, R);
+    for (int r = 0; r < R; ++r)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const size_t idx = (size_t)(line0 + r) * nx + i;
+            P.img[idx] = P.img[idx] - slot(res, R + r, i, nx) / P.c2[idx];
+        }
+}
+
 template <typename T> struct Plan : public PlanBase {
     DevPlan<T> P{};
     HostTables H;   // kept for the FP64 tables' sizes and for rebuilding
@@ -537,6 +605,8 @@ template <typename T> struct Plan : public PlanBase {
         seta((const void*)k_adj_rho<T, D>, row_smem);
         seta((const void*)k_adj_u<T, D>, row_smem);
         seta((const void*)k_adj_p<T, D>, row_smem);
+        seta((const void*)k_atd_a5_fwd<T, D>, row_smem);
+        seta((const void*)k_atd_a5_inv<T, D>, row_smem);
         seta((const void*)k_spec<T, D, SPEC_PLAIN_FWD>, spec_smem);
         seta((const void*)k_spec<T, D, SPEC_PLAIN_INV>, spec_smem);
         seta((const void*)k_spec<T, D, SPEC_GRAD>, spec_smem);
@@ -718,10 +788,12 @@ template <typename T> struct Plan : public PlanBase {
     // medium gradient with checkpoints (direct launches of the per-phase kernels)
     // ---------------------------------------------------------------------------------------
     // forward step n -> n + 1 on the state of Q; q^{n+1} = d p^{n+1} / d c0^2 into qrow
-    template <int D> void fwd_step_on(const DevPlan<T>& Q, int n, T* data_row, T* qrow, cudaStream_t s) {
+    // (u_from_p0 = false: u^{-1/2} is the state in Q.u, not (dt/2) b D+ p^0)
+    template <int D> void fwd_step_on(const DevPlan<T>& Q, int n, T* data_row, T* qrow, cudaStream_t s,
+                                      bool u_from_p0 = true) {
         const int last = (n + 2 == H.Nt);
         spectral_on<D, SPEC_GRAD>(Q, s);
-        row_launch<D>(R2_FWD_U, Q, s, (int)(n == 0));
+        row_launch<D>(R2_FWD_U, Q, s, (int)(n == 0 && u_from_p0));
         spectral_on<D, SPEC_DIV>(Q, s);
         row_launch<D>(R2_FWD_RHO, Q, s, last, data_row, nullptr, Q.lossy ? (T*)nullptr : qrow);
         if (Q.lossy) {
@@ -927,6 +999,176 @@ template <typename T> struct Plan : public PlanBase {
         if (e == cudaSuccess && gp0_out) e = cudaMemcpyAsync(gp0_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
         release();
         if (e != cudaSuccess) return cuda_fail(e, "checkpointed gradient");
+        return PAT_OK;
+    }
+
+    // ---------------------------------------------------------------------------------------
+    // time reversal (Sec. II.B.1, readings T1-T5) and the adjoint-then-discretize adjoint (Sec. III,
+    // readings A1-A5): forward-direction solves with direct launches of the per-phase kernels on the
+    // plan's own state, with the kernels' hooks set in a copy of the device plan
+    // ---------------------------------------------------------------------------------------
+    int* tr_node_d = nullptr;    // [N] sensor enforced at each node (-1: none), built on first use
+    int* tr_list_d = nullptr;    // [Ns] node of each sensor
+    T* aux_rows = nullptr;       // [max(Nt - 1, 1) + 1][Ns]: ATD source rows, then one spare row
+
+    // the node of every sensor, when each sensor is exactly one grid node with weight 1 and no two
+    // share a node (reading T2)
+    pat_status tr_nodes(std::vector<int>& node) {
+        const int Ns = H.Ns;
+        node.assign((size_t)Ns, -1);
+        std::vector<int> cnt((size_t)Ns, 0);
+        for (int line = 0; line < P.nlines; ++line)
+            for (int q = H.g_lineptr[line]; q < H.g_lineptr[line + 1]; ++q) {
+                const int j = H.g_seg_sensor[q];
+                const double w0 = H.g_seg_w0[q], w1 = H.g_seg_w1[q];
+                const long long base = (long long)H.g_seg_line[q] * H.nx + H.g_seg_x0[q];
+                if (w0 != 0.0) {
+                    ++cnt[j];
+                    if (w0 != 1.0) cnt[j] = 99;
+                    node[j] = (int)base;
+                }
+                if (w1 != 0.0) {
+                    ++cnt[j];
+                    if (w1 != 1.0) cnt[j] = 99;
+                    node[j] = (int)(base + 1);
+                }
+            }
+        std::vector<char> used((size_t)P.N, 0);
+        for (int j = 0; j < Ns; ++j) {
+            if (cnt[j] != 1 || node[j] < 0) {
+                set_error("time reversal needs every sensor on one grid node (on-grid sensors)");
+                return PAT_EINVAL;
+            }
+            if (used[(size_t)node[j]]) {
+                set_error("time reversal needs one sensor per grid node");
+                return PAT_EINVAL;
+            }
+            used[(size_t)node[j]] = 1;
+        }
+        return PAT_OK;
+    }
+
+    pat_status aux_alloc(bool tr) {
+        pat_status st = PAT_OK;
+        if (!aux_rows) {
+            aux_rows = dalloc<T>((size_t)(std::max(H.Nt - 1, 1) + 1) * std::max(H.Ns, 1), &st);
+            if (!aux_rows) return st;
+        }
+        if (tr && !tr_node_d) {
+            std::vector<int> node;
+            st = tr_nodes(node);
+            if (st != PAT_OK) return st;
+            std::vector<int> map((size_t)P.N, -1);
+            for (int j = 0; j < H.Ns; ++j) map[(size_t)node[j]] = j;
+            int* m = dalloc<int>((size_t)P.N, &st);
+            if (!m) return st;
+            int* l = dalloc<int>((size_t)std::max(H.Ns, 1), &st);
+            if (!l) return st;
+            cudaError_t e = cudaMemcpy(m, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && H.Ns > 0)
+                e = cudaMemcpy(l, node.data(), node.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (time-reversal nodes)");
+            tr_node_d = m;
+            tr_list_d = l;
+        }
+        return PAT_OK;
+    }
+
+    // image = p at the end of the reversed-time solve with the data enforced at the sensor nodes
+    template <int D> pat_status time_reversal(const void* data, void* img_out, int compensate, double k_cut,
+                                              cudaStream_t s) {
+        pat_status st = aux_alloc(true);
+        if (st != PAT_OK) return st;
+        const int Nt = H.Nt, Ns = H.Ns;
+        const size_t N = (size_t)P.N;
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        T* junk = aux_rows;   // gathered samples of the solve (not used)
+        cudaError_t e = cudaMemcpyAsync(P.data, data, (size_t)Nt * Ns * sizeof(T), cudaMemcpyDefault, s);
+        for (int a = 0; a < D && e == cudaSuccess; ++a) e = cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P.img, 0, N * sizeof(T), s);
+        if (e != cudaSuccess) return cuda_fail(e, "time reversal setup");
+        // p^0: zero except the last datum at the sensor nodes (T3)
+        if (Ns > 0)
+            k_tr_start<T><<<(Ns + 255) / 256, 256, 0, s>>>(P.img, tr_list_d, P.data + (size_t)(Nt - 1) * Ns, Ns);
+        DevPlan<T> Q = P;
+        Q.data = junk;
+        Q.spec16 = std::min(Q.spec16, 1);
+        if (compensate) {
+            double kc = 0.0;
+            for (int a = 0; a < D; ++a) {
+                const double kn = M_PI / in.grid.dx[a];
+                kc = (a == 0) ? kn : std::min(kc, kn);
+            }
+            kc *= k_cut;
+            Q.tr_kc2 = (T)(1.0 / (kc * kc));
+        }
+        Q.tr_node = tr_node_d;
+        // rho^0 = p^0 / (d c0^2), x-FFT of p^0 (its sample goes to the unused row)
+        launch(k_fwd_init<T, D>, dim3(G), B, row_smem, s, Q, R, (int)(Nt == 1));
+        for (int n = 0; n + 1 < Nt; ++n) {
+            Q.tr_row = P.data + (size_t)(Nt - 2 - n) * Ns;
+            Q.tr_img = (n + 2 == Nt) ? P.img : nullptr;
+            fwd_step_on<D>(Q, n, junk, nullptr, s, false);
+        }
+        e = take_launch_err();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(img_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(e, "time reversal");
+        return PAT_OK;
+    }
+
+    // the paper's adjoint: the continuous adjoint system discretised with the same scheme, run forward
+    // in adjoint time on the reversed data (A1-A2); initial_paper = 1: rho*(T) / rho0 (Eq. (adjj)),
+    // 0: the gradient for the forward map's initial state (A5)
+    template <int D> pat_status adjoint_atd(const void* resid, void* img_out, int initial_paper, cudaStream_t s) {
+        pat_status st = aux_alloc(false);
+        if (st != PAT_OK) return st;
+        const int Nt = H.Nt, Ns = H.Ns;
+        const size_t N = (size_t)P.N, Nh = (size_t)H.nz * H.ny * H.ldh;
+        const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        T* junk = aux_rows + (size_t)std::max(Nt - 1, 1) * std::max(Ns, 1);
+        cudaError_t e = cudaMemcpyAsync(P.data, resid, (size_t)Nt * Ns * sizeof(T), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy residual");
+        // source rows s^n = (h~^n + h~^{n+1}) / 2 = (h^{Nt-1-n} + h^{Nt-2-n}) / 2 (A2)
+        if (Nt > 1 && Ns > 0) {
+            const long long cnt = (long long)(Nt - 1) * Ns;
+            k_atd_source<T><<<(int)std::min<long long>((cnt + 255) / 256, 4096), 256, 0, s>>>(aux_rows, P.data, Nt, Ns);
+        }
+        // zero state: u*, rho*, p* (its spectrum feeds the first gradient)
+        for (int a = 0; a < D && e == cudaSuccess; ++a) {
+            e = cudaMemsetAsync(P.u[a], 0, N * sizeof(T), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(P.rh[a], 0, N * sizeof(T), s);
+        }
+        for (int a = 0; a < std::max(D, 2) && e == cudaSuccess; ++a)
+            e = cudaMemsetAsync(P.spec[a], 0, Nh * sizeof(cplx<T>), s);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint-then-discretize setup");
+        DevPlan<T> Q = P;
+        Q.data = junk;
+        Q.atd = 1;
+        for (int n = 0; n + 1 < Nt; ++n) {
+            Q.atd_row = aux_rows + (size_t)n * Ns;
+            fwd_step_on<D>(Q, n, junk, nullptr, s, false);
+        }
+        // g = sum_xi rho*_xi / rho0 (Eq. (adjj)); for the forward map's initial state (A5),
+        // g - L_{y-1}(c0^2 eta g) / c0^2, the fractional Laplacian by one more absorption pass
+        const bool a5 = !initial_paper && P.lossy;
+        const int threads = 256;
+        const int blocks = (int)std::min<size_t>((N + threads - 1) / threads, 8192);
+        k_atd_image<T><<<blocks, threads, 0, s>>>(P, P.img);
+        if (a5) {
+            // channels (0, c0^2 eta g) through x-transform, the absorption pass of the spectral kernels
+            // (channel 1 gets |k|^(y-1)), inverse x-transform, then g - (channel 1) / c0^2
+            launch(k_atd_a5_fwd<T, D>, dim3(G), B, row_smem, s, P, R);
+            spectral_on<D, SPEC_ABS>(P, s);
+            launch(k_atd_a5_inv<T, D>, dim3(G), B, row_smem, s, P, R);
+        }
+        e = take_launch_err();
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess && smooth) {   // (H S)^T = S H^T (reading R9)
+            const pat_status sst = smooth_inplace(P.img, s);
+            if (sst != PAT_OK) return sst;
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(img_out, P.img, N * sizeof(T), cudaMemcpyDefault, s);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint-then-discretize");
         return PAT_OK;
     }
 
@@ -1150,6 +1392,29 @@ pat_status plan_gradient_medium(PlanBase* base, const void* p0, const void* h, v
     auto* p = static_cast<Plan<double>*>(base);
     return p->P.d == 2 ? p->template gradient_medium<2>(p0, h, gc2, grho, gp0, K, s)
                        : p->template gradient_medium<3>(p0, h, gc2, grho, gp0, K, s);
+}
+
+pat_status plan_time_reversal(PlanBase* base, const void* data, void* img, int compensate, double k_cut,
+                              cudaStream_t s) {
+    if (base->info.precision == PAT_F32) {
+        auto* p = static_cast<Plan<float>*>(base);
+        return p->P.d == 2 ? p->template time_reversal<2>(data, img, compensate, k_cut, s)
+                           : p->template time_reversal<3>(data, img, compensate, k_cut, s);
+    }
+    auto* p = static_cast<Plan<double>*>(base);
+    return p->P.d == 2 ? p->template time_reversal<2>(data, img, compensate, k_cut, s)
+                       : p->template time_reversal<3>(data, img, compensate, k_cut, s);
+}
+
+pat_status plan_adjoint_atd(PlanBase* base, const void* resid, void* img, int initial_paper, cudaStream_t s) {
+    if (base->info.precision == PAT_F32) {
+        auto* p = static_cast<Plan<float>*>(base);
+        return p->P.d == 2 ? p->template adjoint_atd<2>(resid, img, initial_paper, s)
+                           : p->template adjoint_atd<3>(resid, img, initial_paper, s);
+    }
+    auto* p = static_cast<Plan<double>*>(base);
+    return p->P.d == 2 ? p->template adjoint_atd<2>(resid, img, initial_paper, s)
+                       : p->template adjoint_atd<3>(resid, img, initial_paper, s);
 }
 
 pat_status plan_set_fault(PlanBase* base, unsigned barrier_extra, double wait_limit_s) {

@@ -635,6 +635,7 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
     rec = {"value": value, "unit": UNIT, "ms_per_step": total_s * 1e3 / args.steps, "dtype": prec,
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
                           layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
+                          radix_schedule=int(op.info.schedule),
                           parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)]),
            "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels, "e2e": e2e,
            "gpu_launches": launches, "clocks": clk}

@@ -88,6 +88,10 @@ typedef struct {
     int layout[2];      /* launch layout: path 0 -> columns per spectral CTA, x-lines per row CTA;
                            paths 1, 2 -> columns per CTA, x-line pairs per CTA */
     int tuned;          /* 1 when the layout was chosen by timing the feasible candidates */
+    int schedule;       /* radix schedule of the 3-D spectral passes over 128- or 256-point lines, timed
+                           with the layouts on path 0 (PAT_SPEC16 pins it): 0 = stages (r0, 8, ..., 8)
+                           everywhere, 1 = two stages (n/16, 16) for the plain y transforms, 2 = two
+                           stages for every pass; 0 where no axis has such lines */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

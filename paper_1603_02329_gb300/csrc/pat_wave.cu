@@ -254,6 +254,7 @@ template <typename T> struct Plan : public PlanBase {
             // passes too (measured slower at 256^3); 0: neither
             const char* e16 = std::getenv("PAT_SPEC16");
             P.spec16 = e16 ? std::max(0, std::min(2, std::atoi(e16))) : 1;
+            info.schedule = (D == 3 && (P.stw16[1] || P.stw16[2])) ? P.spec16 : 0;
         }
         for (int a = 0; a < 3; ++a) {
             if (a < D) {
@@ -369,6 +370,13 @@ template <typename T> struct Plan : public PlanBase {
         LaunchCfg best = cfg;
         float best_ms = 1e30f;
         int tried = 0;
+        // radix schedules of the 3-D spectral passes over 128- and 256-point lines: 0 = the fixed
+        // (r0, 8, ..., 8) stages everywhere, 1 = two stages (n/16, 16) for the plain y transforms,
+        // 2 = two stages for every pass (PAT_SPEC16 pins one)
+        std::vector<int> scheds{P.spec16};
+        if (D == 3 && use_spec2 && (P.stw16[1] || P.stw16[2]) && !std::getenv("PAT_SPEC16")) scheds = {1, 0, 2};
+        int best_sched = P.spec16;
+        for (int sched : scheds)
         for (int w : {1, 2, 4, 8}) {
             if (fw && w != base.col_w) continue;
             if (sizeof(T) == 8 && w > 4) continue;
@@ -388,6 +396,7 @@ template <typename T> struct Plan : public PlanBase {
                 row_smem = rs;
                 row2_smem = r2;
                 spec_smem = ss;
+                P.spec16 = sched;
                 const float ms = time_on_stream(
                     [&] {
                         fwd_step_on<D>(P, 1, P.data, (T*)nullptr, cap_stream);
@@ -396,16 +405,20 @@ template <typename T> struct Plan : public PlanBase {
                     2);
                 ++tried;
                 if (std::getenv("PAT_DEBUG"))
-                    fprintf(stderr, "[pat] tune graph W=%d lines=%d: %.4f ms per step pair\n", w, r, ms);
+                    fprintf(stderr, "[pat] tune graph schedule=%d W=%d lines=%d: %.4f ms per step pair\n", sched, w, r,
+                            ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = c;
+                    best_sched = sched;
                 }
             }
         }
         cudaError_t e = take_launch_err();
         if (e != cudaSuccess) return cuda_fail(e, "autotune (per-phase kernels)");
         cfg = best;
+        P.spec16 = best_sched;
+        info.schedule = P.spec16;
         row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
         row2_smem = use_row2 ? row2_layout<T>(D, H.nx, H.ldh, cfg.row_lines).bytes : 0;
         spec_smem = spec_bytes(D, L, cfg.col_w);

@@ -443,6 +443,24 @@ def test_two_stage_spectral_schedule_matches_oracle(dev, monkeypatch, name, kw):
         assert rel(a[0], out[2][0]) <= 1e-6 and rel(a[1], out[2][1]) <= 1e-6
 
 
+@pytest.mark.parametrize("name,kw", SPEC16_CASES, ids=[c[0] for c in SPEC16_CASES])
+def test_autotuned_radix_schedule_matches_oracle(dev, monkeypatch, name, kw):
+    # without PAT_SPEC16 the plan-time tuner times the three radix schedules with the launch layouts
+    # and keeps the fastest; whichever it picks, the solve matches the oracle
+    monkeypatch.delenv("PAT_SPEC16", raising=False)
+    monkeypatch.delenv("PAT_AUTOTUNE", raising=False)
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(38).standard_normal((pb.Nt, ref.Ns))
+    op = _gpu_op(pb, "f32", dev)
+    assert op.info.path == 0 and op.info.tuned == 1
+    assert op.info.schedule in (0, 1, 2)
+    assert rel(op.forward(_t(pb.p0, "f32", dev)).cpu().numpy(), ref.forward(pb.p0)) <= TOL32
+    assert rel(op.adjoint(_t(h, "f32", dev)).cpu().numpy(), ref.adjoint(h)) <= TOL32
+    monkeypatch.setenv("PAT_SPEC16", "2")
+    assert _gpu_op(pb, "f32", dev).info.schedule == 2
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

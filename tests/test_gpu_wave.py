@@ -236,17 +236,23 @@ def test_tube_128_full_size_prefix_and_dot(dev):
     assert abs(lhs - rhs) <= 1e-5 * Hx.norm().item() * hh.double().norm().item()
 
 
-def test_tube_256_full_size_adjoint_prefix_and_dot(dev):
-    # 256^3, Nt = 1500, 128 x 128 sensors: the largest benchmark configuration (about 2.5 GB of
+def test_tube_256_full_size_prefix_adjoint_and_dot(dev):
+    # 256^3, Nt = 1500, 128 x 128 sensors: the benchmark's default configuration (about 2.5 GB of
     # device state, the kernels compiled for 256-point lines).  The oracle at this size manages a
-    # few steps: the adjoint of a residual supported on the first K = 3 samples (the adjoint wave
-    # spreads from the sensor plane for 3 steps) vs the oracle, and the dot identity over all 1500
-    # samples.
+    # few dozen steps: the first KF = 24 samples of the forward record (the tubes start 6 px beyond
+    # the sensor plane, about 3.3 steps per px, so the record holds 1-4 % of max p0 by then), the
+    # adjoint of a residual supported on the first K = 3 samples (the adjoint wave spreads from the
+    # sensor plane for 3 steps) vs the oracle, and the dot identity over all 1500 samples.
     pb = synth.tube_phantom_3d(seed=3, n=256, pml=20, Nt=1500, sensors=128)
-    K = 3
-    ref = Operator.from_problem(pb, Nt=K)
+    KF = 24
     op = _gpu_op(pb, "f32", dev)
     assert op.info.path == 0
+    d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+    d_ref = Operator.from_problem(pb, Nt=KF).forward(pb.p0)
+    assert np.abs(d_ref[KF - 4:]).max() > 1e-2 * np.abs(pb.p0).max()
+    assert rel(d[:KF], d_ref) <= TOL32
+    K = 3
+    ref = Operator.from_problem(pb, Nt=K)
     rng = np.random.default_rng(14)
     h = np.zeros((pb.Nt, op.Ns))
     h[:K] = rng.standard_normal((K, op.Ns))

@@ -8,11 +8,15 @@ per second over all ranks (Gpt-steps/s).
 
 The default run adds three records to the JSON line:
   - "vessel2d_512": the same measurement on the 2-D 512^2 absorbing workload (Nt = 2000, 512 line
-    sensors), whose state stays in shared memory (one persistent kernel per solve);
+    sensors), whose state stays in shared memory (one persistent kernel per solve), with the
+    time-reversal image, FISTA warm-started from it, and the adjoint-then-discretize deviation;
   - "mg_vs_fista": wall time of 3-level MG-FISTA (256^3 / 128^3 / 64^3) and of single-grid FISTA to
     the same relative error on 40 dB data, 12 iterations of FISTA at most;
   - "mg_precision": relative L2 distance of the FP32 iterates from the FP64 iterates of the same
-    MG-FISTA and FISTA runs on a small 2-D case, per iteration.
+    MG-FISTA and FISTA runs on a small 2-D case, per iteration;
+  - "mg_vs_fista_refined_2d": 2-level MG-FISTA vs FISTA at 512^2 on data generated on a finer grid
+    from contaminated maps (no inverse crime);
+  - "batch": eight uneven 2-D instances as one batched launch vs one at a time.
 
 Multi-GPU: one independent instance per rank (weak scaling, no collective on the data path).
 
@@ -506,6 +510,58 @@ def mg_precision(dev, iters=5):
     return out
 
 
+def tr_atd_record(dev, fista_iters=10):
+    """The two comparison solves on the 2-D 512^2 absorbing workload with 40 dB data: the
+    time-reversal image (Sec. II.B.1; pat_time_reversal, band-limited compensation at half the Nyquist
+    radius, and plain) with its relative error, FISTA started from it against FISTA started from zero
+    (Sec. VI.A parameters), and the paper's adjoint-then-discretize adjoint (pat_adjoint_atd) against
+    dt times the exact transpose for the same residual (the data), over the whole grid and outside the
+    PML layer."""
+    import torch
+
+    from paper_1603_02329_gb300 import synth
+    from paper_1603_02329_gb300.api import PATOperator, mg_fista
+
+    pb = synth.vessel_phantom_2d()
+    op = PATOperator.from_problem(pb, precision="f32", device=dev)
+    x_true = torch.tensor(pb.p0, dtype=torch.float32, device=dev)
+    clean = op.forward(x_true).cpu().numpy()
+    data = torch.tensor(synth.awgn(np.random.default_rng(2), clean, 40.0), dtype=torch.float32, device=dev)
+    re = lambda x: float(torch.linalg.norm(x.double() - x_true.double()) / torch.linalg.norm(x_true.double()))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    tr, t_tr = timed(lambda: op.time_reversal(data, compensate=True, k_cut=0.5))
+    tr0 = op.time_reversal(data, compensate=False)
+    L = op.power_iteration(torch.tensor(synth.random_image(11, pb.shape), dtype=torch.float32, device=dev), 30)
+    common = dict(variant=1, lam=1e-2, step_scale=1.0, recursion=False, max_iter=fista_iters, eps_d=-1.0)
+    _, _, r_zero = mg_fista(op, None, data, torch.zeros_like(x_true), L, p_exact=x_true, **common)
+    _, _, r_tr = mg_fista(op, None, data, tr.clamp(min=0), L, p_exact=x_true, **common)
+    target = r_zero[-1]["RE"]
+    hit = next((r["k"] for r in r_tr if r["RE"] <= target), None)
+    atd, t_atd = timed(lambda: op.adjoint_atd(data))
+    tp = op.adjoint(data) * pb.dt
+    P = pb.pml[0]
+    inner = (slice(P, pb.shape[0] - P), slice(P, pb.shape[1] - P))
+    dev_all = float(torch.linalg.norm((atd - tp).double()) / torch.linalg.norm(tp.double()))
+    dev_in = float(torch.linalg.norm((atd - tp)[inner].double()) / torch.linalg.norm(tp[inner].double()))
+    cos = float(torch.sum(atd.double() * tp.double()) / (torch.linalg.norm(atd.double()) * torch.linalg.norm(tp.double())))
+    op.close()
+    return {"workload": "2-D 512^2 absorbing, 512 line sensors on the first row inside the PML, Nt=2000, 40 dB AWGN",
+            "time_reversal": {"re_compensated": re(tr), "re_plain": re(tr0), "k_cut": 0.5, "solve_s": t_tr},
+            "fista_warm_start": {"iters": fista_iters, "re_from_zero": [round(r["RE"], 4) for r in r_zero],
+                                 "re_from_tr": [round(r["RE"], 4) for r in r_tr],
+                                 "iters_from_tr_to_zero_start_final_re": hit},
+            "adjoint_then_discretize": {"rel_dev_from_dt_transpose": dev_all, "rel_dev_outside_pml": dev_in,
+                                        "cosine": cos, "solve_s": t_atd}}
+
+
 PATH_NAMES = {0: "CUDA graph of per-phase kernels", 1: "persistent kernel per solve",
               2: "persistent kernel per solve, register-fused power-of-two transforms"}
 
@@ -610,6 +666,8 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
             b = solve_bytes(pb.N, pb.Nt, w, D=len(pb.shape), lossy=op.lossy)
         else:
             b = kernel_bytes(kname, pb.N, Nh, w, D=len(pb.shape), lossy=op.lossy)
+            if kname.startswith("spec") and int(op.info.spec_chunks) > 1:
+                b /= int(op.info.spec_chunks)   # one launch covers one chunk of the column tiles
         ms = kernels[dom]
         ach = b / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
@@ -628,14 +686,14 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
     # per time step of the graph path: (3 or 2) spectral operations of 1 (2-D) or 3 (3-D: y, z, y)
     # launches, and as many row kernels
     nops = 3 if op.lossy else 2
-    slots_f = nops * (3 if len(pb.shape) == 3 else 1) + nops
+    slots_f = nops * (3 * int(op.info.spec_chunks) if len(pb.shape) == 3 else 1) + nops
     persistent = int(op.info.path) >= 1
     # per solve: the persistent kernel or the graph's kernels, and the non-finite scan of the output
     launches = args.steps * 2 * ((1 if persistent else (1 + (pb.Nt - 1) * slots_f)) + 1)
     rec = {"value": value, "unit": UNIT, "ms_per_step": total_s * 1e3 / args.steps, "dtype": prec,
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
                           layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
-                          radix_schedule=int(op.info.schedule),
+                          radix_schedule=int(op.info.schedule), spec_chunks=int(op.info.spec_chunks),
                           parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)]),
            "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels, "e2e": e2e,
            "gpu_launches": launches, "clocks": clk}
@@ -689,11 +747,20 @@ def main():
         rec2, op2, _ = measure(args, "vessel2d_512", dev, 1, 0, local, with_e2e=True)
         op2.close()
         rec2["steps"], rec2["warmup"] = args.steps, args.warmup
+        rec2["tr_atd"] = tr_atd_record(dev)
         out["vessel2d_512"] = rec2
     if (args.mg or args.mg_default) and rank == 0:
         out["mg_vs_fista"] = mg_vs_fista(args, dev, pb)
         out["mg_precision"] = mg_precision(dev)
-    if args.batch and rank == 0:
+    if args.mg_default and rank == 0:
+        # the 2-D comparison on data without the inverse crime: generated on a 1.44x finer grid from
+        # 35 dB-contaminated maps (Sec. VI.A's set-up), 2 levels, 20 FISTA iterations
+        from paper_1603_02329_gb300 import synth
+
+        a2 = argparse.Namespace(**vars(args))
+        a2.mg_levels, a2.mg_iters, a2.mg_data = 2, 20, "refined"
+        out["mg_vs_fista_refined_2d"] = mg_vs_fista(a2, dev, synth.vessel_phantom_2d(seed=2))
+    if (args.batch or args.mg_default) and rank == 0:
         out["batch"] = batch_vs_sequential(dev)
     if rank == 0:
         print(json.dumps(out), flush=True)

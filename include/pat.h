@@ -92,6 +92,10 @@ typedef struct {
                            with the layouts on path 0 (PAT_SPEC16 pins it): 0 = stages (r0, 8, ..., 8)
                            everywhere, 1 = two stages (n/16, 16) for the plain y transforms, 2 = two
                            stages for every pass; 0 where no axis has such lines */
+    int spec_chunks;    /* 3-D path 0: each spectral operation runs its y / z / y passes over this many
+                           chunks of the half-spectrum column tiles, one chunk after the other, so
+                           that a chunk's intermediate spectra can stay in L2 (timed with the layouts;
+                           PAT_SPEC_CHUNKS pins it); 1 elsewhere */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

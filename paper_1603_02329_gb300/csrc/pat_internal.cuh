@@ -168,6 +168,9 @@ template <typename T> struct DevPlan {
     // p = c0^2 sum rho - rho0 L_{y-2} dd - rho0 L_{y-1} r.
     int atd;
     const T* atd_row;
+    // first column tile of a spectral launch (blockIdx.x + tile0 is the tile): a 3-D spectral operation
+    // may run its y / z / y passes chunk by chunk over the column tiles (0 = the whole range at once)
+    int tile0;
 
     // phase-timeline trace of the persistent kernel (nullptr = off): globaltimer at entry and
     // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA

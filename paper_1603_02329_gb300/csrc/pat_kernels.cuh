@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(256) k_spec(DevPlan<T> P, int W, int lgW, int 
     T* kl2 = reinterpret_cast<T*>(Z + TB);
     T* ckx2 = kl2 + Lpad;
     const FftAxis& ax = (lax == 1) ? P.fy : P.fz;
-    const int kx0 = blockIdx.x * W;
+    const int kx0 = (blockIdx.x + P.tile0) * W;
     const int wv = min(W, P.nxh - kx0);
     const int outer = blockIdx.y;
     const size_t es = (lax == 1) ? (size_t)P.ldh : (size_t)P.ny * P.ldh;

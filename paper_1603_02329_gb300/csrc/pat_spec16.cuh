@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_spec16(DevPlan<T> P, int W, int lgW, in
     cplx<T>* B = A + spec2_buf_elems<T>(spec2_nf(D, MODE, F), L, W);
     const cplx<T>* tw_f = tab;               // forward radix-16 stage, span R1
     const cplx<T>* tw_i = tab + 15 * R1;     // inverse radix-R1 stage, span 16
-    const int kx0 = blockIdx.x * W, outer = blockIdx.y;
+    const int kx0 = (blockIdx.x + P.tile0) * W, outer = blockIdx.y;
     const int wv = min(W, P.nxh - kx0);
     const size_t es = (lax == 1) ? (size_t)P.ldh : (size_t)P.ny * P.ldh;
     const size_t base = (lax == 1) ? (size_t)outer * P.ny * P.ldh + kx0 : (size_t)outer * P.ldh + kx0;

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     T* kl_s = reinterpret_cast<T*>(ml_s + L);
     cplx<T>* A = tab + spec2_pre_elems<T>(L);
     cplx<T>* B = A + spec2_buf_elems<T>(spec2_nf(D, MODE, F), L, W);
-    const int kx0 = blockIdx.x * W, outer = blockIdx.y;
+    const int kx0 = (blockIdx.x + P.tile0) * W, outer = blockIdx.y;
     const int wv = min(W, P.nxh - kx0);
     const size_t es = (lax == 1) ? (size_t)P.ldh : (size_t)P.ny * P.ldh;
     const size_t base = (lax == 1) ? (size_t)outer * P.ny * P.ldh + kx0 : (size_t)outer * P.ldh + kx0;

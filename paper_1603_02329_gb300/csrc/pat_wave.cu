@@ -255,6 +255,9 @@ template <typename T> struct Plan : public PlanBase {
             const char* e16 = std::getenv("PAT_SPEC16");
             P.spec16 = e16 ? std::max(0, std::min(2, std::atoi(e16))) : 1;
             info.schedule = (D == 3 && (P.stw16[1] || P.stw16[2])) ? P.spec16 : 0;
+            const char* ech = std::getenv("PAT_SPEC_CHUNKS");
+            spec_chunks = (D == 3 && ech) ? std::max(1, std::atoi(ech)) : 1;
+            info.spec_chunks = 1;
         }
         for (int a = 0; a < 3; ++a) {
             if (a < D) {
@@ -332,6 +335,7 @@ template <typename T> struct Plan : public PlanBase {
             st = (D == 2) ? tune_graph<2>() : tune_graph<3>();
             if (st != PAT_OK) return st;
         }
+        info.spec_chunks = (!persistent && D == 3) ? chunk_count() : 1;
         return PAT_OK;
     }
 
@@ -376,6 +380,11 @@ template <typename T> struct Plan : public PlanBase {
         std::vector<int> scheds{P.spec16};
         if (D == 3 && use_spec2 && (P.stw16[1] || P.stw16[2]) && !std::getenv("PAT_SPEC16")) scheds = {1, 0, 2};
         int best_sched = P.spec16;
+        // chunks of column tiles per 3-D spectral operation (PAT_SPEC_CHUNKS pins it)
+        std::vector<int> chunk_cands{spec_chunks};
+        if (D == 3 && !std::getenv("PAT_SPEC_CHUNKS")) chunk_cands = {1, 2, 4, 8};
+        int best_chunks = spec_chunks;
+        for (int nchunk : chunk_cands)
         for (int sched : scheds)
         for (int w : {1, 2, 4, 8}) {
             if (fw && w != base.col_w) continue;
@@ -397,6 +406,7 @@ template <typename T> struct Plan : public PlanBase {
                 row2_smem = r2;
                 spec_smem = ss;
                 P.spec16 = sched;
+                spec_chunks = nchunk;
                 const float ms = time_on_stream(
                     [&] {
                         fwd_step_on<D>(P, 1, P.data, (T*)nullptr, cap_stream);
@@ -405,12 +415,13 @@ template <typename T> struct Plan : public PlanBase {
                     2);
                 ++tried;
                 if (std::getenv("PAT_DEBUG"))
-                    fprintf(stderr, "[pat] tune graph schedule=%d W=%d lines=%d: %.4f ms per step pair\n", sched, w, r,
-                            ms);
+                    fprintf(stderr, "[pat] tune graph chunks=%d schedule=%d W=%d lines=%d: %.4f ms per step pair\n",
+                            nchunk, sched, w, r, ms);
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = c;
                     best_sched = sched;
+                    best_chunks = nchunk;
                 }
             }
         }
@@ -419,6 +430,8 @@ template <typename T> struct Plan : public PlanBase {
         cfg = best;
         P.spec16 = best_sched;
         info.schedule = P.spec16;
+        spec_chunks = best_chunks;
+        info.spec_chunks = chunk_count();
         row_smem = row_smem_bytes<T>(D, H.nx, H.ldh, cfg.row_lines);
         row2_smem = use_row2 ? row2_layout<T>(D, H.nx, H.ldh, cfg.row_lines).bytes : 0;
         spec_smem = spec_bytes(D, L, cfg.col_w);
@@ -712,9 +725,21 @@ template <typename T> struct Plan : public PlanBase {
         cudaLaunchKernelEx(&lc, kern, args...);
     }
 
-    template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F) { spec_launch_on<D, MODE>(P, s, lax, F); }
-    template <int D, int MODE> void spec_launch_on(const DevPlan<T>& Q, cudaStream_t s, int lax, int F) {
-        const int tiles = (Q.nxh + cfg.col_w - 1) / cfg.col_w;
+    // 3-D: each spectral operation runs its y / z / y passes chunk by chunk over the column tiles, so a
+    // chunk's intermediate spectra can stay in L2 between the passes (1 = all tiles at once)
+    int spec_chunks = 1;
+    int spec_tiles() const { return (P.nxh + cfg.col_w - 1) / cfg.col_w; }
+    int chunk_count() const { return std::max(1, std::min(spec_chunks, spec_tiles())); }
+
+    template <int D, int MODE> void spec_launch(cudaStream_t s, int lax, int F, int t0 = 0, int nt = 0) {
+        spec_launch_on<D, MODE>(P, s, lax, F, t0, nt);
+    }
+    // tiles t0 .. t0 + nt - 1 (nt = 0: all)
+    template <int D, int MODE>
+    void spec_launch_on(const DevPlan<T>& Q0, cudaStream_t s, int lax, int F, int t0 = 0, int nt = 0) {
+        DevPlan<T> Q = Q0;
+        Q.tile0 = t0;
+        const int tiles = nt > 0 ? nt : (Q.nxh + cfg.col_w - 1) / cfg.col_w;
         const int outer = (lax == 1) ? Q.nz : Q.ny;
         int lgw = 0;
         while ((1 << lgw) < cfg.col_w) ++lgw;
@@ -743,9 +768,13 @@ template <typename T> struct Plan : public PlanBase {
         }
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
-        spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin);
-        spec_launch_on<D, MODE>(Q, s, 2, 0);
-        spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout);
+        const int tiles = spec_tiles(), nc = chunk_count();
+        for (int c = 0; c < nc; ++c) {
+            const int t0 = (int)((long long)c * tiles / nc), t1 = (int)((long long)(c + 1) * tiles / nc);
+            spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
+            spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
+            spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);
+        }
     }
 
     // ---------------------------------------------------------------------------------------
@@ -1224,12 +1253,16 @@ template <typename T> struct Plan : public PlanBase {
         }
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
-        mark(s, "spec_y_fwd");
-        spec_launch<D, SPEC_PLAIN_FWD>(s, 1, fin);
-        mark(s, name);
-        spec_launch<D, MODE>(s, 2, 0);
-        mark(s, "spec_y_inv");
-        spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout);
+        const int tiles = spec_tiles(), nc = chunk_count();
+        for (int c = 0; c < nc; ++c) {
+            const int t0 = (int)((long long)c * tiles / nc), t1 = (int)((long long)(c + 1) * tiles / nc);
+            mark(s, "spec_y_fwd");
+            spec_launch<D, SPEC_PLAIN_FWD>(s, 1, fin, t0, t1 - t0);
+            mark(s, name);
+            spec_launch<D, MODE>(s, 2, 0, t0, t1 - t0);
+            mark(s, "spec_y_inv");
+            spec_launch<D, SPEC_PLAIN_INV>(s, 1, fout, t0, t1 - t0);
+        }
     }
 
     template <int D> void record_forward(cudaStream_t s) {

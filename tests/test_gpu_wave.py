@@ -467,6 +467,26 @@ def test_autotuned_radix_schedule_matches_oracle(dev, monkeypatch, name, kw):
     assert _gpu_op(pb, "f32", dev).info.schedule == 2
 
 
+@pytest.mark.parametrize("chunks", ["2", "3", "64"])
+def test_chunked_spectral_passes_are_bitwise_equal(dev, monkeypatch, chunks):
+    # a 3-D spectral operation run chunk by chunk over its column tiles does the same arithmetic per
+    # tile: the solves are bitwise equal to the unchunked ones and match the oracle (64 chunks: more
+    # than there are tiles, so one tile per chunk)
+    pb = synth.small_lossy_3d(shape=(16, 32, 64), pml=3, Nt=20)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(39).standard_normal((pb.Nt, ref.Ns))
+    outs = []
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")   # the same layout and radix schedule for both plans
+    for c in ("1", chunks):
+        monkeypatch.setenv("PAT_SPEC_CHUNKS", c)
+        op = _gpu_op(pb, "f32", dev)
+        outs.append((op.forward(_t(pb.p0, "f32", dev)), op.adjoint(_t(h, "f32", dev)), op.info.spec_chunks))
+        op.close()
+    assert outs[0][2] == 1 and outs[1][2] > 1
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert rel(outs[1][0].cpu().numpy(), ref.forward(pb.p0)) <= TOL32
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

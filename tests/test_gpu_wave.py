@@ -239,17 +239,22 @@ def test_tube_128_full_size_prefix_and_dot(dev):
 def test_tube_256_full_size_prefix_adjoint_and_dot(dev):
     # 256^3, Nt = 1500, 128 x 128 sensors: the benchmark's default configuration (about 2.5 GB of
     # device state, the kernels compiled for 256-point lines).  The oracle at this size manages a
-    # few dozen steps: the first KF = 24 samples of the forward record (the tubes start 6 px beyond
-    # the sensor plane, about 3.3 steps per px, so the record holds 1-4 % of max p0 by then), the
-    # adjoint of a residual supported on the first K = 3 samples (the adjoint wave spreads from the
-    # sensor plane for 3 steps) vs the oracle, and the dot identity over all 1500 samples.
+    # few dozen steps: the first KF = 24 samples of the forward record, the adjoint of a residual
+    # supported on the first K = 3 samples (the adjoint wave spreads from the sensor plane for 3
+    # steps) vs the oracle, and the dot identity over all 1500 samples.  The phantom's tubes start
+    # 6 px beyond the sensor plane (about 3.3 steps per px), so over the first 24 samples most of its
+    # record is the pre-arrival floor, ~1e-6 of the field, where FP32 rounding of the field decides
+    # the error; the forward prefix therefore adds a smooth ball 5 px from the plane, whose wave
+    # reaches the sensors within the prefix.
     pb = synth.tube_phantom_3d(seed=3, n=256, pml=20, Nt=1500, sensors=128)
     KF = 24
     op = _gpu_op(pb, "f32", dev)
     assert op.info.path == 0
-    d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
-    d_ref = Operator.from_problem(pb, Nt=KF).forward(pb.p0)
-    assert np.abs(d_ref[KF - 4:]).max() > 1e-2 * np.abs(pb.p0).max()
+    zz, yy, xx = np.meshgrid(*[np.arange(256)] * 3, indexing="ij")
+    x0 = pb.p0 + np.exp(-((zz - 25.0) ** 2 + (yy - 128.0) ** 2 + (xx - 128.0) ** 2) / (2 * 2.0 ** 2))
+    d = op.forward(_t(x0, "f32", dev)).cpu().numpy()
+    d_ref = Operator.from_problem(pb, Nt=KF).forward(x0)
+    assert np.abs(d_ref[KF - 4:]).max() > 5e-2 * np.abs(x0).max()
     assert rel(d[:KF], d_ref) <= TOL32
     K = 3
     ref = Operator.from_problem(pb, Nt=K)

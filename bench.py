@@ -682,6 +682,18 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
     B_pt = (2 * (2 * len(pb.shape) + 1) + (4 if op.lossy else 2)) * w
     step_roof = {"bytes_per_pt_step": B_pt, "achieved_gbs": value * 1e9 * B_pt / 1e9 / world,
                  "frac": value * B_pt / world / peak, "peak": peak, "unit": "GB/s"}
+    # whole-step FP32 roofline: algorithmic flops per grid-point-step of the packed transforms, about
+    # 5.5 (2-D lossy) or 7 (3-D lossy) complex-transform equivalents of 5 log2 N flops each, against
+    # the FMA throughput measured by the library's probe
+    alu = None
+    if prec == "f32" and op.lossy:
+        from paper_1603_02329_gb300.api import probe_fp32_peak
+
+        flops_pt = (7.0 if len(pb.shape) == 3 else 5.5) * 5.0 * np.log2(pb.N)
+        fpeak = probe_fp32_peak(dev)
+        ach = value / world * flops_pt / 1e3
+        alu = {"bound": "alu", "flops_per_pt_step": flops_pt, "achieved": ach, "peak": fpeak, "unit": "TFLOP/s",
+               "frac": ach / fpeak, "peak_source": "pat_probe_fp32_peak (measured FP32 FMA throughput)"}
 
     # per time step of the graph path: (3 or 2) spectral operations of 1 (2-D) or 3 (3-D: y, z, y)
     # launches, and as many row kernels
@@ -695,7 +707,7 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
                           layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
                           radix_schedule=int(op.info.schedule), spec_chunks=int(op.info.spec_chunks),
                           parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)]),
-           "roofline": roof, "step_roofline": step_roof, "kernel_ms": kernels, "e2e": e2e,
+           "roofline": roof, "step_roofline": step_roof, "fp32_roofline": alu, "kernel_ms": kernels, "e2e": e2e,
            "gpu_launches": launches, "clocks": clk}
     return rec, op, pb
 
@@ -725,8 +737,8 @@ def main():
     out = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic"}
-    out.update({k: rec[k] for k in ("config", "roofline", "step_roofline", "kernel_ms", "e2e", "gpu_launches",
-                                    "clocks")})
+    out.update({k: rec[k] for k in ("config", "roofline", "step_roofline", "fp32_roofline", "kernel_ms", "e2e",
+                                    "gpu_launches", "clocks")})
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args, pb)
     x = None

@@ -475,6 +475,12 @@ pat_status pat_plan_read_trace(pat_plan* plan, unsigned long long* out, size_t c
  * normal operation.  No effect on the per-phase (graph) path, which has no device-side waits. */
 pat_status pat_plan_set_fault(pat_plan* plan, int barrier_extra, double wait_limit_s);
 
+/* pat_probe_fp32_peak -- measurement aid, not part of the method: *tflops = the FP32 FMA throughput
+ * of the current device in TFLOP/s (best of three timed launches of eight independent FMA chains per
+ * thread, 8 CTAs of 256 threads per SM), the denominator of the FP32 instruction roofline of the
+ * spectral kernels.  Allocates and frees a few bytes on `stream`; synchronises it. */
+pat_status pat_probe_fp32_peak(double* tflops, void* stream);
+
 /* pat_last_error -- message describing the calling thread's last failed call ("" if none).
  * The pointer stays valid until the next pat_* call on the same thread. */
 const char* pat_last_error(void);

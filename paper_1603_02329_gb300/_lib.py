@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.pat_gradient_rho.restype = i32
     L.pat_gradient_medium.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
     L.pat_gradient_medium.restype = i32
+    L.pat_probe_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
+    L.pat_probe_fp32_peak.restype = i32
     L.pat_time_reversal.argtypes = [vp, vp, vp, i32, ctypes.c_double, vp]
     L.pat_time_reversal.restype = i32
     L.pat_adjoint_atd.argtypes = [vp, vp, vp, i32, vp]

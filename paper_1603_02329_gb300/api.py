@@ -418,6 +418,15 @@ FISTA_DEFAULTS = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25, vartheta=
                       eps_c=1e-2, tv_rho=1e-2, n_tv=20, max_iter=50, recursion=True, target_re=0.0)
 
 
+def probe_fp32_peak(device=None) -> float:
+    """pat_probe_fp32_peak: measured FP32 FMA throughput of the device [TFLOP/s]."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    v = ctypes.c_double()
+    with torch.cuda.device(dev):
+        check(lib().pat_probe_fp32_peak(ctypes.byref(v), _stream_ptr(None, dev)))
+    return v.value
+
+
 def mg_fista(fine: "PATOperator", coarse: Optional["PATOperator"], data: torch.Tensor, x0: torch.Tensor, L: float,
              L_coarse: float = 0.0, p_exact: Optional[torch.Tensor] = None, callback=None, stream=None, **opts):
     """pat_mg_fista: Alg. 3 (two levels) or Alg. 2 / Alg. 1.  Returns (x, report dict, records).

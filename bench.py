@@ -423,14 +423,14 @@ def mg_vs_fista(args, dev, pb):
     common = dict(variant=1, lam=1e-2, step_scale=1.0, kappa=0.25 if d == 2 else 0.125, vartheta=0.1, q_d=3,
                   q_c=8, eps_d=-1.0, eps_c=1e-2, tv_rho=1e-2 if d == 2 else 3e-2, n_tv=20)
 
-    def timed(coarse, recursion, max_iter, target):
+    def timed(coarse, recursion, max_iter, target, coarse_weight=0.0):
         stamps = []
         t_start = time.perf_counter()
         Lco = Lc
         if coarse is not None and opc2 is not None:
             coarse, Lco = [opc, opc2], [Lc, Lc2]
         _, rep, recs = mg_fista(op, coarse, data, x0, L, L_coarse=Lco, p_exact=x_true, recursion=recursion,
-                                max_iter=max_iter, target_re=target,
+                                max_iter=max_iter, target_re=target, coarse_weight=coarse_weight,
                                 callback=lambda r: stamps.append(time.perf_counter() - t_start), **common)
         for r, ts in zip(recs, stamps):
             r["t"] = ts
@@ -444,6 +444,9 @@ def mg_vs_fista(args, dev, pb):
     rep_m, recs_m = timed(opc, True, args.mg_iters, target)
     hit = [r for r in recs_m if r["RE"] <= target]
     t_m = hit[0]["t"] if hit else None
+    # the coarse data term as Eq. (Fourteen) prints it (weight 1) instead of reading O11's 2^(1-d)
+    _, recs_u = timed(opc, True, min(args.mg_iters, it_f + 1), target, coarse_weight=1.0)   # capped: past FISTA's count it cannot win
+    hit_u = [r for r in recs_u if r["RE"] <= target]
 
     def pair_s(o):   # one forward + one adjoint solve of a level (the cost unit of both methods)
         xx = torch.zeros(o.shape, dtype=torch.float32, device=dev)
@@ -465,6 +468,8 @@ def mg_vs_fista(args, dev, pb):
             "mgfista_s": t_m, "mgfista_iters": hit[0]["k"] if hit else None,
             "mgfista_recursive_iters": sum(1 for r in recs_m if r["branch"] == "recursive"),
             "speedup": (t_f / t_m) if t_m else None, "setup_s_power_method": setup_s,
+            "unweighted_coarse_term": {"mgfista_curve": curve(recs_u), "mgfista_s": hit_u[0]["t"] if hit_u else None,
+                                       "speedup": (t_f / hit_u[0]["t"]) if hit_u else None},
             "data": data_desc,
             "params": dict(common, lam=1e-2, L=L, L_coarse=Lc, L_coarse2=Lc2)}
 

@@ -177,12 +177,6 @@ template <typename T> struct Plan : public PlanBase {
         if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
-        if (side_stream) {
-            cudaStreamSynchronize(side_stream);
-            cudaStreamDestroy(side_stream);
-        }
-        if (fork_ev) cudaEventDestroy(fork_ev);
-        if (join_ev) cudaEventDestroy(join_ev);
         for (int g = 0; g < 2; ++g)
             for (cudaEvent_t ev : probe_ev[g]) cudaEventDestroy(ev);
         for (void* p : allocs) cudaFree(p);
@@ -334,14 +328,6 @@ template <typename T> struct Plan : public PlanBase {
         if (arena) return PAT_OK;
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-        if (D == 3) {
-            e = cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming);
-            if (e != cudaSuccess) return cuda_fail(e, "side stream");
-            const char* ef = std::getenv("PAT_SPEC_FORK");
-            spec_fork = (ef && std::atoi(ef) > 0) ? 1 : 0;
-        }
         CHK2(configure_persistent(h));
         info.layout[0] = persistent ? pcfg.W : cfg.col_w;
         info.layout[1] = persistent ? pcfg.ppc : cfg.row_lines;
@@ -783,37 +769,20 @@ template <typename T> struct Plan : public PlanBase {
         spectral_chain<D, MODE>(Q, s, nullptr);
     }
 
-    // 3-D spectral operation: y forward, z with the multiply, y inverse, over chunks of the column
-    // tiles.  With spec_fork, the chunks are split between `s` and the plan's side stream, forked from
-    // `s` and joined back by events, so that the passes of one half can run beside those of the other
-    // (in a capture they become two graph branches).  `name` != nullptr: probe marks on `s`.
-    cudaStream_t side_stream = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    int spec_fork = 0;
+    // 3-D spectral operation: y forward, z with the multiply, y inverse, chunk after chunk of the column
+    // tiles; `name` != nullptr: probe marks
     template <int D, int MODE> void spectral_chain(const DevPlan<T>& Q, cudaStream_t s, const char* name) {
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
-        const int tiles = spec_tiles();
-        const bool fork = spec_fork && side_stream && tiles >= 2;
-        const int nc = fork ? std::max(2, chunk_count()) : chunk_count();
-        if (fork) {
-            cudaEventRecord(fork_ev, s);
-            cudaStreamWaitEvent(side_stream, fork_ev, 0);
-        }
+        const int tiles = spec_tiles(), nc = chunk_count();
         for (int c = 0; c < nc; ++c) {
             const int t0 = (int)((long long)c * tiles / nc), t1 = (int)((long long)(c + 1) * tiles / nc);
-            cudaStream_t cs = (fork && c >= nc / 2) ? side_stream : s;
-            const bool mk = name && cs == s;
-            if (mk) mark(s, "spec_y_fwd");
-            spec_launch_on<D, SPEC_PLAIN_FWD>(Q, cs, 1, fin, t0, t1 - t0);
-            if (mk) mark(s, name);
-            spec_launch_on<D, MODE>(Q, cs, 2, 0, t0, t1 - t0);
-            if (mk) mark(s, "spec_y_inv");
-            spec_launch_on<D, SPEC_PLAIN_INV>(Q, cs, 1, fout, t0, t1 - t0);
-        }
-        if (fork) {
-            cudaEventRecord(join_ev, side_stream);
-            cudaStreamWaitEvent(s, join_ev, 0);
+            if (name) mark(s, "spec_y_fwd");
+            spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
+            if (name) mark(s, name);
+            spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
+            if (name) mark(s, "spec_y_inv");
+            spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);
         }
     }
 

@@ -131,3 +131,20 @@ def test_adjoint_then_discretize_with_smoothing(dev):
     op.set_smoothing(True)
     g = op.adjoint_atd(_T(h, "f64", dev)).cpu().numpy()
     assert rel(g, adjoint_then_discretize(ref, h)) <= 1e-11
+
+
+def test_time_reversal_and_atd_on_the_512_workload(dev):
+    # the 2-D 512^2 absorbing workload at full size (Nt = 2000, 512 line sensors on the first row inside
+    # the PML), FP32, against the oracle: the compensated time-reversal image of the noise-free data,
+    # and the adjoint-then-discretize image of that data as the residual (about 35 s of oracle per solve)
+    from paper_1603_02329_gb300.api import PATOperator
+
+    pb = synth.vessel_phantom_2d()
+    ref = Operator.from_problem(pb)
+    op = PATOperator.from_problem(pb, precision="f32", device=dev)
+    d_ref = ref.forward(pb.p0)           # the oracle's record is the input of both sides
+    d = _T(d_ref, "f32", dev)
+    img = op.time_reversal(d, compensate=True, k_cut=0.5).cpu().numpy()
+    assert rel(img, time_reversal(ref, d_ref, compensate=True, k_cut=0.5)) <= 1e-5
+    g = op.adjoint_atd(d).cpu().numpy()
+    assert rel(g, adjoint_then_discretize(ref, d_ref)) <= 1e-5

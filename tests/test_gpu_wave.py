@@ -472,12 +472,11 @@ def test_autotuned_radix_schedule_matches_oracle(dev, monkeypatch, name, kw):
     assert _gpu_op(pb, "f32", dev).info.schedule == 2
 
 
-@pytest.mark.parametrize("chunks,fork", [("2", "0"), ("3", "0"), ("64", "0"), ("2", "1"), ("5", "1")])
-def test_chunked_spectral_passes_are_bitwise_equal(dev, monkeypatch, chunks, fork):
+@pytest.mark.parametrize("chunks", ["2", "3", "64"])
+def test_chunked_spectral_passes_are_bitwise_equal(dev, monkeypatch, chunks):
     # a 3-D spectral operation run chunk by chunk over its column tiles does the same arithmetic per
     # tile: the solves are bitwise equal to the unchunked ones and match the oracle (64 chunks: more
-    # than there are tiles, so one tile per chunk).  fork = 1: the chunks run on two streams (two graph
-    # branches) joined before the next row kernel.
+    # than there are tiles, so one tile per chunk)
     pb = synth.small_lossy_3d(shape=(16, 32, 64), pml=3, Nt=20)
     ref = Operator.from_problem(pb)
     h = np.random.default_rng(39).standard_normal((pb.Nt, ref.Ns))
@@ -485,7 +484,6 @@ def test_chunked_spectral_passes_are_bitwise_equal(dev, monkeypatch, chunks, for
     monkeypatch.setenv("PAT_AUTOTUNE", "0")   # the same layout and radix schedule for both plans
     for c in ("1", chunks):
         monkeypatch.setenv("PAT_SPEC_CHUNKS", c)
-        monkeypatch.setenv("PAT_SPEC_FORK", fork if c != "1" else "0")
         op = _gpu_op(pb, "f32", dev)
         outs.append((op.forward(_t(pb.p0, "f32", dev)), op.adjoint(_t(h, "f32", dev)), op.info.spec_chunks))
         op.close()

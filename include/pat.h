@@ -91,7 +91,9 @@ typedef struct {
     int schedule;       /* radix schedule of the 3-D spectral passes over 128- or 256-point lines, timed
                            with the layouts on path 0 (PAT_SPEC16 pins it): 0 = stages (r0, 8, ..., 8)
                            everywhere, 1 = two stages (n/16, 16) for the plain y transforms, 2 = two
-                           stages for every pass; 0 where no axis has such lines */
+                           stages for every pass, 3 = two stages for the plain transforms and for the
+                           multiply passes whose fields are independent (D-, its transpose, the
+                           absorption pass); 0 where no axis has such lines */
     int spec_chunks;    /* 3-D path 0: each spectral operation runs its y / z / y passes over this many
                            chunks of the half-spectrum column tiles, one chunk after the other, so
                            that a chunk's intermediate spectra can stay in L2 (timed with the layouts;

@@ -109,7 +109,7 @@ __device__ void s16_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, 
 
 // LG = 7 or 8 (128 or 256 points); D = 3
 template <typename T, int D, int MODE, int LG>
-__global__ void __launch_bounds__(256) k_spec16(DevPlan<T> P, int W, int lgW, int lax, int F) {
+__global__ void __launch_bounds__(384) k_spec16(DevPlan<T> P, int W, int lgW, int lax, int F) {
     static_assert(LG == 7 || LG == 8, "two-stage schedule for 128 or 256 points");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool MUL = (MODE != SPEC_PLAIN_FWD && MODE != SPEC_PLAIN_INV);

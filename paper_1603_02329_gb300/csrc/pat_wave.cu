@@ -253,7 +253,7 @@ template <typename T> struct Plan : public PlanBase {
             // 1 (default): the plain y passes take the two-stage schedule; 2: the fused multiply
             // passes too (measured slower at 256^3); 0: neither
             const char* e16 = std::getenv("PAT_SPEC16");
-            P.spec16 = e16 ? std::max(0, std::min(2, std::atoi(e16))) : 1;
+            P.spec16 = e16 ? std::max(0, std::min(3, std::atoi(e16))) : 1;
             info.schedule = (D == 3 && (P.stw16[1] || P.stw16[2])) ? P.spec16 : 0;
             const char* ech = std::getenv("PAT_SPEC_CHUNKS");
             spec_chunks = (D == 3 && ech) ? std::max(1, std::atoi(ech)) : 1;
@@ -378,7 +378,7 @@ template <typename T> struct Plan : public PlanBase {
         // (r0, 8, ..., 8) stages everywhere, 1 = two stages (n/16, 16) for the plain y transforms,
         // 2 = two stages for every pass (PAT_SPEC16 pins one)
         std::vector<int> scheds{P.spec16};
-        if (D == 3 && use_spec2 && (P.stw16[1] || P.stw16[2]) && !std::getenv("PAT_SPEC16")) scheds = {1, 0, 2};
+        if (D == 3 && use_spec2 && (P.stw16[1] || P.stw16[2]) && !std::getenv("PAT_SPEC16")) scheds = {1, 0, 2, 3};
         int best_sched = P.spec16;
         // chunks of column tiles per 3-D spectral operation (PAT_SPEC_CHUNKS pins it)
         std::vector<int> chunk_cands{spec_chunks};
@@ -744,9 +744,13 @@ template <typename T> struct Plan : public PlanBase {
         int lgw = 0;
         while ((1 << lgw) < cfg.col_w) ++lgw;
         if (use_spec2) {
+            // schedule 3: the field-wise multiply passes run their radix-16 stages with one thread per
+            // butterfly of each field (128 per field of an 8-column tile)
+            const bool fieldwise = (MODE == SPEC_DIV || MODE == SPEC_DIVT || MODE == SPEC_ABS);
+            const bool wide = D == 3 && Q.spec16 == 3 && fieldwise && Q.stw16[lax] != nullptr && cfg.col_w == 8;
             cudaLaunchConfig_t lc = {};
             lc.gridDim = dim3(tiles, outer);
-            lc.blockDim = dim3(256);
+            lc.blockDim = dim3(wide ? 128 * (MODE == SPEC_ABS ? 2 : D) : 256);
             // shared memory for the fields this launch holds (at most spec_smem)
             lc.dynamicSmemBytes = spec2_smem_bytes<T>(spec2_nf(D, MODE, F), lax == 1 ? H.ny : H.nz, cfg.col_w);
             lc.stream = s;

@@ -98,6 +98,8 @@ typedef struct {
                            chunks of the half-spectrum column tiles, one chunk after the other, so
                            that a chunk's intermediate spectra can stay in L2 (timed with the layouts;
                            PAT_SPEC_CHUNKS pins it); 1 elsewhere */
+    int tma;            /* 1 when the 3-D spectral passes stage their 8-column tiles with tensor-memory-access
+                           copies (cp.async.bulk.tensor, FP32 plans with lines of at most 256 points) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

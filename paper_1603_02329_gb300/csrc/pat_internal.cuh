@@ -171,6 +171,13 @@ template <typename T> struct DevPlan {
     // first column tile of a spectral launch (blockIdx.x + tile0 is the tile): a 3-D spectral operation
     // may run its y / z / y passes chunk by chunk over the column tiles (0 = the whole range at once)
     int tile0;
+    // Tensor-memory-access staging of the 3-D spectral tiles (8 columns): tmaps holds the tensor maps
+    // of the half spectra spec[0..2] for y-pass tiles (boxes of 8 columns x ny lines) at [0..2] and for
+    // z-pass tiles (8 columns x nz lines) at [3..5], in device memory; use_tma = 0 stages with cp.async.
+    // fault: the plan's status word, set to PAT_ETIMEOUT when a bounded wait for a tile runs out.
+    const void* tmaps;
+    int use_tma;
+    unsigned* fault;
 
     // phase-timeline trace of the persistent kernel (nullptr = off): globaltimer at entry and
     // exit of grid barriers trace_k0 .. trace_k0 + trace_nk - 1, per CTA

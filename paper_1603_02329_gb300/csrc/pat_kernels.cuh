@@ -57,6 +57,44 @@ template <typename T> __device__ __forceinline__ void stage_elems(T* s, const T*
     for (int k = threadIdx.x; k < n; k += blockDim.x) cp_async<sizeof(T)>(s + k, g + k);
 }
 
+// ------------------------------------------------------------------------------------------
+// tensor memory access (cp.async.bulk.tensor) with an mbarrier that counts the bytes in flight
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (tensor-copy) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+// box of a 3-D tensor map at coordinates (c0, c1, c2) into shared memory, completing on `bar`
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(d),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(b)
+        : "memory");
+}
+// wait for phase `parity` of the barrier to complete, at most `tries` polls; true when it did
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned tries) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    for (unsigned k = 0; k < tries; ++k) {
+        unsigned done = 0;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Wait for the preceding kernel of the stream (and its memory) -- a no-op without PDL.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 // Let the next kernel of the stream start its prologue.

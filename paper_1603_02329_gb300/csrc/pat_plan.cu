@@ -632,7 +632,8 @@ pat_status pat_plan_status(pat_plan* plan) {
         e = cudaMemcpy(&f, b->fstat, sizeof(f), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read status word");
         if (f != 0) {
-            set_error("the last solve's output holds NaN or infinite values");
+            set_error(f == PAT_ETIMEOUT ? "a bounded device-side wait ran out (tensor copy of a spectral tile)"
+                                        : "the last solve's output holds NaN or infinite values");
             return (pat_status)f;
         }
     }

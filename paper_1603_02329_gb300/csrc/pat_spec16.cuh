@@ -111,7 +111,7 @@ __device__ void s16_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, 
 template <typename T, int D, int MODE, int LG>
 __global__ void __launch_bounds__(384) k_spec16(DevPlan<T> P, int W, int lgW, int lax, int F) {
     static_assert(LG == 7 || LG == 8, "two-stage schedule for 128 or 256 points");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr bool MUL = (MODE != SPEC_PLAIN_FWD && MODE != SPEC_PLAIN_INV);
     constexpr int L = 1 << LG, R1 = L / 16;
     const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
@@ -139,24 +139,7 @@ __global__ void __launch_bounds__(384) k_spec16(DevPlan<T> P, int W, int lgW, in
     pdl_trigger();
     pdl_wait();
     // stage the tile's columns of every input field: B[f][i][c] (k_spec2's staging)
-    const int cb = W * (int)sizeof(cplx<T>);
-    for (int f = 0; f < fin; ++f) {
-        const cplx<T>* src = P.spec[f] + base;
-        cplx<T>* d = B + f * L * W;
-        if (cb >= 16) {
-            constexpr int EPC = 16 / (int)sizeof(cplx<T>);
-            const int cpr = cb / 16, lgc = lgW - (EPC == 2 ? 1 : 0);
-            for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
-                const int i = t >> lgc, ch = t & (cpr - 1);
-                cp_async<16>(d + i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
-            }
-        } else {
-            for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async<sizeof(cplx<T>)>(d + i, src + (size_t)i * es);
-        }
-    }
-    cp_commit();
-    cp_wait_all();
-    __syncthreads();
+    if (!spec_stage_tile(P, B, fin, L, W, lgW, lax, kx0, outer, base, es)) return;
 
     if constexpr (MODE == SPEC_PLAIN_INV) {
         s2_in<T, 16, true>(A, B, fin, W, lgW, ay);

@@ -19,6 +19,58 @@
 
 namespace pat {
 
+// Stage the tile's columns of the fin input fields into B[f][i][c] (dense, W columns per line; tiles
+// reach into the zeroed padding columns of the half spectra, kx0 + W <= ldh).  With the plan's tensor
+// maps (FP32, W = 8 columns: 64-byte rows; lines of at most 256 points), one thread issues one tensor
+// copy per field onto an mbarrier that counts the bytes, and the CTA waits for them; otherwise every
+// thread issues 16-byte cp.async copies.  The wait is bounded: when it runs out the status word gets
+// PAT_ETIMEOUT, the CTA waits (bounded again) for the copies in flight and the function returns
+// false in every thread, and the caller returns.
+template <typename T>
+__device__ __forceinline__ bool spec_stage_tile(const DevPlan<T>& P, cplx<T>* B, int fin, int L, int W, int lgW,
+                                                int lax, int kx0, int outer, size_t base, size_t es) {
+    __shared__ unsigned long long tma_bar;
+    const bool tma = sizeof(T) == 4 && P.use_tma && W == 8 && L <= 256 &&
+                     (((unsigned)__cvta_generic_to_shared(B)) & 127u) == 0;
+    if (tma) {
+        if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&tma_bar, (unsigned)((size_t)fin * L * W * sizeof(cplx<T>)));
+            const char* maps = static_cast<const char*>(P.tmaps) + (lax == 1 ? 0 : 3) * 128;
+            for (int f = 0; f < fin; ++f)
+                tma_load_3d(B + (size_t)f * L * W, maps + f * 128, 2 * kx0, lax == 1 ? 0 : outer, lax == 1 ? outer : 0,
+                            &tma_bar);
+        }
+        const bool ok = mbar_wait(&tma_bar, 0, 1u << 22);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0 && P.fault) atomicExch(P.fault, (unsigned)PAT_ETIMEOUT);
+            mbar_wait(&tma_bar, 0, 1u << 22);
+            return false;
+        }
+        return true;
+    }
+    const int cb = W * (int)sizeof(cplx<T>);
+    for (int f = 0; f < fin; ++f) {
+        const cplx<T>* src = P.spec[f] + base;
+        cplx<T>* d = B + f * L * W;
+        if (cb >= 16) {
+            constexpr int EPC = 16 / (int)sizeof(cplx<T>);
+            const int cpr = cb / 16, lgc = lgW - (EPC == 2 ? 1 : 0);   // 16-byte pieces per row: 2^lgc
+            for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
+                const int i = t >> lgc, ch = t & (cpr - 1);
+                cp_async<16>(d + i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
+            }
+        } else {
+            for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async<sizeof(cplx<T>)>(d + i, src + (size_t)i * es);
+        }
+    }
+    cp_commit();
+    cp_wait_all();
+    __syncthreads();
+    return true;
+}
+
 // stage 0 (radix R, no twiddles; forward or inverse) from the staged tile S[f][i][c]
 template <typename T, int R, bool INV, class AX>
 __device__ void s2_in(cplx<T>* dst, const cplx<T>* S, int FI, int W, int lgW, const AX& ay) {
@@ -134,7 +186,7 @@ __device__ void s2_fuse(const DevPlan<T>& P, const cplx<T>* src, cplx<T>* dst, c
 // LG > 0: compiled for lines of 2^LG points (the launcher checks the plan); 0: any power of two
 template <typename T, int D, int MODE, int LG = 0>
 __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int lax, int F) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr bool MUL = (MODE != SPEC_PLAIN_FWD && MODE != SPEC_PLAIN_INV);
     const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
     const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : (MUL ? D : F));
@@ -160,26 +212,8 @@ __global__ void __launch_bounds__(256) k_spec2(DevPlan<T> P, int W, int lgW, int
     }
     pdl_trigger();
     pdl_wait();
-    // stage the tile's columns of every input field: B[f][i][c]; tiles reach into the zeroed
-    // padding columns of the half spectra (kx0 + W <= ldh)
-    const int cb = W * (int)sizeof(cplx<T>);
-    for (int f = 0; f < fin; ++f) {
-        const cplx<T>* src = P.spec[f] + base;
-        cplx<T>* d = B + f * L * W;
-        if (cb >= 16) {
-            constexpr int EPC = 16 / (int)sizeof(cplx<T>);
-            const int cpr = cb / 16, lgc = lgW - (EPC == 2 ? 1 : 0);   // 16-byte pieces per row: 2^lgc
-            for (int t = threadIdx.x; t < L * cpr; t += blockDim.x) {
-                const int i = t >> lgc, ch = t & (cpr - 1);
-                cp_async<16>(d + i * W + ch * EPC, src + (size_t)i * es + ch * EPC);
-            }
-        } else {
-            for (int i = threadIdx.x; i < L; i += blockDim.x) cp_async<sizeof(cplx<T>)>(d + i, src + (size_t)i * es);
-        }
-    }
-    cp_commit();
-    cp_wait_all();
-    __syncthreads();
+    // stage the tile's columns of every input field: B[f][i][c]
+    if (!spec_stage_tile(P, B, fin, L, W, lgW, lax, kx0, outer, base, es)) return;
 
     if constexpr (MODE == SPEC_PLAIN_INV) {
         s2_in<T, 8, true>(A, B, fin, W, lgW, ay);

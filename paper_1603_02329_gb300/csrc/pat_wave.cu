@@ -6,6 +6,10 @@
 #include <cstdio>
 #include <cstring>
 
+#include <cuda.h>   // CUtensorMap and its encoder's types; the encoder is fetched from the driver at run time
+
+#include <mutex>
+
 #include "pat_host.h"
 #include "pat_persist.cuh"
 #include "pat_p2.h"
@@ -102,6 +106,27 @@ template <typename T, int D> __global__ void __launch_bounds__(256) k_atd_a5_inv
             const size_t idx = (size_t)(line0 + r) * nx + i;
             P.img[idx] = P.img[idx] - slot(res, R + r, i, nx) / P.c2[idx];
         }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
 }
 
 template <typename T> struct Plan : public PlanBase {
@@ -325,7 +350,9 @@ template <typename T> struct Plan : public PlanBase {
         if (D == 2) st = set_attrs<2>();
         else st = set_attrs<3>();
         if (st != PAT_OK) return st;
+        P.fault = fstat;
         if (arena) return PAT_OK;
+        CHK2(build_tmaps());
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
         CHK2(configure_persistent(h));
@@ -336,6 +363,41 @@ template <typename T> struct Plan : public PlanBase {
             if (st != PAT_OK) return st;
         }
         info.spec_chunks = (!persistent && D == 3) ? chunk_count() : 1;
+        return PAT_OK;
+    }
+
+    // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
+    // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
+    // PAT_TMA=0 keeps the cp.async staging.  Without the driver's encoder, or for other plans, nothing.
+    pat_status build_tmaps() {
+        P.tmaps = nullptr;
+        P.use_tma = 0;
+        const char* ev = std::getenv("PAT_TMA");
+        if (ev && std::atoi(ev) == 0) return PAT_OK;
+        if (sizeof(T) != 4 || H.d != 3 || !use_spec2 || H.ny > 256 || H.nz > 256) return PAT_OK;
+        EncodeTiledFn enc = encode_tiled();
+        if (!enc) return PAT_OK;
+        CUtensorMap maps[6];
+        const cuuint64_t dims[3] = {(cuuint64_t)2 * H.ldh, (cuuint64_t)H.ny, (cuuint64_t)H.nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)H.ldh * sizeof(cplx<T>), (cuuint64_t)H.ny * H.ldh * sizeof(cplx<T>)};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        for (int k = 0; k < 6; ++k) {
+            const int a = k % 3;
+            const void* base = (a < std::max(H.d, 2)) ? (const void*)P.spec[a] : (const void*)P.spec[0];
+            const cuuint32_t box[3] = {16, k < 3 ? (cuuint32_t)H.ny : 1u, k < 3 ? 1u : (cuuint32_t)H.nz};
+            const CUresult r = enc(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return PAT_OK;   // keep the cp.async staging
+        }
+        pat_status st = PAT_OK;
+        void* d = dalloc<unsigned char>(sizeof(maps), &st);
+        if (!d) return st;
+        const cudaError_t e = cudaMemcpy(d, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (tensor maps)");
+        P.tmaps = d;
+        P.use_tma = 1;
+        info.tma = 1;
         return PAT_OK;
     }
 
@@ -925,6 +987,7 @@ template <typename T> struct Plan : public PlanBase {
             ok = grho && gbx && gebuf;
         }
         DevPlan<T> Pf = P;
+        Pf.use_tma = 0;   // its spectra are other buffers than the tensor maps describe
         for (int a = 0; a < D && ok; ++a) {
             ok = ok && (Pf.u[a] = (T*)alloc(N * sizeof(T))) && (Pf.rh[a] = (T*)alloc(N * sizeof(T)));
         }

@@ -492,6 +492,30 @@ def test_chunked_spectral_passes_are_bitwise_equal(dev, monkeypatch, chunks):
     assert rel(outs[1][0].cpu().numpy(), ref.forward(pb.p0)) <= TOL32
 
 
+@pytest.mark.parametrize("shape", [(16, 32, 64), (32, 64, 40), (64, 16, 32)])
+def test_tensor_copy_staging_is_bitwise_equal(dev, monkeypatch, shape):
+    from paper_1603_02329_gb300 import _lib
+
+    # the 3-D spectral passes stage their 8-column tiles with tensor copies (cp.async.bulk.tensor) by
+    # default, or with cp.async under PAT_TMA=0; the staged data and so the solves are identical
+    pb = synth.small_lossy_3d(shape=shape, pml=3, Nt=16)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(41).standard_normal((pb.Nt, ref.Ns))
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")
+    monkeypatch.setenv("PAT_COL_W", "8")
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_TMA", flag)
+        op = _gpu_op(pb, "f32", dev)
+        outs.append((op.forward(_t(pb.p0, "f32", dev)), op.adjoint(_t(h, "f32", dev)), op.info.tma))
+        assert _lib.lib().pat_plan_status(op._plan) == 0
+        op.close()
+    assert outs[0][2] == 1 and outs[1][2] == 0
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert rel(outs[0][0].cpu().numpy(), ref.forward(pb.p0)) <= TOL32
+    assert rel(outs[0][1].cpu().numpy(), ref.adjoint(h)) <= TOL32
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

@@ -109,6 +109,14 @@ template <typename T>
 cudaError_t spec2_launch(const cudaLaunchConfig_t* lc, int D, int mode, const DevPlan<T>& P, int W, int lgW, int lax,
                          int F);
 template <typename T> cudaError_t spec2_set_attrs(int bytes);
+// raise kernel k's dynamic shared-memory limit to `bytes` less its static shared memory (the spectral
+// kernels hold the mbarrier of their tensor copies there), so that the sum stays within the opt-in limit
+inline cudaError_t set_dyn_smem(const void* k, int bytes) {
+    cudaFuncAttributes a{};
+    cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes - (int)a.sharedSizeBytes);
+}
 // k_spec2's lanes step across the tile's lines: every line is followed by 16 bytes of padding
 template <typename T> __host__ __device__ __forceinline__ int spec2_line_pad() { return 16 / (int)sizeof(cplx<T>); }
 // fields a k_spec2 launch holds at once: max(fields in, fields out)

@@ -53,7 +53,7 @@ template <> cudaError_t spec2_set_attrs_f32_3d<8>(int bytes) {
         (const void*)k_spec16<float, 3, SPEC_GRADT, 8>,
     };
     for (const void* k : ks) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e = set_dyn_smem(k, bytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

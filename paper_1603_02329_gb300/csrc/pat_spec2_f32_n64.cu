@@ -30,7 +30,7 @@ template <> cudaError_t spec2_set_attrs_f32_3d<6>(int bytes) {
         (const void*)k_spec2<float, 3, SPEC_GRADT, 6>,
     };
     for (const void* k : ks) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e = set_dyn_smem(k, bytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -43,7 +43,7 @@ template <> cudaError_t spec2_set_attrs<double>(int bytes) {
         (const void*)k_spec2<double, 3, SPEC_GRADT>,
     };
     for (const void* k : ks) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e = set_dyn_smem(k, bytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -462,7 +462,7 @@ template <typename T> struct Plan : public PlanBase {
                 const size_t rs = row_smem_bytes<T>(D, H.nx, H.ldh, r), ss = spec_bytes(D, L, w);
                 const size_t r2 = use_row2 ? row2_layout<T>(D, H.nx, H.ldh, r).bytes : 0;
                 if (r2 > (size_t)optin) continue;
-                if (rs > (size_t)optin || ss > (size_t)optin) continue;
+                if (rs > (size_t)optin || ss + 64 > (size_t)optin) continue;   // 64: the spectral kernels' static mbarrier
                 cfg = c;
                 row_smem = rs;
                 row2_smem = r2;
@@ -678,7 +678,7 @@ template <typename T> struct Plan : public PlanBase {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (row_smem > (size_t)optin || spec_smem > (size_t)optin) {
+        if (row_smem > (size_t)optin || spec_smem + 64 > (size_t)optin) {
             set_error("grid too large for the shared-memory kernels of this device");
             return PAT_EUNSUPPORTED;
         }

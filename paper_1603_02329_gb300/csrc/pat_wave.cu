@@ -809,7 +809,9 @@ template <typename T> struct Plan : public PlanBase {
             // schedule 3: the field-wise multiply passes run their radix-16 stages with one thread per
             // butterfly of each field (128 per field of an 8-column tile)
             const bool fieldwise = (MODE == SPEC_DIV || MODE == SPEC_DIVT || MODE == SPEC_ABS);
-            const bool wide = D == 3 && Q.spec16 == 3 && fieldwise && Q.stw16[lax] != nullptr && cfg.col_w == 8;
+            // (k_spec16 runs only in the kernels compiled for fixed line lengths; the others keep 256 threads)
+            const bool wide = D == 3 && Q.spec16 == 3 && fieldwise && Q.stw16[lax] != nullptr && Q.fixed_len &&
+                              cfg.col_w == 8;
             cudaLaunchConfig_t lc = {};
             lc.gridDim = dim3(tiles, outer);
             lc.blockDim = dim3(wide ? 128 * (MODE == SPEC_ABS ? 2 : D) : 256);

@@ -147,10 +147,10 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
 MEASURED_TRAFFIC = {
     ("vessel2d_512", "k_persist2_adj"): 6.66e6,
     ("vessel2d_512", "k_persist2_fwd"): 8.26e6,
-    # the y forward transform at 256^3 (k_spec16 mode 0), from a capture of the three launches of one
-    # forward step (1, 3 and 2 fields: 682.5 MB over 12 field transfers) scaled to the mean launch of a
-    # forward + adjoint step (28 field transfers over 6 launches)
-    ("tube3d_256", "y_fwd"): 682.5e6 / 12 * 28 / 6,
+    # the y forward transform at 256^3 (k_spec16 mode 0, tiles staged with tensor copies), from a capture
+    # of the three launches of one forward step (1, 3 and 2 fields: 682.8 MB over 12 field transfers)
+    # scaled to the mean launch of a forward + adjoint step (28 field transfers over 6 launches)
+    ("tube3d_256", "y_fwd"): 682.8e6 / 12 * 28 / 6,
 }
 
 

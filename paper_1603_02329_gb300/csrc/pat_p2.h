@@ -136,6 +136,11 @@ template <typename T> size_t spec2_smem_bytes(int nf, int L, int W) {
     return (spec2_pre_elems<T>(L) + 2 * spec2_buf_elems<T>(nf, L, W)) * sizeof(cplx<T>);
 }
 
+// register-resident z passes of 256-point lines, float (pat_zreg.cuh): launch k_zreg<mode> with the
+// grid, stream and attributes of `lc` (block size and shared memory are set here)
+cudaError_t zreg_launch(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P);
+cudaError_t zreg_set_attrs();
+
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
 enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };
 // shared memory of k_row2: stage twiddle tables | A | B (also the staging of the spectra) | gb

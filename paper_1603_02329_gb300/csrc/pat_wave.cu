@@ -9,6 +9,7 @@
 #include <cuda.h>   // CUtensorMap and its encoder's types; the encoder is fetched from the driver at run time
 
 #include <mutex>
+#include <type_traits>
 
 #include "pat_host.h"
 #include "pat_persist.cuh"
@@ -366,6 +367,8 @@ template <typename T> struct Plan : public PlanBase {
         return PAT_OK;
     }
 
+    bool use_zreg = false;
+
     // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
     // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
     // PAT_TMA=0 keeps the cp.async staging.  Without the driver's encoder, or for other plans, nothing.
@@ -377,16 +380,20 @@ template <typename T> struct Plan : public PlanBase {
         if (sizeof(T) != 4 || H.d != 3 || !use_spec2 || H.ny > 256 || H.nz > 256) return PAT_OK;
         EncodeTiledFn enc = encode_tiled();
         if (!enc) return PAT_OK;
-        CUtensorMap maps[6];
+        // [0..2] y-pass boxes, [3..5] z-pass boxes, [6..8] z-pass boxes under the 64-byte swizzle (the
+        // register-resident z passes of 256-point lines)
+        CUtensorMap maps[9];
+        const int nmaps = (H.nz == 256) ? 9 : 6;
         const cuuint64_t dims[3] = {(cuuint64_t)2 * H.ldh, (cuuint64_t)H.ny, (cuuint64_t)H.nz};
         const cuuint64_t strides[2] = {(cuuint64_t)H.ldh * sizeof(cplx<T>), (cuuint64_t)H.ny * H.ldh * sizeof(cplx<T>)};
         const cuuint32_t estr[3] = {1, 1, 1};
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < nmaps; ++k) {
             const int a = k % 3;
             const void* base = (a < std::max(H.d, 2)) ? (const void*)P.spec[a] : (const void*)P.spec[0];
             const cuuint32_t box[3] = {16, k < 3 ? (cuuint32_t)H.ny : 1u, k < 3 ? 1u : (cuuint32_t)H.nz};
             const CUresult r = enc(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
-                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   k < 6 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_64B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return PAT_OK;   // keep the cp.async staging
         }
@@ -398,6 +405,14 @@ template <typename T> struct Plan : public PlanBase {
         P.tmaps = d;
         P.use_tma = 1;
         info.tma = 1;
+        // the register-resident z passes (fixed-length kernels, 256-point z-lines); PAT_ZREG selects them
+        const char* ez = std::getenv("PAT_ZREG");
+        use_zreg = nmaps == 9 && P.fixed_len && ez && std::atoi(ez) > 0;
+        if (use_zreg) {
+            const cudaError_t ea = zreg_set_attrs();
+            if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (z passes)");
+        }
+        info.zreg = use_zreg ? 1 : 0;
         return PAT_OK;
     }
 
@@ -839,6 +854,27 @@ template <typename T> struct Plan : public PlanBase {
 
     // 3-D spectral operation: y forward, z with the multiply, y inverse, chunk after chunk of the column
     // tiles; `name` != nullptr: probe marks
+    // the register-resident z pass applies to this plan copy (its spectra are the ones the tensor maps
+    // describe, 8-column tiles)
+    bool zreg_ok(const DevPlan<T>& Q) const { return use_zreg && Q.use_tma && cfg.col_w == 8; }
+    void zreg_launch_on(const DevPlan<T>& Q0, cudaStream_t s, int mode, int t0, int nt) {
+        if constexpr (std::is_same<T, float>::value) {
+            DevPlan<T> Q = Q0;
+            Q.tile0 = t0;
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(nt, Q.ny);
+            lc.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            note_launch(zreg_launch(&lc, mode, Q));
+        } else {
+            (void)Q0; (void)s; (void)mode; (void)t0; (void)nt;
+        }
+    }
+
     template <int D, int MODE> void spectral_chain(const DevPlan<T>& Q, cudaStream_t s, const char* name) {
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
@@ -848,7 +884,8 @@ template <typename T> struct Plan : public PlanBase {
             if (name) mark(s, "spec_y_fwd");
             spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
             if (name) mark(s, name);
-            spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
+            if (zreg_ok(Q)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
+            else spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
             if (name) mark(s, "spec_y_inv");
             spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);
         }

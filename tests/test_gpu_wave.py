@@ -516,6 +516,36 @@ def test_tensor_copy_staging_is_bitwise_equal(dev, monkeypatch, shape):
     assert rel(outs[0][1].cpu().numpy(), ref.adjoint(h)) <= TOL32
 
 
+@pytest.mark.parametrize("name,kw", [("256x16x32_lossy", dict(shape=(256, 16, 32), pml=3, Nt=18)),
+                                     ("256x32x16_lossless", dict(shape=(256, 32, 16), pml=3, Nt=16, alpha0=0.0)),
+                                     ("256x16x48_lossy_generic_x", dict(shape=(256, 16, 48), pml=3, Nt=14))])
+def test_register_z_passes_match_oracle(dev, monkeypatch, name, kw):
+    # the z passes with the multiply on 256-point z-lines held in registers (PAT_ZREG=1: 16 x 16
+    # transform per half-warp, tiles by tensor copies under the 64-byte swizzle) against the oracle and
+    # against the shared-memory z passes (different rounding order: within 1e-6)
+    from paper_1603_02329_gb300 import _lib
+
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(43).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")
+    monkeypatch.setenv("PAT_COL_W", "8")
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_ZREG", flag)
+        op = _gpu_op(pb, "f32", dev)
+        assert op.info.zreg == int(flag)
+        d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+        g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+        assert _lib.lib().pat_plan_status(op._plan) == 0
+        assert rel(d, d_ref) <= TOL32, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= TOL32, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

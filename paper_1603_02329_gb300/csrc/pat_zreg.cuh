@@ -35,11 +35,12 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// forward 256-point transform of a line held as v[n] = x[t + 16 n]; afterwards v[k] = X[t + 16 k]
-__device__ __forceinline__ void zfwd(float2 (&v)[16], int t, float2* tb, const float2* tw) {
+// forward 256-point transform of a line held as v[n] = x[t + 16 n]; afterwards v[k] = X[t + 16 k].
+// twl[k 16 + t] = W256^(t k): lanes read consecutive entries (no bank conflicts)
+__device__ __forceinline__ void zfwd(float2 (&v)[16], int t, float2* tb, const float2* twl) {
     dft<float, 16, false>(v);
 #pragma unroll
-    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], tw[(t * k) & 255]);
+    for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], twl[k * 16 + t]);
 #pragma unroll
     for (int k = 0; k < 16; ++k) tb[t * 16 + (k ^ t)] = v[k];
     __syncwarp();
@@ -49,10 +50,10 @@ __device__ __forceinline__ void zfwd(float2 (&v)[16], int t, float2* tb, const f
     dft<float, 16, false>(v);
 }
 // inverse (unnormalised) of a line held as v[k] = X[t + 16 k]; afterwards v[n] = x[t + 16 n]
-__device__ __forceinline__ void zinv(float2 (&v)[16], int t, float2* tb, const float2* tw) {
+__device__ __forceinline__ void zinv(float2 (&v)[16], int t, float2* tb, const float2* twl) {
     dft<float, 16, true>(v);
 #pragma unroll
-    for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], tw[(t * k) & 255]);
+    for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], twl[k * 16 + t]);
 #pragma unroll
     for (int k = 0; k < 16; ++k) tb[t * 16 + (k ^ t)] = v[k];
     __syncwarp();
@@ -67,10 +68,11 @@ template <int MODE> struct ZregDims {
     static constexpr int FO = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : 3);
     static constexpr int NF = FI > FO ? FI : FO;   // fields the tile holds; 128 threads (8 lines) each
 };
-// shared memory: tile [NF][256][8] | transpose blocks [8 NF][16][16] | twiddles [256] | z shift [256]
-// (complex) | z wavenumbers [256] (real) | mbarrier
+// shared memory: tile [NF][256][8] | transpose blocks [8 NF][16][16] | twiddles [256] (the plan's,
+// staged) | lane-major twiddles [16][16] | z shift [256] (complex) | z wavenumbers [256] | kappa / N of
+// the tile [8][256] (real) | mbarrier
 template <int MODE> __host__ __device__ constexpr size_t zreg_smem_bytes() {
-    return (size_t)(ZregDims<MODE>::NF * 2048 + ZregDims<MODE>::NF * 2048 + 512) * 8 + 256 * 4 + 16;
+    return (size_t)(ZregDims<MODE>::NF * 2048 + ZregDims<MODE>::NF * 2048 + 768) * 8 + 256 * 4 + 2048 * 4 + 16;
 }
 
 template <int MODE>
@@ -81,9 +83,11 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
     float2* stg = reinterpret_cast<float2*>(smem_raw);
     float2* tbuf = stg + NF * 2048;
     float2* tw = tbuf + NF * 2048;
-    float2* ml = tw + 256;
+    float2* twl = tw + 256;
+    float2* ml = twl + 256;
     float* kl = reinterpret_cast<float*>(ml + 256);
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(kl + 256);
+    float* kap_s = kl + 256;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(kap_s + 2048);
     const int kx0 = (blockIdx.x + P.tile0) * 8, outer = blockIdx.y;
     const int h = threadIdx.x >> 4, t = threadIdx.x & 15;
     const char* maps = static_cast<const char*>(P.tmaps) + 6 * 128;   // the swizzled z-pass maps
@@ -114,6 +118,18 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
         return;
     }
 
+    // lane-major twiddles, and kappa / N of the tile's (kx, ky, kz) once for all its lines
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) twl[i] = tw[((i & 15) * (i >> 4)) & 255];
+    if constexpr (MODE != SPEC_ABS) {
+        const float ky = P.kv[1][outer];
+        for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
+            const int cc = i >> 8, m = i & 255;
+            const float kxv = P.kv[0][min(kx0 + cc, P.nxh - 1)], k = kl[m];
+            kap_s[i] = sinc_sq(P.kap_a * P.kap_a * (kxv * kxv + k * k + ky * ky)) * P.invN;
+        }
+    }
+    __syncthreads();
+
     // the multiply's column constants (padding columns take the last valid kx; their data are zero)
     const int c = h & 7;
     const int kx = min(kx0 + c, P.nxh - 1);
@@ -123,14 +139,14 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
     const float2 mo = plus ? P.dp[1][outer] : P.dm[1][outer];
     float2* tb = tbuf + h * 256;
     auto k2_at = [&](int m) { const float k = kl[m]; return ckx2 + k * k + ko2; };
-    auto kap_at = [&](int m) { return sinc_sq(P.kap_a * P.kap_a * k2_at(m)) * P.invN; };
+    auto kap_at = [&](int m) { return kap_s[c * 256 + m]; };
     float2 v[16];
 
     if constexpr (MODE == SPEC_DIV || MODE == SPEC_DIVT || MODE == SPEC_ABS) {
         const int f = h >> 3;
 #pragma unroll
         for (int n = 0; n < 16; ++n) v[n] = stg[f * 2048 + zsw(t + 16 * n, c)];
-        zfwd(v, t, tb, tw);
+        zfwd(v, t, tb, twl);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int m = t + 16 * k;
@@ -144,7 +160,7 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
                 v[k] = cscale(cmul(v[k], mf), (MODE == SPEC_DIVT) ? -kap : kap);
             }
         }
-        zinv(v, t, tb, tw);
+        zinv(v, t, tb, twl);
 #pragma unroll
         for (int n = 0; n < 16; ++n) stg[f * 2048 + zsw(t + 16 * n, c)] = v[n];
     } else if constexpr (MODE == SPEC_GRAD) {
@@ -152,7 +168,7 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
         if (h < 8) {
 #pragma unroll
             for (int n = 0; n < 16; ++n) v[n] = stg[zsw(t + 16 * n, c)];
-            zfwd(v, t, tb, tw);
+            zfwd(v, t, tb, twl);
 #pragma unroll
             for (int k = 0; k < 16; ++k) stg[zsw(t + 16 * k, c)] = v[k];
         }
@@ -168,14 +184,14 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
             const float2 mf = (f == 0) ? mx : (f == 1 ? mo : ml[m]);
             v[k] = cmul(cscale(v[k], kap_at(m)), mf);
         }
-        zinv(v, t, tb, tw);
+        zinv(v, t, tb, twl);
 #pragma unroll
         for (int n = 0; n < 16; ++n) stg[f * 2048 + zsw(t + 16 * n, c)] = v[n];
     } else {   // SPEC_GRADT: out = -kappa sum_f D+-_f in_f
         const int f = h >> 3;
 #pragma unroll
         for (int n = 0; n < 16; ++n) v[n] = stg[f * 2048 + zsw(t + 16 * n, c)];
-        zfwd(v, t, tb, tw);
+        zfwd(v, t, tb, twl);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int m = t + 16 * k;
@@ -192,7 +208,7 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
                 a = cadd(a, stg[4096 + zsw(m, c)]);
                 v[k] = cscale(a, -kap_at(m));
             }
-            zinv(v, t, tb, tw);
+            zinv(v, t, tb, twl);
 #pragma unroll
             for (int n = 0; n < 16; ++n) stg[zsw(t + 16 * n, c)] = v[n];
         }

@@ -100,8 +100,9 @@ typedef struct {
                            PAT_SPEC_CHUNKS pins it); 1 elsewhere */
     int tma;            /* 1 when the 3-D spectral passes stage their 8-column tiles with tensor-memory-access
                            copies (cp.async.bulk.tensor, FP32 plans with lines of at most 256 points) */
-    int zreg;           /* 1 when the z passes with the k-space multiply hold each 256-point line in
-                           registers (16 x 16 transform, half a warp per line; PAT_ZREG=1 selects it) */
+    int zreg;           /* 1 when the D- z passes (and with PAT_ZREG=2 every z pass with a multiply) hold
+                           each 256-point line in registers: 16 x 16 transform, half a warp per line
+                           (FP32 plans with tensor-copy staging and 256-point z-lines; PAT_ZREG=0 off) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

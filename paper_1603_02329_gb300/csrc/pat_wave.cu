@@ -368,6 +368,7 @@ template <typename T> struct Plan : public PlanBase {
     }
 
     bool use_zreg = false;
+    bool zreg_all = false;
 
     // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
     // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
@@ -405,9 +406,11 @@ template <typename T> struct Plan : public PlanBase {
         P.tmaps = d;
         P.use_tma = 1;
         info.tma = 1;
-        // the register-resident z passes (fixed-length kernels, 256-point z-lines); PAT_ZREG selects them
+        // the register-resident z passes (fixed-length kernels, 256-point z-lines): by default for the D-
+        // passes (DIV and its transpose), where they are faster; PAT_ZREG=0 none, 2 every multiply pass
         const char* ez = std::getenv("PAT_ZREG");
-        use_zreg = nmaps == 9 && P.fixed_len && ez && std::atoi(ez) > 0;
+        zreg_all = ez && std::atoi(ez) >= 2;
+        use_zreg = nmaps == 9 && P.fixed_len && !(ez && std::atoi(ez) == 0);
         if (use_zreg) {
             const cudaError_t ea = zreg_set_attrs();
             if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (z passes)");
@@ -884,7 +887,7 @@ template <typename T> struct Plan : public PlanBase {
             if (name) mark(s, "spec_y_fwd");
             spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
             if (name) mark(s, name);
-            if (zreg_ok(Q)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
+            if (zreg_ok(Q) && (zreg_all || MODE == SPEC_DIV || MODE == SPEC_DIVT)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
             else spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
             if (name) mark(s, "spec_y_inv");
             spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);

@@ -72,7 +72,8 @@ template <int MODE> struct ZregDims {
 // staged) | lane-major twiddles [16][16] | z shift [256] (complex) | z wavenumbers [256] | kappa / N of
 // the tile [8][256] (real) | mbarrier
 template <int MODE> __host__ __device__ constexpr size_t zreg_smem_bytes() {
-    return (size_t)(ZregDims<MODE>::NF * 2048 + ZregDims<MODE>::NF * 2048 + 768) * 8 + 256 * 4 + 2048 * 4 + 16;
+    return (size_t)(ZregDims<MODE>::NF * 2048 + ZregDims<MODE>::NF * 2048 + 768) * 8 + 256 * 4 +
+           (MODE == SPEC_ABS ? 0 : 2048 * 4) + 16;
 }
 
 template <int MODE>
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(384) k_zreg(DevPlan<float> P) {
     float2* twl = tw + 256;
     float2* ml = twl + 256;
     float* kl = reinterpret_cast<float*>(ml + 256);
-    float* kap_s = kl + 256;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(kap_s + 2048);
+    float* kap_s = kl + 256;   // (none for ABS)
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(kap_s + (MODE == SPEC_ABS ? 0 : 2048));
     const int kx0 = (blockIdx.x + P.tile0) * 8, outer = blockIdx.y;
     const int h = threadIdx.x >> 4, t = threadIdx.x & 15;
     const char* maps = static_cast<const char*>(P.tmaps) + 6 * 128;   // the swizzled z-pass maps

@@ -103,6 +103,10 @@ typedef struct {
     int zreg;           /* 1 when the D- z passes (and with PAT_ZREG=2 every z pass with a multiply) hold
                            each 256-point line in registers: 16 x 16 transform, half a warp per line
                            (FP32 plans with tensor-copy staging and 256-point z-lines; PAT_ZREG=0 off) */
+    int ywide;          /* 1 when the plain y transforms of 128- or 256-point y-lines run on 16-column tiles,
+                           one field per CTA, in place in the tile staged by one tensor copy (FP32 plans
+                           with tensor-copy staging; radix schedules 1-3, whose two-stage y transforms
+                           they compute with the same operations; one chunk; PAT_YWIDE=0 off) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

@@ -140,6 +140,10 @@ template <typename T> size_t spec2_smem_bytes(int nf, int L, int W) {
 // grid, stream and attributes of `lc` (block size and shared memory are set here)
 cudaError_t zreg_launch(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P);
 cudaError_t zreg_set_attrs();
+// plain y transforms of 128- and 256-point y-lines on 16-column tiles, float (pat_ywide.cuh): launch
+// k_ywide with the grid (ceil(nxh / 16), nz, fields), stream and attributes of `lc`
+cudaError_t ywide_launch(const cudaLaunchConfig_t* lc, bool inverse, const DevPlan<float>& P);
+cudaError_t ywide_set_attrs();
 
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
 enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };

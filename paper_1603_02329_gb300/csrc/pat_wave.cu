@@ -369,10 +369,12 @@ template <typename T> struct Plan : public PlanBase {
 
     bool use_zreg = false;
     bool zreg_all = false;
+    bool use_ywide = false;
 
     // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
     // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
     // PAT_TMA=0 keeps the cp.async staging.  Without the driver's encoder, or for other plans, nothing.
+    // Also the boxes of 16 columns of the plain y transforms on 128- and 256-point y-lines (k_ywide).
     pat_status build_tmaps() {
         P.tmaps = nullptr;
         P.use_tma = 0;
@@ -382,19 +384,23 @@ template <typename T> struct Plan : public PlanBase {
         EncodeTiledFn enc = encode_tiled();
         if (!enc) return PAT_OK;
         // [0..2] y-pass boxes, [3..5] z-pass boxes, [6..8] z-pass boxes under the 64-byte swizzle (the
-        // register-resident z passes of 256-point lines)
-        CUtensorMap maps[9];
-        const int nmaps = (H.nz == 256) ? 9 : 6;
+        // register-resident z passes of 256-point lines), [9..11] y-pass boxes of 16 columns (128-byte
+        // rows; 128- and 256-point y-lines); slots of maps a plan does not use stay zero
+        CUtensorMap maps[12];
+        std::memset(maps, 0, sizeof(maps));
+        const bool zmaps = H.nz == 256, ymaps = H.ny == 128 || H.ny == 256;
         const cuuint64_t dims[3] = {(cuuint64_t)2 * H.ldh, (cuuint64_t)H.ny, (cuuint64_t)H.nz};
         const cuuint64_t strides[2] = {(cuuint64_t)H.ldh * sizeof(cplx<T>), (cuuint64_t)H.ny * H.ldh * sizeof(cplx<T>)};
         const cuuint32_t estr[3] = {1, 1, 1};
-        for (int k = 0; k < nmaps; ++k) {
+        for (int k = 0; k < 12; ++k) {
+            if ((k >= 6 && k < 9 && !zmaps) || (k >= 9 && !ymaps)) continue;
             const int a = k % 3;
             const void* base = (a < std::max(H.d, 2)) ? (const void*)P.spec[a] : (const void*)P.spec[0];
-            const cuuint32_t box[3] = {16, k < 3 ? (cuuint32_t)H.ny : 1u, k < 3 ? 1u : (cuuint32_t)H.nz};
+            const bool ypass = k < 3 || k >= 9;
+            const cuuint32_t box[3] = {k >= 9 ? 32u : 16u, ypass ? (cuuint32_t)H.ny : 1u, ypass ? 1u : (cuuint32_t)H.nz};
             const CUresult r = enc(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                   k < 6 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_64B,
+                                   (k >= 6 && k < 9) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return PAT_OK;   // keep the cp.async staging
         }
@@ -410,12 +416,21 @@ template <typename T> struct Plan : public PlanBase {
         // passes (DIV and its transpose), where they are faster; PAT_ZREG=0 none, 2 every multiply pass
         const char* ez = std::getenv("PAT_ZREG");
         zreg_all = ez && std::atoi(ez) >= 2;
-        use_zreg = nmaps == 9 && P.fixed_len && !(ez && std::atoi(ez) == 0);
+        use_zreg = zmaps && P.fixed_len && !(ez && std::atoi(ez) == 0);
         if (use_zreg) {
             const cudaError_t ea = zreg_set_attrs();
             if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (z passes)");
         }
         info.zreg = use_zreg ? 1 : 0;
+        // the 16-column plain y transforms (fixed-length kernels, 128- and 256-point y-lines); PAT_YWIDE=0
+        // keeps k_spec16 / k_spec2 for them
+        const char* ey = std::getenv("PAT_YWIDE");
+        use_ywide = ymaps && P.fixed_len && !(ey && std::atoi(ey) == 0);
+        if (use_ywide) {
+            const cudaError_t ea = ywide_set_attrs();
+            if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (y passes)");
+        }
+        info.ywide = use_ywide ? 1 : 0;
         return PAT_OK;
     }
 
@@ -878,19 +893,42 @@ template <typename T> struct Plan : public PlanBase {
         }
     }
 
+    // the 16-column plain y transforms apply to this plan copy (the spectra of the tensor maps; the
+    // two-stage schedule of the plain y transforms, whose arithmetic they share) when the tiles run in
+    // one chunk
+    bool ywide_ok(const DevPlan<T>& Q) const { return use_ywide && Q.use_tma && Q.spec16 >= 1 && chunk_count() == 1; }
+    void ywide_launch_on(const DevPlan<T>& Q, cudaStream_t s, bool inverse, int F) {
+        if constexpr (std::is_same<T, float>::value) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3((Q.nxh + 15) / 16, Q.nz, F);
+            lc.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            note_launch(ywide_launch(&lc, inverse, Q));
+        } else {
+            (void)Q; (void)s; (void)inverse; (void)F;
+        }
+    }
+
     template <int D, int MODE> void spectral_chain(const DevPlan<T>& Q, cudaStream_t s, const char* name) {
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int tiles = spec_tiles(), nc = chunk_count();
         for (int c = 0; c < nc; ++c) {
             const int t0 = (int)((long long)c * tiles / nc), t1 = (int)((long long)(c + 1) * tiles / nc);
+            const bool yw = ywide_ok(Q);
             if (name) mark(s, "spec_y_fwd");
-            spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
+            if (yw) ywide_launch_on(Q, s, false, fin);
+            else spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
             if (name) mark(s, name);
             if (zreg_ok(Q) && (zreg_all || MODE == SPEC_DIV || MODE == SPEC_DIVT)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
             else spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
             if (name) mark(s, "spec_y_inv");
-            spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);
+            if (yw) ywide_launch_on(Q, s, true, fout);
+            else spec_launch_on<D, SPEC_PLAIN_INV>(Q, s, 1, fout, t0, t1 - t0);
         }
     }
 

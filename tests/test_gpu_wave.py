@@ -548,6 +548,40 @@ def test_register_z_passes_match_oracle(dev, monkeypatch, name, kw):
         assert rel(a[0], out[2][0]) <= 1e-6 and rel(a[1], out[2][1]) <= 1e-6
 
 
+@pytest.mark.parametrize("name,kw", [("32x256x12_lossy", dict(shape=(32, 256, 12), pml=3, Nt=16)),
+                                     ("64x128x16_lossless", dict(shape=(64, 128, 16), pml=3, Nt=16, alpha0=0.0)),
+                                     ("256x256x8_lossy", dict(shape=(256, 256, 8), pml=2, Nt=10))])
+def test_wide_y_passes_match_oracle(dev, monkeypatch, name, kw):
+    # the plain y transforms of 128- and 256-point y-lines on 16-column tiles, one field per CTA, in
+    # place in the tile staged by one tensor copy (the default), against the oracle and against the
+    # 8-column k_spec16 passes of the same two-stage schedule (PAT_YWIDE=0); the last tile holds one
+    # valid column (nxh = 17, 33, 129)
+    from paper_1603_02329_gb300 import _lib
+
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(44).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")
+    monkeypatch.setenv("PAT_COL_W", "8")
+    monkeypatch.setenv("PAT_SPEC16", "1")
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_YWIDE", flag)
+        op = _gpu_op(pb, "f32", dev)
+        assert op.info.ywide == (flag == "1")
+        d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+        g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+        assert _lib.lib().pat_plan_status(op._plan) == 0
+        assert rel(d, d_ref) <= TOL32, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= TOL32, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    print(f"{name}: wide against 8-column y passes: forward {rel(out[0][0], out[1][0]):.2e}, "
+          f"adjoint {rel(out[0][1], out[1][1]):.2e}")
+    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

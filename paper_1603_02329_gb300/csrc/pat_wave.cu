@@ -356,6 +356,7 @@ template <typename T> struct Plan : public PlanBase {
         CHK2(build_tmaps());
         cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        CHK2(build_kap());
         CHK2(configure_persistent(h));
         info.layout[0] = persistent ? pcfg.W : cfg.col_w;
         info.layout[1] = persistent ? pcfg.ppc : cfg.row_lines;
@@ -370,11 +371,14 @@ template <typename T> struct Plan : public PlanBase {
     bool use_zreg = false;
     bool zreg_all = false;
     bool use_ywide = false;
+    bool use_zwide = false;
+    float* kap3 = nullptr;   // kappa / N on the half spectrum, [ky][kz][ldh] (the 16-column z passes)
 
     // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
     // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
     // PAT_TMA=0 keeps the cp.async staging.  Without the driver's encoder, or for other plans, nothing.
-    // Also the boxes of 16 columns of the plain y transforms on 128- and 256-point y-lines (k_ywide).
+    // Also the boxes of 16 columns of the plain y transforms on 128- and 256-point y-lines (k_ywide) and
+    // of the field-wise z passes on 128- and 256-point z-lines (k_zwide).
     pat_status build_tmaps() {
         P.tmaps = nullptr;
         P.use_tma = 0;
@@ -385,18 +389,19 @@ template <typename T> struct Plan : public PlanBase {
         if (!enc) return PAT_OK;
         // [0..2] y-pass boxes, [3..5] z-pass boxes, [6..8] z-pass boxes under the 64-byte swizzle (the
         // register-resident z passes of 256-point lines), [9..11] y-pass boxes of 16 columns (128-byte
-        // rows; 128- and 256-point y-lines); slots of maps a plan does not use stay zero
-        CUtensorMap maps[12];
+        // rows; 128- and 256-point y-lines), [12..14] z-pass boxes of 16 columns (128- and 256-point
+        // z-lines); slots of maps a plan does not use stay zero
+        CUtensorMap maps[15];
         std::memset(maps, 0, sizeof(maps));
-        const bool zmaps = H.nz == 256, ymaps = H.ny == 128 || H.ny == 256;
+        const bool zmaps = H.nz == 256, ymaps = H.ny == 128 || H.ny == 256, zwmaps = H.nz == 128 || H.nz == 256;
         const cuuint64_t dims[3] = {(cuuint64_t)2 * H.ldh, (cuuint64_t)H.ny, (cuuint64_t)H.nz};
         const cuuint64_t strides[2] = {(cuuint64_t)H.ldh * sizeof(cplx<T>), (cuuint64_t)H.ny * H.ldh * sizeof(cplx<T>)};
         const cuuint32_t estr[3] = {1, 1, 1};
-        for (int k = 0; k < 12; ++k) {
-            if ((k >= 6 && k < 9 && !zmaps) || (k >= 9 && !ymaps)) continue;
+        for (int k = 0; k < 15; ++k) {
+            if ((k >= 6 && k < 9 && !zmaps) || (k >= 9 && k < 12 && !ymaps) || (k >= 12 && !zwmaps)) continue;
             const int a = k % 3;
             const void* base = (a < std::max(H.d, 2)) ? (const void*)P.spec[a] : (const void*)P.spec[0];
-            const bool ypass = k < 3 || k >= 9;
+            const bool ypass = k < 3 || (k >= 9 && k < 12);
             const cuuint32_t box[3] = {k >= 9 ? 32u : 16u, ypass ? (cuuint32_t)H.ny : 1u, ypass ? 1u : (cuuint32_t)H.nz};
             const CUresult r = enc(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -431,6 +436,28 @@ template <typename T> struct Plan : public PlanBase {
             if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (y passes)");
         }
         info.ywide = use_ywide ? 1 : 0;
+        // the 16-column field-wise z passes (fixed-length kernels, 128- and 256-point z-lines); PAT_ZWIDE=0
+        // keeps k_zreg / k_spec16 / k_spec2 for them.  Their kappa table is filled once the plan's stream
+        // exists (build_kap).
+        const char* ew = std::getenv("PAT_ZWIDE");
+        use_zwide = zwmaps && P.fixed_len && !(ew && std::atoi(ew) == 0);
+        if (use_zwide) {
+            const cudaError_t ea = zwide_set_attrs();
+            if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (z passes)");
+            pat_status st2 = PAT_OK;
+            kap3 = dalloc<float>((size_t)H.ny * H.nz * H.ldh, &st2);
+            if (!kap3) return st2;
+        }
+        info.zwide = use_zwide ? 1 : 0;
+        return PAT_OK;
+    }
+    pat_status build_kap() {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!use_zwide) return PAT_OK;
+            cudaError_t e = zwide_kap_table(P, kap3, cap_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cap_stream);
+            if (e != cudaSuccess) return cuda_fail(e, "kappa table");
+        }
         return PAT_OK;
     }
 
@@ -913,6 +940,25 @@ template <typename T> struct Plan : public PlanBase {
         }
     }
 
+    // the 16-column field-wise z passes apply to this plan copy (the spectra of the tensor maps) when the
+    // tiles run in one chunk
+    bool zwide_ok(const DevPlan<T>& Q) const { return use_zwide && Q.use_tma && chunk_count() == 1; }
+    void zwide_launch_on(const DevPlan<T>& Q, cudaStream_t s, int mode, int F) {
+        if constexpr (std::is_same<T, float>::value) {
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(F, (Q.nxh + 15) / 16, Q.ny);
+            lc.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            note_launch(zwide_launch(&lc, mode, Q, kap3));
+        } else {
+            (void)Q; (void)s; (void)mode; (void)F;
+        }
+    }
+
     template <int D, int MODE> void spectral_chain(const DevPlan<T>& Q, cudaStream_t s, const char* name) {
         const int fin = (MODE == SPEC_GRAD) ? 1 : (MODE == SPEC_ABS ? 2 : D);
         const int fout = (MODE == SPEC_GRADT) ? 1 : (MODE == SPEC_ABS ? 2 : D);
@@ -924,7 +970,8 @@ template <typename T> struct Plan : public PlanBase {
             if (yw) ywide_launch_on(Q, s, false, fin);
             else spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
             if (name) mark(s, name);
-            if (zreg_ok(Q) && (zreg_all || MODE == SPEC_DIV || MODE == SPEC_DIVT)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
+            if (zwide_ok(Q) && (MODE == SPEC_DIV || MODE == SPEC_DIVT || MODE == SPEC_ABS)) zwide_launch_on(Q, s, MODE, fin);
+            else if (zreg_ok(Q) && (zreg_all || MODE == SPEC_DIV || MODE == SPEC_DIVT)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
             else spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
             if (name) mark(s, "spec_y_inv");
             if (yw) ywide_launch_on(Q, s, true, fout);

@@ -532,8 +532,9 @@ def test_register_z_passes_match_oracle(dev, monkeypatch, name, kw):
     d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
     monkeypatch.setenv("PAT_AUTOTUNE", "0")
     monkeypatch.setenv("PAT_COL_W", "8")
+    monkeypatch.setenv("PAT_ZWIDE", "0")   # the 16-column field-wise z passes would take DIV and DIVT
     out = []
-    for flag in ("2", "1", "0"):   # every multiply pass / the D- passes (default) / none
+    for flag in ("2", "1", "0"):   # every multiply pass / the D- passes / none
         monkeypatch.setenv("PAT_ZREG", flag)
         op = _gpu_op(pb, "f32", dev)
         assert op.info.zreg == (flag != "0")
@@ -548,14 +549,18 @@ def test_register_z_passes_match_oracle(dev, monkeypatch, name, kw):
         assert rel(a[0], out[2][0]) <= 1e-6 and rel(a[1], out[2][1]) <= 1e-6
 
 
-@pytest.mark.parametrize("name,kw", [("32x256x12_lossy", dict(shape=(32, 256, 12), pml=3, Nt=16)),
-                                     ("64x128x16_lossless", dict(shape=(64, 128, 16), pml=3, Nt=16, alpha0=0.0)),
-                                     ("256x256x8_lossy", dict(shape=(256, 256, 8), pml=2, Nt=10))])
+# shapes are (nz, ny, nx); nxh = nx / 2 + 1 half-spectrum columns make ceil(nxh / 16) tiles of 16.
+# The tensor-copy staging (and so the 16-column passes) needs power-of-two y- and z-lines of 16 to 256
+# points.
+@pytest.mark.parametrize("name,kw", [("16x256x48_lossy", dict(shape=(16, 256, 48), pml=3, Nt=16)),
+                                     ("16x128x64_lossless", dict(shape=(16, 128, 64), pml=3, Nt=16, alpha0=0.0)),
+                                     ("16x256x256_lossy", dict(shape=(16, 256, 256), pml=3, Nt=8)),
+                                     ("32x256x12_lossy", dict(shape=(32, 256, 12), pml=3, Nt=16))])
 def test_wide_y_passes_match_oracle(dev, monkeypatch, name, kw):
     # the plain y transforms of 128- and 256-point y-lines on 16-column tiles, one field per CTA, in
     # place in the tile staged by one tensor copy (the default), against the oracle and against the
-    # 8-column k_spec16 passes of the same two-stage schedule (PAT_YWIDE=0); the last tile holds one
-    # valid column (nxh = 17, 33, 129)
+    # 8-column k_spec16 passes of the same two-stage schedule (PAT_YWIDE=0); nxh = 25, 33, 129, 7:
+    # 2, 3, 9 and 1 tiles, the last one partly valid
     from paper_1603_02329_gb300 import _lib
 
     pb = synth.small_lossy_3d(**kw)
@@ -578,6 +583,40 @@ def test_wide_y_passes_match_oracle(dev, monkeypatch, name, kw):
         out.append((d, g))
         op.close()
     print(f"{name}: wide against 8-column y passes: forward {rel(out[0][0], out[1][0]):.2e}, "
+          f"adjoint {rel(out[0][1], out[1][1]):.2e}")
+    assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
+
+
+@pytest.mark.parametrize("name,kw", [("256x16x48_lossy", dict(shape=(256, 16, 48), pml=3, Nt=16)),
+                                     ("128x16x64_lossy", dict(shape=(128, 16, 64), pml=3, Nt=16)),
+                                     ("128x32x32_lossless", dict(shape=(128, 32, 32), pml=3, Nt=16, alpha0=0.0)),
+                                     ("256x16x256_lossy", dict(shape=(256, 16, 256), pml=3, Nt=8))])
+def test_wide_z_passes_match_oracle(dev, monkeypatch, name, kw):
+    # the z passes with a field-wise multiply (D-, its transpose, the absorption pass) of 128- and
+    # 256-point z-lines on 16-column tiles, one field per CTA, kappa from the plan's table (the
+    # default), against the oracle and against the 8-column z passes (PAT_ZWIDE=0: k_zreg for D- and
+    # its transpose on 256-point lines, k_spec2 otherwise); shapes (nz, ny, nx), 2, 3, 2 and 9 tiles
+    from paper_1603_02329_gb300 import _lib
+
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(45).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")
+    monkeypatch.setenv("PAT_COL_W", "8")
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("PAT_ZWIDE", flag)
+        op = _gpu_op(pb, "f32", dev)
+        assert op.info.zwide == (flag == "1")
+        d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+        g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+        assert _lib.lib().pat_plan_status(op._plan) == 0
+        assert rel(d, d_ref) <= TOL32, (flag, rel(d, d_ref))
+        assert rel(g, g_ref) <= TOL32, (flag, rel(g, g_ref))
+        out.append((d, g))
+        op.close()
+    print(f"{name}: wide against 8-column z passes: forward {rel(out[0][0], out[1][0]):.2e}, "
           f"adjoint {rel(out[0][1], out[1][1]):.2e}")
     assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
 

@@ -107,11 +107,11 @@ typedef struct {
                            one field per CTA, in place in the tile staged by one tensor copy (FP32 plans
                            with tensor-copy staging; radix schedules 1-3, whose two-stage y transforms
                            they compute with the same operations; one chunk; PAT_YWIDE=0 off) */
-    int zwide;          /* 1 when the z passes with a field-wise multiply (D-, its transpose, the absorption
-                           pass) of 128- or 256-point z-lines run on 16-column tiles, one field per CTA,
-                           in place in the tile staged by one tensor copy, with kappa / N from a table
-                           the plan fills once (FP32 plans with tensor-copy staging; one chunk;
-                           PAT_ZWIDE=0 off) */
+    int zwide;          /* 1 when the z passes with the multiply (D+, D-, their transposes, the absorption
+                           pass) of 128- or 256-point z-lines run on 16-column tiles transformed in place
+                           in shared memory after one tensor copy per input field, with the multipliers
+                           from tables the plan fills once (FP32 plans with tensor-copy staging; one
+                           chunk; PAT_ZWIDE=0 off) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

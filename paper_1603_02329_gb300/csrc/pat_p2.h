@@ -144,12 +144,14 @@ cudaError_t zreg_set_attrs();
 // k_ywide with the grid (ceil(nxh / 16), nz, fields), stream and attributes of `lc`
 cudaError_t ywide_launch(const cudaLaunchConfig_t* lc, bool inverse, const DevPlan<float>& P);
 cudaError_t ywide_set_attrs();
-// z passes with a field-wise multiply (SPEC_DIV, SPEC_DIVT, SPEC_ABS) of 128- and 256-point z-lines
-// on 16-column tiles, float (pat_zwide.cuh): launch k_zwide with the grid (fields, ceil(nxh / 16), ny),
-// stream and attributes of `lc`; kap = the plan's kappa / N table (zwide_kap_table, [ky][kz][ldh])
-cudaError_t zwide_launch(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P, const float* kap);
+// z passes with the k-space multiply of 128- and 256-point z-lines on 16-column tiles, float
+// (pat_zwide.cuh): launch k_zwide<mode> with the grid ((fields or 1), ceil(nxh / 16), ny), stream and
+// attributes of `lc`; mt = the plan's kappa / N table (zwide_kap_table, [ky][kz][ldh]) for every mode
+// but SPEC_ABS, the absorption tables (zwide_abs_table, [2][ky][kz][ldh]) or nullptr for SPEC_ABS
+cudaError_t zwide_launch(const cudaLaunchConfig_t* lc, int mode, const DevPlan<float>& P, const float* mt);
 cudaError_t zwide_set_attrs();
 cudaError_t zwide_kap_table(const DevPlan<float>& P, float* kap, cudaStream_t s);
+cudaError_t zwide_abs_table(const DevPlan<float>& P, float* tab, cudaStream_t s);
 
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
 enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };

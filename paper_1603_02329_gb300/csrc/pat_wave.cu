@@ -373,6 +373,7 @@ template <typename T> struct Plan : public PlanBase {
     bool use_ywide = false;
     bool use_zwide = false;
     float* kap3 = nullptr;   // kappa / N on the half spectrum, [ky][kz][ldh] (the 16-column z passes)
+    float* abs3 = nullptr;   // |k|^(y-2) / N and |k|^(y-1) / N, [2][ky][kz][ldh] (absorbing plans)
 
     // Tensor maps of the half spectra for the 3-D spectral tiles (FP32; boxes of 8 columns x the whole
     // line: ny for y passes, nz for z passes; lines of at most 256 points): staging by tensor copies.
@@ -436,8 +437,8 @@ template <typename T> struct Plan : public PlanBase {
             if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (y passes)");
         }
         info.ywide = use_ywide ? 1 : 0;
-        // the 16-column field-wise z passes (fixed-length kernels, 128- and 256-point z-lines); PAT_ZWIDE=0
-        // keeps k_zreg / k_spec16 / k_spec2 for them.  Their kappa table is filled once the plan's stream
+        // the 16-column z passes (fixed-length kernels, 128- and 256-point z-lines); PAT_ZWIDE=0 keeps
+        // k_zreg / k_spec16 / k_spec2 for them.  Their multiplier tables are filled once the plan's stream
         // exists (build_kap).
         const char* ew = std::getenv("PAT_ZWIDE");
         use_zwide = zwmaps && P.fixed_len && !(ew && std::atoi(ew) == 0);
@@ -445,8 +446,13 @@ template <typename T> struct Plan : public PlanBase {
             const cudaError_t ea = zwide_set_attrs();
             if (ea != cudaSuccess) return cuda_fail(ea, "cudaFuncSetAttribute (z passes)");
             pat_status st2 = PAT_OK;
-            kap3 = dalloc<float>((size_t)H.ny * H.nz * H.ldh, &st2);
+            const size_t nt = (size_t)H.ny * H.nz * H.ldh;
+            kap3 = dalloc<float>(nt, &st2);
             if (!kap3) return st2;
+            if (P.lossy) {
+                abs3 = dalloc<float>(2 * nt, &st2);
+                if (!abs3) return st2;
+            }
         }
         info.zwide = use_zwide ? 1 : 0;
         return PAT_OK;
@@ -455,6 +461,7 @@ template <typename T> struct Plan : public PlanBase {
         if constexpr (std::is_same<T, float>::value) {
             if (!use_zwide) return PAT_OK;
             cudaError_t e = zwide_kap_table(P, kap3, cap_stream);
+            if (e == cudaSuccess && abs3) e = zwide_abs_table(P, abs3, cap_stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(cap_stream);
             if (e != cudaSuccess) return cuda_fail(e, "kappa table");
         }
@@ -940,20 +947,24 @@ template <typename T> struct Plan : public PlanBase {
         }
     }
 
-    // the 16-column field-wise z passes apply to this plan copy (the spectra of the tensor maps) when the
-    // tiles run in one chunk
+    // the 16-column z passes apply to this plan copy (the spectra of the tensor maps) when the tiles run
+    // in one chunk
     bool zwide_ok(const DevPlan<T>& Q) const { return use_zwide && Q.use_tma && chunk_count() == 1; }
+    // grid: one CTA per field of a tile for the field-wise passes, one per tile for D+ and its transpose;
+    // the absorption pass reads its table unless the plan copy windows it (time reversal)
     void zwide_launch_on(const DevPlan<T>& Q, cudaStream_t s, int mode, int F) {
         if constexpr (std::is_same<T, float>::value) {
+            const bool fieldwise = (mode == SPEC_DIV || mode == SPEC_DIVT || mode == SPEC_ABS);
+            const float* mt = (mode != SPEC_ABS) ? kap3 : (Q.tr_kc2 > 0.f ? nullptr : abs3);
             cudaLaunchConfig_t lc = {};
-            lc.gridDim = dim3(F, (Q.nxh + 15) / 16, Q.ny);
+            lc.gridDim = dim3(fieldwise ? F : 1, (Q.nxh + 15) / 16, Q.ny);
             lc.stream = s;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             lc.attrs = attr;
             lc.numAttrs = 1;
-            note_launch(zwide_launch(&lc, mode, Q, kap3));
+            note_launch(zwide_launch(&lc, mode, Q, mt));
         } else {
             (void)Q; (void)s; (void)mode; (void)F;
         }
@@ -970,7 +981,7 @@ template <typename T> struct Plan : public PlanBase {
             if (yw) ywide_launch_on(Q, s, false, fin);
             else spec_launch_on<D, SPEC_PLAIN_FWD>(Q, s, 1, fin, t0, t1 - t0);
             if (name) mark(s, name);
-            if (zwide_ok(Q) && (MODE == SPEC_DIV || MODE == SPEC_DIVT || MODE == SPEC_ABS)) zwide_launch_on(Q, s, MODE, fin);
+            if (zwide_ok(Q)) zwide_launch_on(Q, s, MODE, fin);
             else if (zreg_ok(Q) && (zreg_all || MODE == SPEC_DIV || MODE == SPEC_DIVT)) zreg_launch_on(Q, s, MODE, t0, t1 - t0);
             else spec_launch_on<D, MODE>(Q, s, 2, 0, t0, t1 - t0);
             if (name) mark(s, "spec_y_inv");

@@ -44,6 +44,9 @@ TR_CASES = [
     ("2d_generic_lossy", lambda: synth.vessel_phantom_2d(n=60, pml=6, Nt=130, n_vessels=2, n_discs=2)),
     ("3d_lossy", lambda: synth.small_lossy_3d(shape=(16, 20, 24), pml=3, Nt=40)),
     ("3d_pow2_lossy", lambda: synth.small_lossy_3d(shape=(16, 16, 32), pml=3, Nt=36)),
+    # 128-point z-lines: FP32 takes the 16-column z passes, whose absorption pass computes the windowed
+    # multiplier inline
+    ("3d_wide_z_lossy", lambda: synth.small_lossy_3d(shape=(128, 16, 32), pml=3, Nt=30)),
 ]
 
 
@@ -99,6 +102,7 @@ ATD_CASES = [
     ("2d_pow2_lossless", lambda: synth.small_lossy_2d(shape=(32, 32), pml=4, Nt=33, n_sensors=12, alpha0=0.0)),
     ("3d_lossy", lambda: synth.small_lossy_3d(shape=(12, 16, 20), pml=3, Nt=21)),
     ("3d_pow2_lossy", lambda: synth.small_lossy_3d(shape=(16, 16, 16), pml=3, Nt=25)),
+    ("3d_wide_z_lossy", lambda: synth.small_lossy_3d(shape=(128, 16, 32), pml=3, Nt=21)),
 ]
 
 

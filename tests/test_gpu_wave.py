@@ -592,10 +592,10 @@ def test_wide_y_passes_match_oracle(dev, monkeypatch, name, kw):
                                      ("128x32x32_lossless", dict(shape=(128, 32, 32), pml=3, Nt=16, alpha0=0.0)),
                                      ("256x16x256_lossy", dict(shape=(256, 16, 256), pml=3, Nt=8))])
 def test_wide_z_passes_match_oracle(dev, monkeypatch, name, kw):
-    # the z passes with a field-wise multiply (D-, its transpose, the absorption pass) of 128- and
-    # 256-point z-lines on 16-column tiles, one field per CTA, kappa from the plan's table (the
-    # default), against the oracle and against the 8-column z passes (PAT_ZWIDE=0: k_zreg for D- and
-    # its transpose on 256-point lines, k_spec2 otherwise); shapes (nz, ny, nx), 2, 3, 2 and 9 tiles
+    # the z passes with the multiply (D+, D-, their transposes, the absorption pass) of 128- and
+    # 256-point z-lines on 16-column tiles, the multipliers from the plan's tables (the default),
+    # against the oracle and against the 8-column z passes (PAT_ZWIDE=0: k_zreg for D- and its
+    # transpose on 256-point lines, k_spec2 otherwise); shapes (nz, ny, nx), 2, 3, 2 and 9 tiles
     from paper_1603_02329_gb300 import _lib
 
     pb = synth.small_lossy_3d(**kw)

@@ -112,6 +112,8 @@ typedef struct {
                            in shared memory after one tensor copy per input field, with the multipliers
                            from tables the plan fills once (FP32 plans with tensor-copy staging; one
                            chunk; PAT_ZWIDE=0 off) */
+    int rowu1;          /* 1 when the u update and its transpose run one velocity component per CTA (FP32
+                           3-D plans with x-lines of 128 or 256 points; PAT_ROWU1=0 off) */
 } pat_plan_info_t;
 
 /* pat_plan_create -- build a plan: medium, geometry and time axis (Sec. II.A, Sec. III).

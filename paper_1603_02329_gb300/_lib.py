@@ -32,7 +32,7 @@ class pat_plan_info_t(ctypes.Structure):
                 ("dt", ctypes.c_double), ("c_ref", ctypes.c_double), ("path", ctypes.c_int),
                 ("layout", ctypes.c_int * 2), ("tuned", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("spec_chunks", ctypes.c_int), ("tma", ctypes.c_int),
-                ("zreg", ctypes.c_int), ("ywide", ctypes.c_int), ("zwide", ctypes.c_int)]
+                ("zreg", ctypes.c_int), ("ywide", ctypes.c_int), ("zwide", ctypes.c_int), ("rowu1", ctypes.c_int)]
 
 
 class pat_fista_opts(ctypes.Structure):

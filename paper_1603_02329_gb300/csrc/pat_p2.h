@@ -152,6 +152,10 @@ cudaError_t zwide_launch(const cudaLaunchConfig_t* lc, int mode, const DevPlan<f
 cudaError_t zwide_set_attrs();
 cudaError_t zwide_kap_table(const DevPlan<float>& P, float* kap, cudaStream_t s);
 cudaError_t zwide_abs_table(const DevPlan<float>& P, float* tab, cudaStream_t s);
+// the momentum row kernels with one velocity component per CTA (pat_rowu1.cuh), float, 3-D x-lines of
+// 128 and 256 points: launch k_row_u1 with the grid (nlines / R, 3), stream and attributes of `lc`
+cudaError_t rowu1_launch(const cudaLaunchConfig_t* lc, bool adjoint, const DevPlan<float>& P, int R, int flag);
+cudaError_t rowu1_set_attrs(int bytes);
 
 // row kernels of the per-phase path for power-of-two x-lines (pat_row2.cuh)
 enum Row2Kind : int { R2_FWD_U = 0, R2_FWD_RHO, R2_FWD_P, R2_ADJ_RHO, R2_ADJ_U, R2_ADJ_P };

@@ -338,6 +338,12 @@ template <typename T> struct Plan : public PlanBase {
             const int R0 = cfg.row_lines;
             use_row2 = !(er2 && std::atoi(er2) == 0) && h.fx.pow2 && h.fx.lgn >= 4 && h.fx.lgn <= 11 &&
                        (R0 & (R0 - 1)) == 0 && R0 <= 32;
+            // FP32 3-D x-lines of 128 and 256 points: the u update and its transpose one velocity component
+            // per CTA (PAT_ROWU1=0: all three in k_row2)
+            const char* eu1 = std::getenv("PAT_ROWU1");
+            use_rowu1 = use_row2 && sizeof(T) == 4 && D == 3 && P.fixed_len && (h.fx.lgn == 7 || h.fx.lgn == 8) &&
+                        !(eu1 && std::atoi(eu1) == 0);
+            info.rowu1 = use_rowu1 ? 1 : 0;
         }
         row_smem = row_smem_bytes<T>(D, h.nx, h.ldh, cfg.row_lines);
         row2_smem = use_row2 ? row2_layout<T>(D, h.nx, h.ldh, cfg.row_lines).bytes : 0;
@@ -771,6 +777,9 @@ template <typename T> struct Plan : public PlanBase {
         seta((const void*)k_spec<T, D, SPEC_GRADT>, spec_smem);
         if (e == cudaSuccess && use_spec2) e = spec2_set_attrs<T>(optin);
         if (e == cudaSuccess && use_row2) e = row2_set_attrs<T>(optin);
+        if constexpr (std::is_same<T, float>::value) {
+            if (e == cudaSuccess && use_rowu1) e = rowu1_set_attrs(optin);
+        }
         if (row2_smem > (size_t)optin) {
             set_error("grid too large for the shared-memory kernels of this device");
             return PAT_EINVAL;
@@ -781,6 +790,7 @@ template <typename T> struct Plan : public PlanBase {
 
     bool use_spec2 = false;
     bool use_row2 = false;
+    bool use_rowu1 = false;   // the momentum row kernels with one velocity component per CTA
     size_t row2_smem = 0;
 
     // one step kernel of the row pass (Row2Kind): the register-fused power-of-two kernel, or the
@@ -789,6 +799,20 @@ template <typename T> struct Plan : public PlanBase {
     void row_launch(int kind, const DevPlan<T>& Q, cudaStream_t s, int flag, T* data_row = nullptr,
                     const T* h_row = nullptr, T* qrow = nullptr, T* gc2 = nullptr, const T* p0c = nullptr) {
         const int R = cfg.row_lines, G = row_grid(), B = cfg.row_threads;
+        if constexpr (std::is_same<T, float>::value) {
+            if (use_rowu1 && D == 3 && (kind == R2_FWD_U || kind == R2_ADJ_U)) {
+                cudaLaunchConfig_t lc = {};
+                lc.gridDim = dim3(G, 3);
+                lc.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                attr[0].val.programmaticStreamSerializationAllowed = 1;
+                lc.attrs = attr;
+                lc.numAttrs = 1;
+                note_launch(rowu1_launch(&lc, kind == R2_ADJ_U, Q, R, flag));
+                return;
+            }
+        }
         if (use_row2) {
             cudaLaunchConfig_t lc = {};
             lc.gridDim = dim3(G);

@@ -136,6 +136,25 @@ def test_gradient_rho_matches_oracle(dev, name, make, prec, Ks):
         assert abs(float(np.sum(first * pb.rho))) <= 1e-9 * float(np.sum(np.abs(first * pb.rho)))
 
 
+@pytest.mark.parametrize("rowu1", ["1", "0"])
+def test_gradient_medium_fp32_3d_on_the_fused_paths(dev, monkeypatch, rowu1):
+    # FP32 3-D with 128-point x-lines: the checkpointed sweep's hooks in the one-component momentum
+    # row kernels (default) and in k_row2 (PAT_ROWU1=0), c0^2 and rho0 gradients against the oracle
+    from paper_1603_02329_gb300.api import PATOperator
+
+    monkeypatch.setenv("PAT_ROWU1", rowu1)
+    pb = synth.small_lossy_3d(shape=(12, 16, 128), pml=3, Nt=20)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(41).standard_normal((pb.Nt, ref.Ns))
+    op = PATOperator.from_problem(pb, precision="f32", device=dev)
+    assert op.info.rowu1 == (rowu1 == "1")
+    gr, gc, gp = op.gradient_medium(_T(pb.p0, "f32", dev), _T(h, "f32", dev), checkpoint_every=6)
+    gc_ref, gp_ref = pm.sound_speed_gradient(ref, pb.p0, h, pb.y)
+    assert rel(gc.cpu().numpy(), gc_ref) <= 1e-5
+    assert rel(gr.cpu().numpy(), pm.density_gradient(ref, pb.p0, h)) <= 1e-5
+    assert rel(gp.cpu().numpy(), gp_ref) <= 1e-5
+
+
 def test_gradient_medium_one_sweep_equals_separate_sweeps(dev):
     from paper_1603_02329_gb300.api import PATOperator
 

@@ -621,6 +621,34 @@ def test_wide_z_passes_match_oracle(dev, monkeypatch, name, kw):
     assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
 
 
+@pytest.mark.parametrize("name,kw", [("12x16x128_lossy", dict(shape=(12, 16, 128), pml=3, Nt=18)),
+                                     ("8x12x256_lossless", dict(shape=(8, 12, 256), pml=2, Nt=14, alpha0=0.0)),
+                                     ("16x16x256_lossy", dict(shape=(16, 16, 256), pml=3, Nt=14))])
+def test_one_component_momentum_rows_match_oracle(dev, monkeypatch, name, kw):
+    # the u update and its transpose with one velocity component per CTA (the default for FP32 3-D
+    # x-lines of 128 and 256 points) against the oracle and against k_row2's three components per
+    # CTA (PAT_ROWU1=0), on every tuned row layout's line count
+    pb = synth.small_lossy_3d(**kw)
+    ref = Operator.from_problem(pb)
+    h = np.random.default_rng(46).standard_normal((pb.Nt, ref.Ns))
+    d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
+    monkeypatch.setenv("PAT_AUTOTUNE", "0")
+    for lines in ("8", "4", "2"):
+        monkeypatch.setenv("PAT_ROW_LINES", lines)
+        out = []
+        for flag in ("1", "0"):
+            monkeypatch.setenv("PAT_ROWU1", flag)
+            op = _gpu_op(pb, "f32", dev)
+            assert op.info.rowu1 == (flag == "1") and op.info.layout[1] == int(lines)
+            d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
+            g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
+            assert rel(d, d_ref) <= TOL32, (lines, flag, rel(d, d_ref))
+            assert rel(g, g_ref) <= TOL32, (lines, flag, rel(g, g_ref))
+            out.append((d, g))
+            op.close()
+        assert rel(out[0][0], out[1][0]) <= 1e-6 and rel(out[0][1], out[1][1]) <= 1e-6
+
+
 @pytest.mark.parametrize("persist", ["1", "0"])
 def test_non_finite_output_is_reported(dev, monkeypatch, persist):
     # Failure detection on the host side of a solve: a NaN in p0 (forward) or in the residual

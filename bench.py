@@ -145,17 +145,33 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
 # is the set-up loads of the medium and tables), so the figure is taken as the full-length launch's.
 # Valid for the kernel version the captures were taken of (the 512^2 fixed-size k_persist2).
 MEASURED_TRAFFIC = {
-    ("vessel2d_512", "k_persist2_adj"): 6.66e6,
-    ("vessel2d_512", "k_persist2_fwd"): 8.26e6,
-    # the y forward transform at 256^3 (k_spec16 mode 0, tiles staged with tensor copies), from a capture
-    # of the three launches of one forward step (1, 3 and 2 fields: 682.8 MB over 12 field transfers)
-    # scaled to the mean launch of a forward + adjoint step (28 field transfers over 6 launches)
-    ("tube3d_256", "y_fwd"): 682.8e6 / 12 * 28 / 6,
+    ("vessel2d_512", "k_persist2_adj", "k_persist2_adj"): 6.66e6,
+    ("vessel2d_512", "k_persist2_fwd", "k_persist2_fwd"): 8.26e6,
+    # the y forward transform at 256^3 on 8-column tiles (k_spec16 mode 0, tiles staged with tensor
+    # copies; PAT_YWIDE=0), from a capture of the three launches of one forward step (1, 3 and 2 fields:
+    # 682.8 MB over 12 field transfers) scaled to the mean launch of a forward + adjoint step (28 field
+    # transfers over 6 launches)
+    ("tube3d_256", "y_fwd", "k_spec16"): 682.8e6 / 12 * 28 / 6,
+    # the y transforms at 256^3 on 16-column tiles (k_ywide, the default), from a capture of the six
+    # launches of one forward step: forward 674.3 MB over 12 field transfers, inverse 954.1 MB over 16,
+    # scaled to the mean launch of each direction in a forward + adjoint step (28 transfers, 6 launches)
+    ("tube3d_256", "y_fwd", "k_ywide"): 674.3e6 / 12 * 28 / 6,
+    ("tube3d_256", "y_inv", "k_ywide"): 954.1e6 / 16 * 28 / 6,
 }
 
 
-def measured_traffic(workload, kernel):
-    return MEASURED_TRAFFIC.get((workload, kernel))
+def measured_traffic(workload, kernel, version):
+    """DRAM bytes per launch of `kernel` from an ncu capture of that kernel version, or None."""
+    return MEASURED_TRAFFIC.get((workload, kernel, version))
+
+
+def kernel_version(op, fam):
+    """Which compiled kernel runs family `fam` on this plan (the captures above are per version)."""
+    if fam.startswith("k_persist"):
+        return fam
+    if fam in ("y_fwd", "y_inv"):
+        return "k_ywide" if int(getattr(op.info, "ywide", 0)) else "k_spec16"
+    return None
 
 
 def solve_bytes(N, Nt, w, D=2, lossy=True):
@@ -721,7 +737,7 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
             launches, share = fams[fam]["launches"], fams[fam]["ms"] / tot_ms
         ach = b / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": measured_traffic(name, fam) if not args.nt else None,
+                "traffic": measured_traffic(name, fam, kernel_version(op, fam)) if not args.nt else None,
                 "kernel": fam, "kernel_ms": ms, "algorithmic_bytes": b, "launches_per_step": launches,
                 "share_of_step": share, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "note": ("one persistent launch per solve keeps the state in shared memory (DRAM traffic: "
@@ -757,7 +773,9 @@ def measure(args, name, dev, world, rank, local, with_e2e=True):
            "config": dict(desc, l2="flushed between timed steps (512 MB write)", instances_per_gpu=1,
                           layout=list(op.info.layout), layout_tuned=int(op.info.tuned),
                           radix_schedule=int(op.info.schedule), spec_chunks=int(op.info.spec_chunks),
-                          parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)]),
+                          parallelism=f"replicas x{world}", path=PATH_NAMES[int(op.info.path)],
+                          kernels={"y_passes_16col": int(op.info.ywide), "z_passes_16col": int(op.info.zwide),
+                                   "u_rows_per_component": int(op.info.rowu1), "tensor_copies": int(op.info.tma)}),
            "roofline": roof, "step_roofline": step_roof, "fp32_roofline": alu, "kernel_ms": kernels, "e2e": e2e,
            "gpu_launches": launches, "clocks": clk}
     return rec, op, pb

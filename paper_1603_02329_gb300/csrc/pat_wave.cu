@@ -343,6 +343,9 @@ template <typename T> struct Plan : public PlanBase {
             const char* eu1 = std::getenv("PAT_ROWU1");
             use_rowu1 = use_row2 && sizeof(T) == 4 && D == 3 && P.fixed_len && (h.fx.lgn == 7 || h.fx.lgn == 8) &&
                         !(eu1 && std::atoi(eu1) == 0);
+            const char* eul = std::getenv("PAT_ROWU1_LINES");
+            const int ul = eul ? std::atoi(eul) : 0;
+            rowu1_pin = (ul >= 2 && ul <= 32 && (ul & (ul - 1)) == 0) ? ul : 0;
             info.rowu1 = use_rowu1 ? 1 : 0;
         }
         row_smem = row_smem_bytes<T>(D, h.nx, h.ldh, cfg.row_lines);
@@ -791,6 +794,13 @@ template <typename T> struct Plan : public PlanBase {
     bool use_spec2 = false;
     bool use_row2 = false;
     bool use_rowu1 = false;   // the momentum row kernels with one velocity component per CTA
+    int rowu1_pin = 0;        // PAT_ROWU1_LINES: x-lines per CTA of those kernels (0: rowu1_lines())
+    // x-lines per CTA of the one-component momentum kernels: 16 where they divide the grid's lines (a
+    // 256-thread CTA then has a butterfly per thread in every stage), else the row kernels' count
+    int rowu1_lines() const {
+        if (rowu1_pin > 0 && P.nlines % rowu1_pin == 0) return rowu1_pin;
+        return (P.nlines % 16 == 0) ? 16 : cfg.row_lines;
+    }
     size_t row2_smem = 0;
 
     // one step kernel of the row pass (Row2Kind): the register-fused power-of-two kernel, or the
@@ -802,14 +812,15 @@ template <typename T> struct Plan : public PlanBase {
         if constexpr (std::is_same<T, float>::value) {
             if (use_rowu1 && D == 3 && (kind == R2_FWD_U || kind == R2_ADJ_U)) {
                 cudaLaunchConfig_t lc = {};
-                lc.gridDim = dim3(G, 3);
+                const int RU = rowu1_lines();
+                lc.gridDim = dim3(P.nlines / RU, 3);
                 lc.stream = s;
                 cudaLaunchAttribute attr[1];
                 attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
                 attr[0].val.programmaticStreamSerializationAllowed = 1;
                 lc.attrs = attr;
                 lc.numAttrs = 1;
-                note_launch(rowu1_launch(&lc, kind == R2_ADJ_U, Q, R, flag));
+                note_launch(rowu1_launch(&lc, kind == R2_ADJ_U, Q, RU, flag));
                 return;
             }
         }

@@ -627,19 +627,21 @@ def test_wide_z_passes_match_oracle(dev, monkeypatch, name, kw):
 def test_one_component_momentum_rows_match_oracle(dev, monkeypatch, name, kw):
     # the u update and its transpose with one velocity component per CTA (the default for FP32 3-D
     # x-lines of 128 and 256 points) against the oracle and against k_row2's three components per
-    # CTA (PAT_ROWU1=0), on every tuned row layout's line count
+    # CTA (PAT_ROWU1=0), for 2 to 32 x-lines per CTA of the one-component kernels (32: more than
+    # 8 x 12 x 256 has in a multiple, so its default of 16 runs)
     pb = synth.small_lossy_3d(**kw)
     ref = Operator.from_problem(pb)
     h = np.random.default_rng(46).standard_normal((pb.Nt, ref.Ns))
     d_ref, g_ref = ref.forward(pb.p0), ref.adjoint(h)
     monkeypatch.setenv("PAT_AUTOTUNE", "0")
-    for lines in ("8", "4", "2"):
-        monkeypatch.setenv("PAT_ROW_LINES", lines)
+    monkeypatch.setenv("PAT_ROW_LINES", "8")
+    for lines in ("16", "8", "2", "32"):
+        monkeypatch.setenv("PAT_ROWU1_LINES", lines)
         out = []
         for flag in ("1", "0"):
             monkeypatch.setenv("PAT_ROWU1", flag)
             op = _gpu_op(pb, "f32", dev)
-            assert op.info.rowu1 == (flag == "1") and op.info.layout[1] == int(lines)
+            assert op.info.rowu1 == (flag == "1") and op.info.layout[1] == 8
             d = op.forward(_t(pb.p0, "f32", dev)).cpu().numpy()
             g = op.adjoint(_t(h, "f32", dev)).cpu().numpy()
             assert rel(d, d_ref) <= TOL32, (lines, flag, rel(d, d_ref))

@@ -6,10 +6,11 @@ sensor array at stride 2, Nt = 1500, FP32 fields (about 1 GB of state: larger th
 pat_forward_plan + pat_adjoint through the C ABI: 2 N Nt grid-point-steps.  value = grid-point-steps
 per second over all ranks (Gpt-steps/s).
 
-The default run adds three records to the JSON line:
+The default run adds these records to the JSON line:
   - "vessel2d_512": the same measurement on the 2-D 512^2 absorbing workload (Nt = 2000, 512 line
     sensors), whose state stays in shared memory (one persistent kernel per solve), with the
-    time-reversal image, FISTA warm-started from it, and the adjoint-then-discretize deviation;
+    time-reversal image, FISTA warm-started from it, the adjoint-then-discretize deviation, and the
+    oracle's bounded sample timed on one core and as one replica per host core;
   - "mg_vs_fista": wall time of 3-level MG-FISTA (256^3 / 128^3 / 64^3) and of single-grid FISTA to
     the same relative error on 40 dB data, 12 iterations of FISTA at most;
   - "mg_precision": relative L2 distance of the FP32 iterates from the FP64 iterates of the same
@@ -336,6 +337,59 @@ def cpu_baseline(args, pb):
     return {"value": 2.0 * pb.N * Nt_s / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one forward+adjoint over the first {Nt_s} of {pb.Nt} time steps of the same grid "
                       f"({t:.1f} s), FP64 numpy"}
+
+
+def _oracle_replica(name, Nt_s, barrier, results):
+    """One replica of the bounded oracle sample, in its own spawned process on one core: build the
+    workload's problem, wait for every replica to be ready, time one forward+adjoint over the first
+    Nt_s steps.  perf_counter is the system-wide monotonic clock on Linux, so the start and end
+    stamps of different replicas compare."""
+    from oracle.pat_oracle import Operator
+
+    pb, _, _ = workload(name, 0)
+    op = Operator.from_problem(pb, Nt=min(Nt_s, pb.Nt))
+    barrier.wait()
+    t0 = time.perf_counter()
+    op.adjoint(op.forward(pb.p0))
+    results.put((t0, time.perf_counter(), pb.N, min(Nt_s, pb.Nt)))
+
+
+def cpu_baseline_all_cores(name, Nt_s, cores=0, timeout_s=300.0):
+    """The bounded oracle sample of cpu_baseline on every host core at once.  One solve does not split
+    across cores (its time steps are sequential and numpy's FFT runs one thread), so each core runs
+    an independent replica of the same sample; value = the grid-point-steps of all replicas over the
+    span from the first replica's start to the last one's end.  The replicas are spawned processes
+    (no fork of a process that holds a CUDA context) with one thread each."""
+    import multiprocessing as mp
+
+    C = cores if cores > 0 else min(len(os.sched_getaffinity(0)), 32)   # at most 32 replicas on a shared host
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    barrier, results = ctx.Barrier(C), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(name, Nt_s, barrier, results)) for _ in range(C)]
+    try:
+        for p in procs:
+            p.start()
+        got = [results.get(timeout=timeout_s) for _ in range(C)]
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        for p in procs:
+            p.join(timeout=10.0)
+            if p.is_alive():
+                p.terminate()
+                p.join()
+    span = max(g[1] for g in got) - min(g[0] for g in got)
+    N, nt = got[0][2], got[0][3]
+    return {"value": 2.0 * N * nt * C / span / 1e9, "unit": UNIT, "cores": C, "kind": "oracle", "span_s": span,
+            "sample": f"{C} independent replicas, one per core, each one forward+adjoint over the first {nt} "
+                      f"time steps of the same grid ({span:.1f} s from the first start to the last end; one "
+                      f"replica alone: see cpu_baseline), FP64 numpy"}
 
 
 def batch_vs_sequential(dev):
@@ -825,9 +879,17 @@ def main():
     del op
     torch.cuda.empty_cache()
     if rank == 0 and args.workload == "tube3d_256" and not args.no_secondary and not args.nt:
-        rec2, op2, _ = measure(args, "vessel2d_512", dev, 1, 0, local, with_e2e=True)
+        rec2, op2, pb2 = measure(args, "vessel2d_512", dev, 1, 0, local, with_e2e=True)
         op2.close()
         rec2["steps"], rec2["warmup"] = args.steps, args.warmup
+        if not args.no_cpu:
+            a2 = argparse.Namespace(**vars(args))
+            a2.workload = "vessel2d_512"
+            rec2["cpu_baseline"] = cpu_baseline(a2, pb2)
+            try:
+                rec2["cpu_baseline_all_cores"] = cpu_baseline_all_cores("vessel2d_512", 200)
+            except Exception as e:   # the record is context: its failure must not cost the bench line
+                rec2["cpu_baseline_all_cores"] = {"error": f"{type(e).__name__}: {e}"}
         rec2["tr_atd"] = tr_atd_record(dev)
         out["vessel2d_512"] = rec2
     if (args.mg or args.mg_default) and rank == 0:

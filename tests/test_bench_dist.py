@@ -80,3 +80,17 @@ def test_single_rank_helpers_need_no_process_group():
     assert bench.max_over_ranks(1.5, 1) == 1.5
     assert bench.aggregate_gpts(2e9, 1, 2.0) == 1.0
     assert json.dumps(bench.dist_env()) is not None
+
+
+def test_cpu_baseline_all_cores_counts_every_replica():
+    """The all-cores oracle leg: spawned single-thread replicas of the same bounded sample, the
+    value counting every replica's grid-point-steps over the span from the first start to the
+    last end, so it is at most the replicas' count times one replica's rate."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.cpu_baseline_all_cores("disc2d_168", 60, cores=2, timeout_s=120.0)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == bench.UNIT
+    assert r["span_s"] > 0
+    units = 2 * 2.0 * 168 * 168 * 60     # 2 replicas x 2 N Nt_s
+    assert r["value"] == pytest.approx(units / r["span_s"] / 1e9, rel=1e-12)

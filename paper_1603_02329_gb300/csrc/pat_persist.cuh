@@ -68,12 +68,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, unsigned nblocks, u
         unsigned long long spins = 0;
         const unsigned long long t0 = globaltimer_ns();
         int ab = 0;
+        // one load per poll: the error word of another CTA and the clock are looked at every 64th
+        // poll, so the poll that sees the last arrival is not queued behind a second L2 round trip
         while (ld_acquire_gpu(&gbar[0]) < target) {
+            if ((++spins & 63) != 0) continue;
             if (*(volatile unsigned*)&gbar[2] != 0u) {
                 ab = 1;
                 break;
             }
-            if (++spins > kBarrierSpinLimit || ((spins & 63) == 0 && globaltimer_ns() - t0 > limit_ns)) {
+            if (spins > kBarrierSpinLimit || globaltimer_ns() - t0 > limit_ns) {
                 atomicExch(&gbar[2], (unsigned)PAT_ETIMEOUT);
                 ab = 1;
                 break;

@@ -141,13 +141,14 @@ def kernel_bytes(name, N, Nh, w, D=2, lossy=True):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from
-# ncu captures of the same command with the time axis cut to Nt = 20 and Nt = 40: the two agree
-# (forward 8.25 / 8.26 MB, adjoint 6.60 / 6.72 MB; the state stays in shared memory, so the traffic
-# is the set-up loads of the medium and tables), so the figure is taken as the full-length launch's.
-# Valid for the kernel version the captures were taken of (the 512^2 fixed-size k_persist2).
+# ncu captures of the same command with the time axis cut to Nt = 20 (and, for an earlier build of
+# the kernel, Nt = 40: the two agreed, forward 8.25 / 8.26 MB, adjoint 6.60 / 6.72 MB; the state
+# stays in shared memory, so the traffic is the set-up loads of the medium and tables), so the
+# figure is taken as the full-length launch's.  Valid for the kernel version the captures were
+# taken of (the 512^2 fixed-size k_persist2 with the one-load barrier poll).
 MEASURED_TRAFFIC = {
-    ("vessel2d_512", "k_persist2_adj", "k_persist2_adj"): 6.66e6,
-    ("vessel2d_512", "k_persist2_fwd", "k_persist2_fwd"): 8.26e6,
+    ("vessel2d_512", "k_persist2_adj", "k_persist2_adj"): 6.570e6,
+    ("vessel2d_512", "k_persist2_fwd", "k_persist2_fwd"): 8.250e6,
     # the y forward transform at 256^3 on 8-column tiles (k_spec16 mode 0, tiles staged with tensor
     # copies; PAT_YWIDE=0), from a capture of the three launches of one forward step (1, 3 and 2 fields:
     # 682.8 MB over 12 field transfers) scaled to the mean launch of a forward + adjoint step (28 field

@@ -471,7 +471,8 @@ def phase_trace(op, x, data, stream, nk):
 
 
 def c2_gradient_timing(op, pb, K, dev, dtype):
-    """Checkpointed c0^2 gradient (pat_gradient_c2, interval K) against one forward + adjoint."""
+    """Checkpointed c0^2 gradient (pat_gradient_c2, interval K) and the c0^2 + rho0 + p0 gradients of one
+    sweep (pat_gradient_medium), each against one forward + adjoint."""
     import torch
 
     x = torch.tensor(pb.p0, dtype=dtype, device=dev)
@@ -487,12 +488,17 @@ def c2_gradient_timing(op, pb, K, dev, dtype):
 
     t_fa = timed(lambda: op.adjoint(op.forward(x)))
     t_g = timed(lambda: op.gradient_c2(x, h, checkpoint_every=K))
+    # the c0^2, rho0 and p0 gradients from one sweep (pat_gradient_medium)
+    t_m = timed(lambda: op.gradient_medium(x, h, checkpoint_every=K, want=("c2", "rho", "p0")))
     w = 4 if dtype == torch.float32 else 8
     nseg = (pb.Nt - 2) // K + 1
     nh = int(np.prod(pb.shape[:-1])) * ((pb.shape[-1] // 2 + 1 + 7) // 8 * 8)
     d = len(pb.shape)
     return {"K": K, "fwd_adj_s": t_fa, "gradient_s": t_g, "ratio": t_g / t_fa,
-            "checkpoint_bytes": nseg * (2 * d * pb.N + 2 * nh) * w, "q_bytes": min(K, pb.Nt) * pb.N * w}
+            "checkpoint_bytes": nseg * (2 * d * pb.N + 2 * nh) * w, "q_bytes": min(K, pb.Nt) * pb.N * w,
+            "medium_gradient_s": t_m, "medium_ratio": t_m / t_fa,
+            # the density gradient also stores D+p and D-u (2 d fields) per level of a segment
+            "medium_extra_bytes": (min(K, pb.Nt) + 1) * 2 * d * pb.N * w}
 
 
 def mg_vs_fista(args, dev, pb):

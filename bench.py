@@ -340,7 +340,7 @@ def cpu_baseline(args, pb):
                       f"({t:.1f} s), FP64 numpy"}
 
 
-def _oracle_replica(name, Nt_s, barrier, results):
+def _oracle_replica(name, Nt_s, barrier, results, wait_s=120.0):
     """One replica of the bounded oracle sample, in its own spawned process on one core: build the
     workload's problem, wait for every replica to be ready, time one forward+adjoint over the first
     Nt_s steps.  perf_counter is the system-wide monotonic clock on Linux, so the start and end
@@ -349,19 +349,21 @@ def _oracle_replica(name, Nt_s, barrier, results):
 
     pb, _, _ = workload(name, 0)
     op = Operator.from_problem(pb, Nt=min(Nt_s, pb.Nt))
-    barrier.wait()
+    barrier.wait(timeout=wait_s)   # a replica that failed to start breaks the barrier for the others
     t0 = time.perf_counter()
     op.adjoint(op.forward(pb.p0))
     results.put((t0, time.perf_counter(), pb.N, min(Nt_s, pb.Nt)))
 
 
-def cpu_baseline_all_cores(name, Nt_s, cores=0, timeout_s=300.0):
+def cpu_baseline_all_cores(name, Nt_s, cores=0, timeout_s=180.0):
     """The bounded oracle sample of cpu_baseline on every host core at once.  One solve does not split
     across cores (its time steps are sequential and numpy's FFT runs one thread), so each core runs
     an independent replica of the same sample; value = the grid-point-steps of all replicas over the
     span from the first replica's start to the last one's end.  The replicas are spawned processes
-    (no fork of a process that holds a CUDA context) with one thread each."""
+    (no fork of a process that holds a CUDA context) with one thread each.  A replica that fails ends
+    the measurement with an error at once; the whole leg is bounded by timeout_s."""
     import multiprocessing as mp
+    import queue
 
     C = cores if cores > 0 else min(len(os.sched_getaffinity(0)), 32)   # at most 32 replicas on a shared host
     ctx = mp.get_context("spawn")
@@ -369,11 +371,20 @@ def cpu_baseline_all_cores(name, Nt_s, cores=0, timeout_s=300.0):
     for k in saved:
         os.environ[k] = "1"
     barrier, results = ctx.Barrier(C), ctx.Queue()
-    procs = [ctx.Process(target=_oracle_replica, args=(name, Nt_s, barrier, results)) for _ in range(C)]
+    procs = [ctx.Process(target=_oracle_replica, args=(name, Nt_s, barrier, results, timeout_s)) for _ in range(C)]
     try:
         for p in procs:
             p.start()
-        got = [results.get(timeout=timeout_s) for _ in range(C)]
+        got = []
+        deadline = time.perf_counter() + timeout_s
+        while len(got) < C:
+            try:
+                got.append(results.get(timeout=1.0))
+            except queue.Empty:
+                if any(p.exitcode not in (None, 0) for p in procs):
+                    raise RuntimeError("an oracle replica exited with an error")
+                if time.perf_counter() > deadline:
+                    raise TimeoutError(f"oracle replicas unfinished after {timeout_s:.0f} s")
     finally:
         for k, v in saved.items():
             if v is None:

@@ -94,3 +94,17 @@ def test_cpu_baseline_all_cores_counts_every_replica():
     assert r["span_s"] > 0
     units = 2 * 2.0 * 168 * 168 * 60     # 2 replicas x 2 N Nt_s
     assert r["value"] == pytest.approx(units / r["span_s"] / 1e9, rel=1e-12)
+
+
+def test_cpu_baseline_all_cores_fails_fast_when_a_replica_fails():
+    """A replica that raises (here: a workload name whose grid size does not parse) ends the leg
+    with an error at once instead of leaving the others waiting at the start barrier."""
+    import time
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    t0 = time.perf_counter()
+    with pytest.raises(RuntimeError):
+        bench.cpu_baseline_all_cores("tube3d_x", 2, cores=2, timeout_s=60.0)
+    assert time.perf_counter() - t0 < 45.0

@@ -1,6 +1,7 @@
-"""Host arithmetic of the benchmark's roofline: the algorithmic bytes it divides by the measured
+"""Host logic of the benchmark: the roofline's algorithmic bytes, which it divides by the measured
 kernel times, checked against sums written out by hand from the operands each kernel reads and
-writes once (real fields of N values, half spectra of Ny Nz (Nx/2 + 1) complex values)."""
+writes once (real fields of N values, half spectra of Ny Nz (Nx/2 + 1) complex values); and the
+summary of the clocks sampled during the timed region."""
 import os
 import sys
 
@@ -72,3 +73,20 @@ def test_family_time_counts_chunks():
     assert four["launches"] == 4 * one["launches"] and four["bytes"] == one["bytes"]
     assert one["ms"] == pytest.approx(3 * 0.5 + 3 * 0.25)
     assert four["ms"] == pytest.approx(4 * one["ms"])
+
+
+def test_clock_summary_of_sampled_lines():
+    # nvidia-smi --format=csv,noheader,nounits lines: index, clocks.sm, clocks.max.sm, power.draw,
+    # active reasons mask, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    c = bench.ClockSampler.summarize(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = lines[:1] + ["0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"]
+    assert bench.ClockSampler.summarize(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize(["x"]) is None

@@ -30,6 +30,7 @@
 #ifndef PAT_H
 #define PAT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -121,3 +121,31 @@ def test_host_side_argument_validation(L):
     # p0 smoothing: NULL plan / arguments (checked before any device work)
     assert L.pat_plan_set_smoothing(None, 1) == PAT_EINVAL
     assert L.pat_plan_smooth(None, None, None, None) == PAT_EINVAL
+
+
+def test_header_is_plain_c_and_every_declaration_links(L, tmp_path):
+    """include/*.h compile as strict C99 and C++17 on their own (no other header before them), and a C
+    program that takes the address of every declared entry point links against the library: the
+    boundary is plain C with unmangled names."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not found")
+    names = _declared_symbols()
+    src = tmp_path / "abi.c"
+    body = "\n".join(f"    (fn_t)&{n}," for n in names)
+    src.write_text('#include "pat.h"\n#include <stdio.h>\ntypedef void (*fn_t)(void);\n'
+                   f"static const fn_t entry[] = {{\n{body}\n}};\n"
+                   'int main(void) { printf("%d\\n", (int)(sizeof(entry) / sizeof(entry[0]))); return 0; }\n')
+    inc = os.path.join(ROOT, "include")
+    for std, lang in (("c99", "c"), ("c++17", "c++")):
+        r = subprocess.run([cc if lang == "c" else (shutil.which("g++") or cc), f"-std={std}", "-Wall", "-Wextra",
+                            "-pedantic", "-Werror", "-fsyntax-only", "-I", inc, "-x", lang, str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    so = L._name   # the path the binding loaded the library from
+    exe = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-I", inc, str(src), so, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

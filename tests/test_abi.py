@@ -149,3 +149,67 @@ def test_header_is_plain_c_and_every_declaration_links(L, tmp_path):
     exe = tmp_path / "abi"
     r = subprocess.run([cc, "-std=c99", "-I", inc, str(src), so, "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def _prototypes():
+    """name -> number of parameters of every pat_* function declared in include/*.h"""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(pat_[A-Za-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+            params = " ".join(m.group(2).split())
+            if m.group(1).startswith("pat_iter_callback") or params in ("", "void"):
+                out.setdefault(m.group(1), 0)
+                continue
+            depth, n = 0, 1
+            for ch in params:
+                depth += ch == "("
+                depth -= ch == ")"
+                n += ch == "," and depth == 0
+            out[m.group(1)] = n
+    return out
+
+
+def test_binding_declares_every_entry_point_with_the_headers_arity(L):
+    """The ctypes binding gives every declared entry point its argument list (ctypes would otherwise
+    pass Python ints as 32-bit C ints) with as many arguments as the prototype."""
+    protos = _prototypes()
+    assert set(_declared_symbols()) <= set(protos)
+    for name in _declared_symbols():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == protos[name], (name, len(f.argtypes), protos[name])
+
+
+def test_binding_structs_match_the_c_layout(L, tmp_path):
+    """Size and field offsets of every struct the binding mirrors, as gcc lays them out from pat.h."""
+    import shutil
+    import subprocess
+
+    from paper_1603_02329_gb300 import _lib
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not found")
+    structs = [_lib.pat_grid, _lib.pat_sensors, _lib.pat_plan_info_t, _lib.pat_fista_opts, _lib.pat_fista_report]
+    lines = ['#include "pat.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for S in structs:
+        c = S.__name__
+        lines.append(f'    printf("{c} size %zu\\n", sizeof({c}));')
+        for fname, _ in S._fields_:
+            cf = fname.rstrip("_")   # lambda_ in Python is lambda in C
+            lines.append(f'    printf("{c} {fname} %zu\\n", offsetof({c}, {cf}));')
+    lines += ["    return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for S in structs:
+        assert got[(S.__name__, "size")] == ctypes.sizeof(S), S.__name__
+        for fname, _ in S._fields_:
+            assert got[(S.__name__, fname)] == getattr(S, fname).offset, (S.__name__, fname)

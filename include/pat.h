@@ -148,13 +148,16 @@ pat_status pat_plan_get_info(const pat_plan* plan, pat_plan_info_t* info);
  *   data  [Nt][Ns] output, overwritten (host or device, plan precision).
  * Runs the whole Nt-step solve on `stream` as one launch: a persistent kernel for 2-D plans whose
  * state fits in the GPU's shared memory (pat_plan_info_t.path 1 or 2), otherwise one CUDA-graph
- * launch of the per-phase kernels (path 0). */
+ * launch of the per-phase kernels (path 0).  The inputs and outputs move by cudaMemcpyAsync on
+ * `stream`: an output in device or page-locked host memory is ready once `stream` is synchronised,
+ * one in pageable host memory when the call returns (that copy waits for the solve). */
 pat_status pat_forward_plan(pat_plan* plan, const void* p0, void* data, void* stream);
 
 /* pat_adjoint -- grad = H^T residual (Sec. III, Eq. (adjj); Sec. IV, Eq. (Six) uses it as
  * grad f = H^T (H x - p_hat)).  The transpose is exact: <H x, h> = <x, H^T h> to rounding.
  *   residual [Nt][Ns] input (host or device, plan precision).
- *   grad     [N]      output, overwritten (host or device, plan precision). */
+ *   grad     [N]      output, overwritten (host or device, plan precision; ready as in
+ *                     pat_forward_plan). */
 pat_status pat_adjoint(pat_plan* plan, const void* residual, void* grad, void* stream);
 
 /* pat_plan_set_smoothing -- the optional smoothing of the initial pressure (Sec. VI.A: the high
